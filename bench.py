@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the space-angle sawtooth multigrid hot path on GB300.
+
+One step = one sawtooth cycle (Fig. multi_grid_it) over every group of the
+workload: fine PG residual, restriction to every level, upwind Jacobi on
+every level with UpSamp, update, fine PG Jacobi, scalar flux and the FP64
+residual norm.  Default workload: 256 x 256 nodes, 16 x 32 directions (512),
+one group, seeded 8 x 8 checkerboard of sigma_t ~ logU[0.1, 10], scattering
+ratio 0.9, source 1, vacuum, quadratic ConvFEM with PG, psi in FP32.
+
+Metric: MG unknown-updates/s = (unknowns x cycles) / seconds, all ranks.
+Multi-GPU runs are independent replicas (one problem per rank, no
+collective on the data path; the path does not need one).
+
+--impl reference times the FP64 CPU oracle (the slow reference program of
+this repository) on the host cores, on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2301_09991_gb300 import inputs as I  # noqa: E402
+
+METRIC = "MG unknown-updates/s"
+UNIT = "unknown-updates/s"
+WORKLOADS = {
+    # name: (builder, description)
+    "checker256": (lambda: I.checkerboard(n=256, n_polar=16, n_azim=32, blocks=8, seed=2, c=0.9),
+                   "256x256 nodes, 16x32 dirs (512), 1 group, 8x8 checkerboard sigma_t~logU[0.1,10] "
+                   "seed 2, c=0.9, q=1, vacuum, quadratic ConvFEM + anisotropic PG"),
+    "checker64": (lambda: I.checkerboard(n=64, n_polar=8, n_azim=16, blocks=8, seed=2, c=0.9),
+                  "64x64 nodes, 8x16 dirs (128), small case of the same family"),
+}
+# Algorithmic work per unknown ("Roofline"):
+PG_FLOPS_PER_UNKNOWN = 250.0  # separable evaluation of Eq. Petrov + Sec. 2.6 on interior nodes
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    # FFMA: 128 lanes/SM x 2 flops x 152 SMs x clock
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profiles(kernel):
+    """dram bytes per launch from the committed ncu summary of `kernel`, or
+    None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src_hash = {}
+    for f in ("k_pg.cu", "k_mg.cu"):
+        p = os.path.join(ROOT, "paper_2301_09991_gb300", "csrc", f)
+        with open(p, "rb") as fh:
+            src_hash[f] = hashlib.sha256(fh.read()).hexdigest()[:16]
+    with open(path) as fh:
+        for line in fh:
+            m = re.match(r"\s*(\w+)\s+bytes_per_launch=(\S+)\s+src=(\S+):(\w+)", line)
+            if m and m.group(1) == kernel:
+                if src_hash.get(m.group(3)) != m.group(4):
+                    return None
+                return float(m.group(2))
+    return None
+
+
+def cpu_baseline(workload, sample_cycles=1):
+    """FP64 oracle: sample_cycles sawtooth cycles of the full workload on all
+    host cores (OpenMP over direction planes)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    prob = WORKLOADS[workload][0]()
+    op = O.OracleProblem(prob)
+    psi = op.zeros()
+    N = int(np.prod(op.shape))
+    t0 = time.perf_counter()
+    for _ in range(sample_cycles):
+        psi, _, _ = op.mg_cycle(psi)
+    dt = time.perf_counter() - t0
+    return {"value": N * sample_cycles / dt, "unit": UNIT, "cores": O.omp_threads(), "kind": "oracle",
+            "sample": "%d FP64 oracle cycle(s) of the full %s workload (%d unknowns), %.1f s"
+                      % (sample_cycles, workload, N, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    # bounded sample: the same checkerboard family on a 128x128 window of the
+    # 256^2 grid (4x4 blocks of 32x32 nodes), all 512 directions
+    prob = I.checkerboard(n=128, n_polar=16, n_azim=32, blocks=4, seed=2, c=0.9)
+    op = O.OracleProblem(prob)
+    psi = op.zeros()
+    N = int(np.prod(op.shape))
+    for _ in range(args.warmup):
+        psi, _, _ = op.mg_cycle(psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        psi, _, _ = op.mg_cycle(psi)
+    dt = time.perf_counter() - t0
+    value = N * args.steps / dt
+    sample = ("FP64 oracle cycles on a 128x128-node window (4x4 checkerboard blocks) of the %s "
+              "workload, all 512 directions, %d unknowns per step" % (args.workload, N))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.omp_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="btmg", choices=["btmg", "reference"])
+    ap.add_argument("--workload", default="checker256", choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cycles", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2301_09991_gb300 import btmg
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+
+    code = {"f32": btmg.F32, "f64": btmg.F64, "bf16": btmg.BF16, "f16": btmg.F16}[args.dtype]
+    prob = WORKLOADS[args.workload][0]()
+    gp = btmg.Problem(prob, dtype=code, pg=1)
+    N = gp.num_unknowns()
+    psi = gp.zeros()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        gp.mg_cycle(psi, want_residual=False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    gp.profile(True)
+    n0 = gp.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        gp.mg_cycle(psi, want_residual=False)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = gp.profile_read()
+    gp.profile(False)
+    launches = gp.launch_count() - n0
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * args.steps * ws / (ms / 1000.0)
+
+    # end to end through the public call with host buffers: H2D of psi from
+    # pinned memory, one cycle, D2H of psi and of the FP64 residual
+    hpsi = torch.zeros(gp.shape, dtype=gp.torch_dtype).pin_memory()
+    hpsi.copy_(psi.cpu())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        dpsi = hpsi.to("cuda", non_blocking=True)
+        gp.mg_cycle(dpsi, want_residual=True)  # reads the residual back (synchronises)
+        hpsi.copy_(dpsi, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    nbytes = psi.numel() * psi.element_size()
+    e2e = {"value": N * args.e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes + 8}
+
+    # roofline of the dominant kernel class (most device time in the timed region)
+    pk, src = peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    avg_s = dom_ms / max(dom_n, 1) / 1000.0
+    per_launch_unknowns = N // gp.G
+    if dom in ("pg_residual", "pg_jacobi"):
+        sm_mhz = float(pk.get("sm_max_mhz", SM_MAX_MHZ))
+        achieved = PG_FLOPS_PER_UNKNOWN * per_launch_unknowns / avg_s / 1e12
+        peak = fp32_peak_tflops(sm_mhz)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_from_profiles("k_pg"),
+                "kernel": "k_pg (%s)" % dom,
+                "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz}
+    else:
+        # upwind fine: reads src + psi (+ coarse delta), writes psi
+        esz = psi.element_size()
+        byts = per_launch_unknowns * (4 + 2 * esz)
+        achieved = byts / avg_s / 1e9
+        peak = float(pk["hbm_gbs"])
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profiles("k_upwind"), "kernel": "k_upwind (%s)" % dom,
+                "peak_source": "%s copy bandwidth" % src}
+    roof["kernel_ms"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items()}
+    roof["kernel_share"] = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
+                       "unknowns_per_gpu": N, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (psi, psi_tmp and r_1 are %d MB each)"
+                             % (nbytes // 2 ** 20)},
+            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

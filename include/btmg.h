@@ -1,0 +1,187 @@
+/*
+ * btmg.h -- C ABI of the GB300 (sm_103a) space-angle sawtooth multigrid
+ * solver for the fixed-source 2D-space x 2D-angle discretised Boltzmann
+ * transport equation (Phillips et al., arXiv 2301.09991).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an int status: BTMG_OK (0) or a negative BTMG_ERR_*.
+ *    No C++ exception crosses the ABI.  btmg_error_string() names a status;
+ *    btmg_last_error() gives a per-thread detail message for the last failure.
+ *  - Angular-flux buffers (psi, r, corrections) and scalar-flux buffers are
+ *    CALLER-OWNED DEVICE pointers (e.g. torch.Tensor.data_ptr()).  The library
+ *    never frees or retains them beyond the call.  The library owns its
+ *    workspaces and frees them in btmg_destroy_problem().
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are stream-ordered and asynchronous unless stated.
+ *  - A problem handle is not thread-safe: one host thread at a time.
+ *  - Layout of an angular flux with G groups on level l (level 0 = finest):
+ *      psi[g][n][y][x], n = face*(nr*nc) + j*nc + i,
+ *    dense, x fastest; face = 4*(xi<0) + 2*(nu<0) + (mu<0) is the octahedron
+ *    face, j the polar and i the azimuthal patch index inside it (Sec. 2.2,
+ *    Fig. octa).  btmg_get_layout() returns the strides.
+ *  - Element type of psi is desc.psi_dtype.  Compute ("accumulation") type
+ *    is FP64 for BTMG_F64 storage and FP32 otherwise; residuals, scalar
+ *    fluxes and explicit sources passed to the library use the compute type.
+ */
+#ifndef BTMG_H
+#define BTMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BTMG_OK 0
+#define BTMG_ERR_INVALID_ARG (-1)
+#define BTMG_ERR_CUDA (-2)
+#define BTMG_ERR_OOM (-3)
+#define BTMG_ERR_NOT_CONVERGED (-4)
+#define BTMG_ERR_DIVERGED (-5)
+#define BTMG_ERR_TIMEOUT (-6)
+#define BTMG_ERR_NAN (-7)
+#define BTMG_ERR_UNSUPPORTED (-8)
+
+/* storage types of psi */
+#define BTMG_F64 0
+#define BTMG_F32 1
+#define BTMG_BF16 2
+#define BTMG_F16 3
+
+/* boundary conditions (Sec. 2.1): vacuum psi = 0 on incoming directions;
+ * reflective d psi / dn = 0 (halo copies the adjacent interior node). */
+#define BTMG_VACUUM 0
+#define BTMG_REFLECTIVE 1
+
+/* smoother kinds for btmg_smooth */
+#define BTMG_SMOOTH_UPWIND 0
+#define BTMG_SMOOTH_PG 1
+
+typedef struct btmg_problem btmg_problem;
+
+/* Problem statement (Sec. 2.1, Eq. gov-simple; materials per region as in
+ * Tab. sing_duct_data).  Nodes are cell centred, dx = lx/nx (Sec. 3.1).
+ * All host arrays are copied by btmg_create_problem.                       */
+typedef struct {
+  int32_t nx, ny;          /* nodes in x and y (>= 1)                        */
+  double lx, ly;           /* domain size (> 0)                              */
+  int32_t order;           /* ConvFEM order: 2 (quadratic 5x5 filters)       */
+  int32_t n_polar, n_azim; /* direction grid: 8 faces of (n_polar/2)x(n_azim/4) */
+  int32_t n_groups;        /* energy groups G (>= 1)                         */
+  const int32_t* region;   /* host [ny][nx] region id per node               */
+  int32_t n_regions;
+  const double* sigma_t;   /* host [n_regions][G] total cross section        */
+  const double* sigma_s;   /* host [n_regions][G][G] isotropic, [to g][from g'] */
+  const double* source;    /* host [n_regions][G] isotropic source / steradian */
+  int32_t bc[4];           /* xlo, xhi, ylo, yhi: BTMG_VACUUM / BTMG_REFLECTIVE */
+  int32_t pg;              /* 1: nonlinear PG on the finest level; 0: upwind */
+  int32_t nu_jacobi;       /* Jacobi sweeps per level (3), 1..8              */
+  double beta_pg;          /* fine PG Jacobi diagonal factor (3.0)           */
+  int32_t psi_dtype;       /* BTMG_F64 / BTMG_F32 / BTMG_BF16 / BTMG_F16     */
+  int32_t max_levels;      /* 0: coarsen until every dimension is 1          */
+  int32_t pg_half;         /* 1: scale f^{k-Diff} by 1/2 (analytic form)     */
+} btmg_problem_desc;
+
+typedef struct {
+  int32_t cycles;        /* sawtooth cycles performed (all groups)           */
+  int32_t status;        /* BTMG_OK, _NOT_CONVERGED, _DIVERGED or _NAN       */
+  double rel_resid;      /* ||r||_W / ||q||_W of the returned psi (FP64)     */
+  double* history;       /* optional caller host array, per-cycle residual   */
+  int32_t history_len;   /* capacity of history (0 if NULL)                  */
+  int32_t check_every;   /* read the residual back every this many cycles (0 -> 1) */
+  int32_t max_outer;     /* passes over the groups (0: 1 without upscatter, else 8) */
+} btmg_solve_info;
+
+/* Builds the quadrature (Sec. 2.2), the space-angle hierarchy with harmonic
+ * averaged cross sections (Sec. 2.5) and the device workspaces.  Copies every
+ * host array.  Errors: INVALID_ARG (bad sizes, region ids, dtype, order != 2
+ * with pg = 1), OOM, CUDA.  *out is NULL on failure.                        */
+int btmg_create_problem(const btmg_problem_desc* desc, void* stream, btmg_problem** out);
+
+/* Frees every library-owned device buffer.  NULL is accepted.              */
+int btmg_destroy_problem(btmg_problem* p);
+
+/* Total unknowns G * n_dirs * ny * nx of the finest level.                 */
+int btmg_num_unknowns(const btmg_problem* p, int64_t* n);
+
+/* Element strides of psi: [g, face, j, i, y, x].                           */
+int btmg_get_layout(const btmg_problem* p, int64_t strides[6]);
+
+/* Number of levels, and per level: dims = {nx, ny, nr, nc, n_dirs},
+ * dxdy = {dX, dY} (Sec. 2.5).                                              */
+int btmg_num_levels(const btmg_problem* p, int32_t* levels);
+int btmg_level_info(const btmg_problem* p, int32_t level, int32_t dims[5], double dxdy[2]);
+
+/* Directions of a level: mu, nu, p (host double arrays of n_dirs).         */
+int btmg_level_quadrature(const btmg_problem* p, int32_t level, double* mu, double* nu,
+                          double* w);
+
+/* phi_g = sum_n p_n psi_{n,g} (Sec. 2.2).  psi: device [G][nd][ny][nx] of
+ * psi_dtype; phi: device [G][ny][nx] of the compute type.                  */
+int btmg_scalar_flux(btmg_problem* p, const void* psi, void* phi, void* stream);
+
+/* r = b - A psi for every group (Eq. Petrov with the anisotropic nonlinear
+ * PG dissipation of Sec. 2.6, or the upwind operator of Sec. 2.3 if pg = 0),
+ * b = s + sum_g' sigma_s[g<-g'] phi_g' / (4 pi).  psi: device
+ * [G][nd][ny][nx] psi_dtype; r: device, same shape, compute type.          */
+int btmg_apply_operator(btmg_problem* p, const void* psi, void* r, void* stream);
+
+/* Jacobi smoothing (Eq. matrix_full).
+ *  kind = BTMG_SMOOTH_PG: level must be 0 and src NULL; `sweeps` fine PG
+ *    Jacobi sweeps psi <- psi + (beta d)^{-1}(b - A psi) on the full problem
+ *    (groups in order), psi device [G][nd][ny][nx].
+ *  kind = BTMG_SMOOTH_UPWIND: `sweeps` Jacobi sweeps of the upwind system
+ *    A_up,l psi = src of level `level` for group `group` (beta = 1, no
+ *    scattering: the correction equation of the cycle); psi and src are
+ *    device buffers of one group on that level, [nd_l][ny_l][nx_l], both of
+ *    the compute type.                                                     */
+int btmg_smooth(btmg_problem* p, void* psi, const void* src, int32_t level, int32_t group,
+                int32_t sweeps, int32_t kind, void* stream);
+
+/* Restriction level -> level+1 (Sec. 2.5): coarse = sum_children
+ * p dx dy fine / (P dX dY).  Buffers of one group, compute type.           */
+int btmg_restrict(btmg_problem* p, int32_t level, const void* fine, void* coarse, void* stream);
+
+/* UpSamp level+1 -> level (Sec. 2.5): every fine unknown takes its coarse
+ * parent's value.  Buffers of one group, compute type.                     */
+int btmg_prolong(btmg_problem* p, int32_t level, const void* coarse, void* fine, void* stream);
+
+/* One sawtooth cycle (Fig. multi_grid_it) per group, groups in order with
+ * the latest scalar fluxes (block Gauss-Seidel).  psi updated in place.
+ * rel_resid (nullable, host) receives ||r||_W/||q||_W of the INPUT psi
+ * (FP64 reduction); if non-NULL the call synchronises the stream.          */
+int btmg_mg_cycle(btmg_problem* p, void* psi, double* rel_resid, void* stream);
+
+/* Fixed-source solve from the caller's psi: groups in order, each cycled
+ * until its relative residual is below rtol or max_cycles; repeated over
+ * groups while upscatter makes the all-group residual exceed rtol.  Cycles
+ * are replayed from a captured CUDA graph.  Synchronises the stream.
+ * info (nullable) receives cycles, final residual and status; the return
+ * value is BTMG_OK, or BTMG_ERR_NOT_CONVERGED / _DIVERGED (> 1e3 growth) /
+ * _NAN when the iteration failed (psi then holds the last iterate).        */
+int btmg_solve(btmg_problem* p, void* psi, double rtol, int32_t max_cycles,
+               btmg_solve_info* info, void* stream);
+
+/* Instrumentation (no counterpart in the paper; used by the benchmark).
+ * btmg_profile(p, 1) brackets every subsequent kernel launch of the cycle
+ * with two CUDA events on the launching stream; btmg_profile_read()
+ * synchronises on them and returns, per kernel class, the summed device
+ * milliseconds and the number of launches, then clears the record.
+ * Classes: 0 PG residual, 1 PG Jacobi, 2 finest-level upwind Jacobi+update,
+ * 3 coarse upwind Jacobi, 4 restriction, 5 scalar flux / source / sums.
+ * Launches made while capturing the solve graph are not bracketed.
+ * btmg_launch_count() returns the number of kernels this problem has
+ * launched (replays of a captured graph are not counted).                  */
+#define BTMG_PROF_CLASSES 6
+int btmg_profile(btmg_problem* p, int32_t enable);
+int btmg_profile_read(btmg_problem* p, double* ms, int64_t* count, int32_t n_classes);
+int btmg_launch_count(const btmg_problem* p, int64_t* n);
+
+const char* btmg_error_string(int status);
+const char* btmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTMG_H */

@@ -797,6 +797,32 @@ int or_apply(const or_problem* P, const double* psi, double* r) {
   return 0;
 }
 
+/* r = b - A psi for a sample of (group, direction) planes only: out holds
+ * nsel planes [nsel][ny][nx], plane s is (g, n) = (sel[2s], sel[2s+1]).
+ * b still uses the scalar flux of all directions.  Same arithmetic as
+ * or_apply, restricted to the requested planes (large-problem checks).   */
+int or_apply_planes(const or_problem* P, const double* psi, const int32_t* sel, int nsel,
+                    double* out) {
+  const or_level* A = &P->lev[0];
+  const size_t np = (size_t)A->nx * A->ny;
+  double* phi = (double*)malloc(sizeof(double) * np * P->G);
+  double* b = (double*)malloc(sizeof(double) * np * P->G);
+  or_scalar_flux(P, psi, phi);
+  for (int g = 0; g < P->G; ++g) group_rhs(P, g, phi, b + (size_t)g * np);
+#pragma omp parallel for schedule(dynamic)
+  for (int s = 0; s < nsel; ++s) {
+    int g = sel[2 * s], n = sel[2 * s + 1];
+    size_t off = ((size_t)g * A->nd + n) * np;
+    fine_residual_plane(P, g, n, psi + off, b + (size_t)g * np,
+                        P->extra_q ? P->extra_q + off : NULL, out + (size_t)s * np,
+                        P->kx_frozen ? P->kx_frozen + off : NULL,
+                        P->ky_frozen ? P->ky_frozen + off : NULL, NULL, NULL);
+  }
+  free(phi);
+  free(b);
+  return 0;
+}
+
 /* PG coefficients of every plane (for tests and for freezing k). */
 int or_kfields(const or_problem* P, const double* psi, double* kx, double* ky) {
   const or_level* A = &P->lev[0];

@@ -81,6 +81,7 @@ def lib():
         L.or_scalar_flux.argtypes = [C.c_void_p, dp, dp]
         L.or_apply.argtypes = [C.c_void_p, dp, dp]
         L.or_kfields.argtypes = [C.c_void_p, dp, dp, dp]
+        L.or_apply_planes.argtypes = [C.c_void_p, dp, C.POINTER(C.c_int32), C.c_int, dp]
         L.or_upwind_apply.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.or_restrict.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.or_prolong.argtypes = [C.c_void_p, C.c_int, dp, dp]
@@ -231,6 +232,15 @@ class OracleProblem:
         r = np.zeros_like(psi)
         lib().or_apply(self.h, _p(psi), _p(r))
         return r
+
+    def apply_planes(self, psi, planes):
+        """Residual of selected (g, n) planes only; returns [len(planes)][ny][nx]."""
+        psi = _f64(psi)
+        sel = np.ascontiguousarray(np.asarray(planes, dtype=np.int32).reshape(-1))
+        out = np.zeros((len(planes), self.ny, self.nx))
+        lib().or_apply_planes(self.h, _p(psi), sel.ctypes.data_as(C.POINTER(C.c_int32)),
+                              len(planes), _p(out))
+        return out
 
     def kfields(self, psi):
         psi = _f64(psi)

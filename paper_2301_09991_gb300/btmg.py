@@ -1,0 +1,321 @@
+"""Thin Python binding of the btmg C ABI (``include/btmg.h``).
+
+Argument marshalling only: every step of the iteration runs in the CUDA
+kernels of ``libbtmg.so``.  PyTorch provides device memory (caller-owned
+tensors passed by ``data_ptr()``) and streams.  There is no CPU fallback: if
+the library cannot be loaded or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+VACUUM, REFLECTIVE = 0, 1
+SMOOTH_UPWIND, SMOOTH_PG = 0, 1
+
+OK = 0
+ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED = -1, -2, -3, -4
+ERR_DIVERGED, ERR_TIMEOUT, ERR_NAN, ERR_UNSUPPORTED = -5, -6, -7, -8
+
+EXPORTS = (
+    "btmg_create_problem", "btmg_destroy_problem", "btmg_num_unknowns", "btmg_get_layout",
+    "btmg_num_levels", "btmg_level_info", "btmg_level_quadrature", "btmg_scalar_flux",
+    "btmg_apply_operator", "btmg_smooth", "btmg_restrict", "btmg_prolong", "btmg_mg_cycle",
+    "btmg_solve", "btmg_error_string", "btmg_last_error", "btmg_profile", "btmg_profile_read",
+    "btmg_launch_count",
+)
+PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
+
+
+class Desc(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32),
+        ("lx", C.c_double), ("ly", C.c_double),
+        ("order", C.c_int32),
+        ("n_polar", C.c_int32), ("n_azim", C.c_int32),
+        ("n_groups", C.c_int32),
+        ("region", C.POINTER(C.c_int32)),
+        ("n_regions", C.c_int32),
+        ("sigma_t", C.POINTER(C.c_double)),
+        ("sigma_s", C.POINTER(C.c_double)),
+        ("source", C.POINTER(C.c_double)),
+        ("bc", C.c_int32 * 4),
+        ("pg", C.c_int32),
+        ("nu_jacobi", C.c_int32),
+        ("beta_pg", C.c_double),
+        ("psi_dtype", C.c_int32),
+        ("max_levels", C.c_int32),
+        ("pg_half", C.c_int32),
+    ]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [
+        ("cycles", C.c_int32), ("status", C.c_int32), ("rel_resid", C.c_double),
+        ("history", C.POINTER(C.c_double)), ("history_len", C.c_int32),
+        ("check_every", C.c_int32), ("max_outer", C.c_int32),
+    ]
+
+
+class BtmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("btmg error %d (%s): %s" % (code, error_string(code), msg))
+        self.code = code
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libbtmg.so`` (building it in-tree if asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError("libbtmg.so is not built: run __graft_entry__.build()")
+        _build.build()
+    L = C.CDLL(path)
+    vp, i32, i64p = C.c_void_p, C.c_int32, C.POINTER(C.c_int64)
+    dp = C.POINTER(C.c_double)
+    L.btmg_create_problem.argtypes = [C.POINTER(Desc), vp, C.POINTER(vp)]
+    L.btmg_destroy_problem.argtypes = [vp]
+    L.btmg_num_unknowns.argtypes = [vp, i64p]
+    L.btmg_get_layout.argtypes = [vp, i64p]
+    L.btmg_num_levels.argtypes = [vp, C.POINTER(i32)]
+    L.btmg_level_info.argtypes = [vp, i32, C.POINTER(i32), dp]
+    L.btmg_level_quadrature.argtypes = [vp, i32, dp, dp, dp]
+    L.btmg_scalar_flux.argtypes = [vp, vp, vp, vp]
+    L.btmg_apply_operator.argtypes = [vp, vp, vp, vp]
+    L.btmg_smooth.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp]
+    L.btmg_restrict.argtypes = [vp, i32, vp, vp, vp]
+    L.btmg_prolong.argtypes = [vp, i32, vp, vp, vp]
+    L.btmg_mg_cycle.argtypes = [vp, vp, dp, vp]
+    L.btmg_solve.argtypes = [vp, vp, C.c_double, i32, C.POINTER(SolveInfo), vp]
+    L.btmg_profile.argtypes = [vp, i32]
+    L.btmg_profile_read.argtypes = [vp, dp, i64p, i32]
+    L.btmg_launch_count.argtypes = [vp, i64p]
+    L.btmg_error_string.restype = C.c_char_p
+    L.btmg_error_string.argtypes = [C.c_int]
+    L.btmg_last_error.restype = C.c_char_p
+    L.btmg_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def error_string(code):
+    return load().btmg_error_string(int(code)).decode()
+
+
+def _check(rc):
+    if rc != OK:
+        raise BtmgError(rc, load().btmg_last_error().decode())
+    return rc
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dtype_of(code):
+    torch = _torch()
+    return {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}[code]
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """A fixed-source problem resident on the GPU.
+
+    ``prob`` is a dict of plain arrays (see ``inputs.py``): nx, ny, lx, ly,
+    n_polar, n_azim, region [ny][nx], sigma_t [R][G], sigma_s [R][G][G],
+    source [R][G], bc.  ``dtype`` is the storage type of psi.
+    """
+
+    def __init__(self, prob, dtype=F32, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0,
+                 order=None, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("btmg needs a CUDA device (sm_103a); there is no CPU path")
+        L = load()
+        self._region = np.ascontiguousarray(prob["region"], dtype=np.int32)
+        self._st = np.ascontiguousarray(prob["sigma_t"], dtype=np.float64)
+        self._ss = np.ascontiguousarray(prob["sigma_s"], dtype=np.float64)
+        self._src = np.ascontiguousarray(prob["source"], dtype=np.float64)
+        d = Desc()
+        d.nx, d.ny = int(prob["nx"]), int(prob["ny"])
+        d.lx, d.ly = float(prob["lx"]), float(prob["ly"])
+        d.order = int(order if order is not None else prob.get("order", 2))
+        d.n_polar, d.n_azim = int(prob["n_polar"]), int(prob["n_azim"])
+        d.n_groups = int(self._st.shape[1])
+        d.region = self._region.ctypes.data_as(C.POINTER(C.c_int32))
+        d.n_regions = int(self._st.shape[0])
+        dp = C.POINTER(C.c_double)
+        d.sigma_t = self._st.ctypes.data_as(dp)
+        d.sigma_s = self._ss.ctypes.data_as(dp)
+        d.source = self._src.ctypes.data_as(dp)
+        for i, b in enumerate(prob.get("bc", (0, 0, 0, 0))):
+            d.bc[i] = int(b)
+        d.pg, d.nu_jacobi, d.beta_pg = int(pg), int(nu), float(beta_pg)
+        d.psi_dtype, d.max_levels, d.pg_half = int(dtype), int(max_levels), int(pg_half)
+        self.desc = d
+        h = C.c_void_p()
+        _check(L.btmg_create_problem(C.byref(d), _stream_ptr(stream), C.byref(h)))
+        self.h = h
+        self.dtype_code = int(dtype)
+        self.torch_dtype = _dtype_of(dtype)
+        self.compute_dtype = torch.float64 if dtype == F64 else torch.float32
+        self.G = d.n_groups
+        n = C.c_int32()
+        _check(L.btmg_num_levels(self.h, C.byref(n)))
+        self.L = n.value
+        self.levels = [self.level_info(l) for l in range(self.L)]
+        self.nd = self.levels[0]["nd"]
+        self.shape = (self.G, self.nd, d.ny, d.nx)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().btmg_destroy_problem(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- queries -------------------------------------------------------------
+    def num_unknowns(self):
+        n = C.c_int64()
+        _check(load().btmg_num_unknowns(self.h, C.byref(n)))
+        return n.value
+
+    def layout(self):
+        s = (C.c_int64 * 6)()
+        _check(load().btmg_get_layout(self.h, s))
+        return tuple(s)
+
+    def level_info(self, l):
+        dims = (C.c_int32 * 5)()
+        dxdy = (C.c_double * 2)()
+        _check(load().btmg_level_info(self.h, l, dims, dxdy))
+        nd = dims[4]
+        mu, nu, w = np.zeros(nd), np.zeros(nd), np.zeros(nd)
+        dp = C.POINTER(C.c_double)
+        _check(load().btmg_level_quadrature(self.h, l, mu.ctypes.data_as(dp), nu.ctypes.data_as(dp),
+                                            w.ctypes.data_as(dp)))
+        return dict(nx=dims[0], ny=dims[1], nr=dims[2], nc=dims[3], nd=nd, dx=dxdy[0], dy=dxdy[1],
+                    mu=mu, nu=nu, p=w)
+
+    def level_shape(self, l):
+        lv = self.levels[l]
+        return (lv["nd"], lv["ny"], lv["nx"])
+
+    def profile(self, enable=True):
+        _check(load().btmg_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        n = len(PROF_CLASSES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        _check(load().btmg_profile_read(self.h, ms, cnt, n))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(PROF_CLASSES)}
+
+    def launch_count(self):
+        n = C.c_int64()
+        _check(load().btmg_launch_count(self.h, C.byref(n)))
+        return n.value
+
+    # -- buffers -------------------------------------------------------------
+    def zeros(self):
+        return _torch().zeros(self.shape, dtype=self.torch_dtype, device="cuda")
+
+    def _check_psi(self, psi):
+        torch = _torch()
+        if not (psi.is_cuda and psi.dtype == self.torch_dtype and psi.is_contiguous()
+                and tuple(psi.shape) == self.shape):
+            raise ValueError("psi must be a contiguous CUDA tensor %s of %s" % (self.shape, self.torch_dtype))
+
+    # -- operations (names follow the C ABI) ---------------------------------
+    def scalar_flux(self, psi, stream=None):
+        self._check_psi(psi)
+        phi = _torch().empty((self.G, self.shape[2], self.shape[3]), dtype=self.compute_dtype, device="cuda")
+        _check(load().btmg_scalar_flux(self.h, _ptr(psi), _ptr(phi), _stream_ptr(stream)))
+        return phi
+
+    def apply_operator(self, psi, r=None, stream=None):
+        self._check_psi(psi)
+        if r is None:
+            r = _torch().empty(self.shape, dtype=self.compute_dtype, device="cuda")
+        _check(load().btmg_apply_operator(self.h, _ptr(psi), _ptr(r), _stream_ptr(stream)))
+        return r
+
+    def smooth_pg(self, psi, sweeps=1, stream=None):
+        self._check_psi(psi)
+        _check(load().btmg_smooth(self.h, _ptr(psi), None, 0, 0, sweeps, SMOOTH_PG, _stream_ptr(stream)))
+        return psi
+
+    def smooth_upwind(self, delta, src, level, group=0, sweeps=3, stream=None):
+        shp = self.level_shape(level)
+        for t in (delta, src):
+            if tuple(t.shape) != shp or t.dtype != self.compute_dtype or not t.is_cuda:
+                raise ValueError("level %d buffers must be %s %s" % (level, shp, self.compute_dtype))
+        _check(load().btmg_smooth(self.h, _ptr(delta), _ptr(src), level, group, sweeps, SMOOTH_UPWIND,
+                                  _stream_ptr(stream)))
+        return delta
+
+    def restrict(self, level, fine, stream=None):
+        coarse = _torch().empty(self.level_shape(level + 1), dtype=self.compute_dtype, device="cuda")
+        _check(load().btmg_restrict(self.h, level, _ptr(fine), _ptr(coarse), _stream_ptr(stream)))
+        return coarse
+
+    def prolong(self, level, coarse, stream=None):
+        fine = _torch().empty(self.level_shape(level), dtype=self.compute_dtype, device="cuda")
+        _check(load().btmg_prolong(self.h, level, _ptr(coarse), _ptr(fine), _stream_ptr(stream)))
+        return fine
+
+    def mg_cycle(self, psi, want_residual=True, stream=None):
+        self._check_psi(psi)
+        rel = C.c_double(0.0)
+        _check(load().btmg_mg_cycle(self.h, _ptr(psi), C.byref(rel) if want_residual else None,
+                                    _stream_ptr(stream)))
+        return rel.value if want_residual else None
+
+    def solve(self, psi, rtol=1e-6, max_cycles=1000, check_every=1, max_outer=0, history=True,
+              stream=None, raise_on_fail=False):
+        self._check_psi(psi)
+        info = SolveInfo()
+        hist = np.zeros(max_cycles * self.G * max(1, max_outer or 8)) if history else None
+        if hist is not None:
+            info.history = hist.ctypes.data_as(C.POINTER(C.c_double))
+            info.history_len = hist.size
+        info.check_every = int(check_every)
+        info.max_outer = int(max_outer)
+        rc = load().btmg_solve(self.h, _ptr(psi), float(rtol), int(max_cycles), C.byref(info),
+                               _stream_ptr(stream))
+        if rc not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_NAN) or (raise_on_fail and rc != OK):
+            _check(rc)
+        out = dict(status=rc, cycles=info.cycles, rel_resid=info.rel_resid)
+        if hist is not None:
+            out["history"] = hist[:min(info.cycles, hist.size)].copy()
+        return out

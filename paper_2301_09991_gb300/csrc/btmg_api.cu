@@ -1,0 +1,946 @@
+// btmg_api.cu -- host side of the btmg C ABI: problem set-up (octahedral
+// quadrature of Sec. 2.2, space-angle hierarchy of Sec. 2.5), device
+// workspaces, the sawtooth cycle sequencing of Fig. multi_grid_it and the
+// CUDA-graph solve loop.  Every arithmetic step of the iteration runs in the
+// kernels of k_pg.cu and k_mg.cu; the host only launches them.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/btmg.h"
+#include "btmg_common.cuh"
+
+using namespace btmg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(...)                                                                                       \
+  do {                                                                                                \
+    cudaError_t e_ = (__VA_ARGS__);                                                                   \
+    if (e_ != cudaSuccess)                                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? BTMG_ERR_OOM : BTMG_ERR_CUDA,                     \
+                  std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kTile = 32;  // tile edge of the PG and upwind kernels
+
+// ------------------------------------------------- quadrature (Sec. 2.2) --
+// Gauss-Legendre on [0,1]: Newton iteration on the three-term recurrence.
+void gauss_legendre_unit(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double t = std::cos(kPi * (4.0 * k + 3.0) / (4.0 * n + 2.0));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double pm = 0.0, p = 1.0;
+      for (int m = 1; m <= n; ++m) {
+        const double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm) / m;
+        pm = p;
+        p = pn;
+      }
+      dp = n * (pm - t * p) / (1.0 - t * t);
+      const double step = p / dp;
+      t -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    x[k] = 0.5 * (1.0 + t);
+    w[k] = 1.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+// Directions of the 8 octahedron faces, each with an nr x nc grid mapped by
+// X(u,t) = (1-t)((1-u) a + u b) + t c (corners a, b, c on the axes, the edge
+// t = 1 collapsed onto c) and projected radially onto the unit sphere.  The
+// solid angle element of the projection is (X . (X_u x X_t)) / |X|^3 du dt
+// = (1-t) / |X|^3 du dt; p_n is its integral over the patch, (mu_n, nu_n)
+// the patch-mean direction.  Weights are scaled so that sum p = 4 pi.
+void octahedral_quadrature(int nr, int nc, std::vector<double>& mu, std::vector<double>& nu,
+                           std::vector<double>& p) {
+  const int nd = 8 * nr * nc, ng = 16;
+  std::vector<double> gx, gw;
+  gauss_legendre_unit(ng, gx, gw);
+  mu.assign(nd, 0.0);
+  nu.assign(nd, 0.0);
+  p.assign(nd, 0.0);
+  double total = 0.0;
+  for (int f = 0; f < 8; ++f) {
+    const double sx = (f & 1) ? -1 : 1, sy = (f & 2) ? -1 : 1, sz = (f & 4) ? -1 : 1;
+    for (int j = 0; j < nr; ++j)
+      for (int i = 0; i < nc; ++i) {
+        double area = 0, mx = 0, my = 0;
+        for (int a = 0; a < ng; ++a)
+          for (int b = 0; b < ng; ++b) {
+            const double t = (j + gx[a]) / nr, u = (i + gx[b]) / nc;
+            const double X0 = (1 - t) * (1 - u) * sx, X1 = (1 - t) * u * sy, X2 = t * sz;
+            const double r2 = X0 * X0 + X1 * X1 + X2 * X2, r = std::sqrt(r2);
+            const double dS = gw[a] * gw[b] / (double(nr) * nc) * (1 - t) / (r2 * r);
+            area += dS;
+            mx += dS * X0 / r;
+            my += dS * X1 / r;
+          }
+        const int n = f * nr * nc + j * nc + i;
+        p[n] = area;
+        mu[n] = mx / area;
+        nu[n] = my / area;
+        total += area;
+      }
+  }
+  for (int n = 0; n < nd; ++n) p[n] *= 4.0 * kPi / total;
+}
+
+struct LevelH {
+  int nx, ny, nr, nc, nd;
+  double dx, dy;
+  std::vector<double> mu, nu, p;
+  std::vector<double> sig;  // [G][ny][nx]
+  int fx = 1, fy = 1, fr = 1, fc = 1;  // factors to the next coarser level
+  size_t npix() const { return (size_t)nx * ny; }
+  size_t n() const { return (size_t)nd * nx * ny; }
+};
+
+size_t dtype_size(int t) { return t == BTMG_F64 ? 8 : t == BTMG_F32 ? 4 : 2; }
+
+}  // namespace
+
+struct btmg_problem {
+  btmg_problem_desc d{};
+  int G = 0, L = 0, dtype = BTMG_F32;
+  bool f64 = false;
+  size_t csize = 4;  // compute element size
+  std::vector<LevelH> lev;
+  int dpc = 1, nchunk = 1, tiles_x = 1, tiles_y = 1;
+  bool upscatter = false;
+  // device buffers (compute type unless noted)
+  std::vector<void*> d_dir, d_rcoef, d_sig, d_s, d_delta;
+  void* d_sigs = nullptr;      // [G][G][npix]
+  void* d_src = nullptr;       // [G][npix]
+  void* d_b = nullptr;         // [npix]
+  void* d_phi_part = nullptr;  // [G][nchunk][npix]
+  void* d_psi_tmp = nullptr;   // storage type, one group
+  double* d_norm_part = nullptr;
+  int n_norm_part = 0;
+  double* d_qn2_part = nullptr;
+  int n_q_blocks = 0;
+  double* d_rn2 = nullptr;  // [G]
+  double* d_qn2 = nullptr;  // [G]
+  double* h_pinned = nullptr;  // [2G]
+  // captured cycle graphs per group
+  std::vector<cudaGraphExec_t> graphs;
+  const void* graph_psi = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  // graphs cannot be captured on the legacy default stream: solve() runs on
+  // this stream when the caller passes NULL, ordered after the caller's work
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t order_event = nullptr;
+  // per-kernel-class CUDA-event timing (btmg_profile) and launch counting
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<int> prof_cls;
+  int64_t launches = 0;
+};
+
+namespace {
+
+template <typename C> C* dptr(void* p) { return reinterpret_cast<C*>(p); }
+
+void free_graphs(btmg_problem* P) {
+  for (auto& g : P->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  P->graphs.assign(P->G, nullptr);
+  P->graph_psi = nullptr;
+}
+
+// --------------------------------------------------------------- launches --
+// Kernel classes reported by btmg_profile_read (BTMG_PROF_*).
+enum { PC_PG_RESID = 0, PC_PG_JACOBI = 1, PC_UP_FINE = 2, PC_UP_COARSE = 3, PC_RESTRICT = 4, PC_MISC = 5, PC_N = 6 };
+
+// Launches f() on stream s; counts the launch and, when profiling, brackets
+// it with two CUDA events recorded on the same stream.
+template <class F> cudaError_t timed(btmg_problem* P, int cls, cudaStream_t s, F&& f) {
+  ++P->launches;
+  if (!P->prof_on) return f();
+  const size_t k = 2 * P->prof_cls.size();
+  while (P->prof_pool.size() < k + 2) {
+    cudaEvent_t e;
+    cudaError_t ec = cudaEventCreate(&e);
+    if (ec != cudaSuccess) return ec;
+    P->prof_pool.push_back(e);
+  }
+  cudaError_t e0 = cudaEventRecord(P->prof_pool[k], s);
+  if (e0 != cudaSuccess) return e0;
+  cudaError_t e = f();
+  if (e != cudaSuccess) return e;
+  P->prof_cls.push_back(cls);
+  return cudaEventRecord(P->prof_pool[k + 1], s);
+}
+
+template <typename T, typename C> struct Impl {
+  static PgArgs<T, C> pg_args(btmg_problem* P, int g, const T* psi) {
+    const LevelH& L0 = P->lev[0];
+    PgArgs<T, C> a{};
+    a.psi = psi;
+    a.b = dptr<C>(P->d_b);
+    a.sigt = dptr<C>(P->d_sig[0]) + (size_t)g * L0.npix();
+    a.dir = reinterpret_cast<const Dir<C>*>(P->d_dir[0]);
+    a.nx = L0.nx;
+    a.ny = L0.ny;
+    a.nd = L0.nd;
+    a.dpc = P->dpc;
+    a.tiles_x = P->tiles_x;
+    a.dx = (C)L0.dx;
+    a.dy = (C)L0.dy;
+    a.inv_dx = (C)(1.0 / L0.dx);
+    a.inv_dy = (C)(1.0 / L0.dy);
+    a.inv_dx2 = (C)(1.0 / (L0.dx * L0.dx));
+    a.inv_dy2 = (C)(1.0 / (L0.dy * L0.dy));
+    a.dxdy = (C)(L0.dx * L0.dy);
+    // Sec. 2.6 constants for order p = 2: eps_k = 1e-3, alpha_kabs = 2^p/16,
+    // alpha_ksquare = 2^p/2; alpha_r = beta_r = 3.
+    a.eps_k = (C)1e-3;
+    a.a_kabs = (C)0.25;
+    a.a_ksq = (C)2.0;
+    a.a_r = (C)3.0;
+    a.half = (C)(P->d.pg_half ? 0.5 : 1.0);
+    a.beta = (C)(P->d.pg ? P->d.beta_pg : 1.0);
+    a.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
+    return a;
+  }
+
+  // b for group g from the scalar-flux partials of every group.
+  static cudaError_t source(btmg_problem* P, int g, cudaStream_t s) {
+    const size_t npix = P->lev[0].npix();
+    cudaError_t e = timed(P, PC_MISC, s, [&] {
+      return launch_source<C>(dptr<C>(P->d_src) + g * npix, dptr<C>(P->d_sigs) + (size_t)g * P->G * npix,
+                              dptr<C>(P->d_phi_part), P->G, g, P->nchunk, (int)npix, dptr<C>(P->d_b), nullptr,
+                              P->d_qn2_part, P->n_q_blocks, s);
+    });
+    if (e != cudaSuccess) return e;
+    return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_qn2_part, P->n_q_blocks, P->d_qn2 + g, s); });
+  }
+
+  static cudaError_t phi_partials(btmg_problem* P, const T* psi, cudaStream_t s) {
+    const LevelH& L0 = P->lev[0];
+    for (int g = 0; g < P->G; ++g) {
+      cudaError_t e = timed(P, PC_MISC, s, [&] {
+        return launch_phi_partial<T, C>(psi + (size_t)g * L0.n(),
+                                        dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix(),
+                                        reinterpret_cast<const Dir<C>*>(P->d_dir[0]), L0.nx, L0.ny, L0.nd, P->dpc,
+                                        P->nchunk, s);
+      });
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  static UpArgs<T, C> up_args(btmg_problem* P, int l, int g) {
+    const LevelH& A = P->lev[l];
+    UpArgs<T, C> u{};
+    u.sig = dptr<C>(P->d_sig[l]) + (size_t)g * A.npix();
+    u.dir = reinterpret_cast<const Dir<C>*>(P->d_dir[l]);
+    u.nx = A.nx;
+    u.ny = A.ny;
+    u.nr = A.nr;
+    u.nc = A.nc;
+    u.nd = A.nd;
+    u.nu = P->d.nu_jacobi;
+    u.src_stride = A.npix();
+    u.tiles_x = (A.nx + kTile - 1) / kTile;
+    u.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
+    u.dpc = 1;
+    if (l + 1 < P->L) {
+      const LevelH& B = P->lev[l + 1];
+      u.nxc = B.nx;
+      u.nyc = B.ny;
+      u.nrc = B.nr;
+      u.ncc = B.nc;
+      u.fx = A.fx;
+      u.fy = A.fy;
+      u.fr = A.fr;
+      u.fc = A.fc;
+    }
+    return u;
+  }
+
+  // One sawtooth cycle of group g (Fig. multi_grid_it); the scalar-flux
+  // partials of every group must describe the current psi on entry and
+  // describe the updated psi on exit.
+  static cudaError_t cycle_group(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
+    cudaError_t e;
+    const int L = P->L;
+    const LevelH& L0 = P->lev[0];
+    // 1. r_1 = b - A psi  (Eq. Petrov), weighted norm
+    if ((e = source(P, g, s)) != cudaSuccess) return e;
+    PgArgs<T, C> a = pg_args(P, g, psi_g);
+    a.r_out = dptr<C>(P->d_s[0]);
+    a.norm_part = P->d_norm_part;
+    if ((e = timed(P, PC_PG_RESID, s, [&] { return launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s); })) !=
+        cudaSuccess)
+      return e;
+    const int nblk = P->tiles_x * P->tiles_y * P->nchunk;
+    if ((e = timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, nblk, P->d_rn2 + g, s); })) != cudaSuccess)
+      return e;
+    // 2. restriction to every coarser level
+    for (int l = 0; l + 1 < L; ++l) {
+      const LevelH &A = P->lev[l], &B = P->lev[l + 1];
+      if ((e = timed(P, PC_RESTRICT, s, [&] {
+             return launch_restrict<C>(dptr<C>(P->d_s[l]), dptr<C>(P->d_s[l + 1]), dptr<C>(P->d_rcoef[l]), A.nx,
+                                       A.ny, A.nr, A.nc, B.nx, B.ny, B.nr, B.nc, A.fx, A.fy, A.fr, A.fc, s);
+           })) != cudaSuccess)
+        return e;
+    }
+    // 3./4. upwind Jacobi from the coarsest level up, UpSamp in between
+    for (int l = L - 1; l >= 1; --l) {
+      UpArgs<T, C> u = up_args(P, l, g);
+      u.src = dptr<C>(P->d_s[l]);
+      u.init_mode = (l == L - 1) ? INIT_ZERO : INIT_UPSAMPLE;
+      u.init = (l == L - 1) ? nullptr : dptr<C>(P->d_delta[l + 1]);
+      u.delta_out = dptr<C>(P->d_delta[l]);
+      if ((e = timed(P, PC_UP_COARSE, s, [&] { return launch_upwind<T, C>(u, UP_CORR, P->lev[l].nd, s); })) !=
+          cudaSuccess)
+        return e;
+    }
+    // 4./5. finest level: nu sweeps from UpSamp(delta_2), psi_tmp = psi + delta
+    {
+      UpArgs<T, C> u = up_args(P, 0, g);
+      u.src = dptr<C>(P->d_s[0]);
+      u.init_mode = (L > 1) ? INIT_UPSAMPLE : INIT_ZERO;
+      u.init = (L > 1) ? dptr<C>(P->d_delta[1]) : nullptr;
+      u.psi_in = psi_g;
+      u.psi_out = dptr<T>(P->d_psi_tmp);
+      u.phi_part = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
+      u.dpc = P->dpc;
+      if ((e = timed(P, PC_UP_FINE, s, [&] { return launch_upwind<T, C>(u, UP_UPDATE, P->nchunk, s); })) !=
+          cudaSuccess)
+        return e;
+    }
+    // 6. fine PG Jacobi sweep with diagonal beta d (Eq. matrix_full)
+    if ((e = source(P, g, s)) != cudaSuccess) return e;
+    PgArgs<T, C> j = pg_args(P, g, dptr<T>(P->d_psi_tmp));
+    j.psi_out = psi_g;
+    j.phi_part = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
+    return timed(P, PC_PG_JACOBI, s, [&] { return launch_pg<T, C>(j, PG_JACOBI, P->d.pg != 0, P->nchunk, s); });
+  }
+
+  static int mg_cycle(btmg_problem* P, void* psi, double* rel, cudaStream_t s) {
+    T* ps = reinterpret_cast<T*>(psi);
+    CK(phi_partials(P, ps, s));
+    for (int g = 0; g < P->G; ++g) CK(cycle_group(P, ps + (size_t)g * P->lev[0].n(), g, s));
+    if (rel) {
+      CK(cudaMemcpyAsync(P->h_pinned, P->d_rn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(P->h_pinned + P->G, P->d_qn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      double sr = 0, sq = 0;
+      for (int g = 0; g < P->G; ++g) {
+        sr += P->h_pinned[g];
+        sq += P->h_pinned[P->G + g];
+      }
+      *rel = sq > 0 ? std::sqrt(sr / (4.0 * kPi * P->lev[0].dx * P->lev[0].dy * sq)) : std::sqrt(sr);
+    }
+    return BTMG_OK;
+  }
+
+  // residual of every group of psi; norms into d_rn2/d_qn2, r to r_out if non-null
+  static cudaError_t residual_all(btmg_problem* P, const T* psi, C* r_out, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = phi_partials(P, psi, s)) != cudaSuccess) return e;
+    const LevelH& L0 = P->lev[0];
+    for (int g = 0; g < P->G; ++g) {
+      if ((e = source(P, g, s)) != cudaSuccess) return e;
+      PgArgs<T, C> a = pg_args(P, g, psi + (size_t)g * L0.n());
+      a.r_out = r_out ? r_out + (size_t)g * L0.n() : dptr<C>(P->d_s[0]);
+      a.norm_part = P->d_norm_part;
+      if ((e = launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s)) != cudaSuccess) return e;
+      if ((e = launch_sum(P->d_norm_part, P->tiles_x * P->tiles_y * P->nchunk, P->d_rn2 + g, s)) != cudaSuccess)
+        return e;
+    }
+    return cudaSuccess;
+  }
+
+  static int read_rel(btmg_problem* P, cudaStream_t s, int g, double* rel_g, double* rel_all) {
+    CK(cudaMemcpyAsync(P->h_pinned, P->d_rn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(P->h_pinned + P->G, P->d_qn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double w = 4.0 * kPi * P->lev[0].dx * P->lev[0].dy;
+    if (rel_g) {
+      const double rn = P->h_pinned[g], qn = P->h_pinned[P->G + g];
+      *rel_g = qn > 0 ? std::sqrt(rn / (w * qn)) : std::sqrt(rn);
+    }
+    if (rel_all) {
+      double sr = 0, sq = 0;
+      for (int h = 0; h < P->G; ++h) {
+        sr += P->h_pinned[h];
+        sq += P->h_pinned[P->G + h];
+      }
+      *rel_all = sq > 0 ? std::sqrt(sr / (w * sq)) : std::sqrt(sr);
+    }
+    return BTMG_OK;
+  }
+
+  static int solve(btmg_problem* P, void* psi, double rtol, int max_cycles, btmg_solve_info* info, cudaStream_t s) {
+    if (!s) {
+      CK(cudaEventRecord(P->order_event, s));
+      CK(cudaStreamWaitEvent(P->own_stream, P->order_event, 0));
+      s = P->own_stream;
+    }
+    T* ps = reinterpret_cast<T*>(psi);
+    const int check = (info && info->check_every > 0) ? info->check_every : 1;
+    if (P->graph_psi != psi || P->graph_stream != s) free_graphs(P);
+    int cycles = 0, status = BTMG_OK;
+    CK(phi_partials(P, ps, s));
+    int max_outer = (info && info->max_outer > 0) ? info->max_outer : (P->upscatter ? 8 : 1);
+    if (P->G == 1) max_outer = 1;
+    double rel_all = 0.0;
+    for (int outer = 0; outer < max_outer; ++outer) {
+      for (int g = 0; g < P->G; ++g) {
+        T* pg = ps + (size_t)g * P->lev[0].n();
+        double best = 1e300;
+        for (int c = 0; c < max_cycles; ++c) {
+          if (!P->graphs[g]) {
+            if (c == 0) {
+              CK(cycle_group(P, pg, g, s));  // eager first cycle (sets kernel attributes)
+            } else {
+              cudaGraph_t graph;
+              CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+              cudaError_t ec = cycle_group(P, pg, g, s);
+              cudaError_t ee = cudaStreamEndCapture(s, &graph);
+              CK(ec);
+              CK(ee);
+              cudaError_t ei = cudaGraphInstantiate(&P->graphs[g], graph, 0);
+              cudaGraphDestroy(graph);
+              CK(ei);
+              P->graph_psi = psi;
+              P->graph_stream = s;
+              CK(cudaGraphLaunch(P->graphs[g], s));
+            }
+          } else {
+            CK(cudaGraphLaunch(P->graphs[g], s));
+          }
+          ++cycles;
+          if ((c + 1) % check == 0 || c + 1 == max_cycles) {
+            double rel;
+            int rc = read_rel(P, s, g, &rel, nullptr);
+            if (rc) return rc;
+            if (info && info->history && cycles - 1 < info->history_len) info->history[cycles - 1] = rel;
+            if (std::isnan(rel)) {
+              status = BTMG_ERR_NAN;
+              break;
+            }
+            if (rel > 1e3 * best && best < 1e299) {
+              status = BTMG_ERR_DIVERGED;
+              break;
+            }
+            if (rel < best) best = rel;
+            if (rel <= rtol) break;
+          }
+        }
+        if (status != BTMG_OK) break;
+      }
+      if (status != BTMG_OK) break;
+      CK(residual_all(P, ps, nullptr, s));
+      int rc = read_rel(P, s, 0, nullptr, &rel_all);
+      if (rc) return rc;
+      if (rel_all <= rtol || outer + 1 == max_outer) break;
+      CK(phi_partials(P, ps, s));
+    }
+    if (status == BTMG_OK && !(rel_all <= rtol)) status = std::isnan(rel_all) ? BTMG_ERR_NAN : BTMG_ERR_NOT_CONVERGED;
+    if (info) {
+      info->cycles = cycles;
+      info->rel_resid = rel_all;
+      info->status = status;
+    }
+    return status;
+  }
+};
+
+template <template <typename, typename> class F, typename... Args>
+int dispatch(int dtype, Args&&... args) {
+  switch (dtype) {
+    case BTMG_F64: return F<double, double>::run(args...);
+    case BTMG_F32: return F<float, float>::run(args...);
+    case BTMG_BF16: return F<__nv_bfloat16, float>::run(args...);
+    case BTMG_F16: return F<__half, float>::run(args...);
+  }
+  return fail(BTMG_ERR_INVALID_ARG, "unknown dtype");
+}
+
+template <typename T, typename C> struct RunCycle {
+  static int run(btmg_problem* P, void* psi, double* rel, cudaStream_t s) { return Impl<T, C>::mg_cycle(P, psi, rel, s); }
+};
+template <typename T, typename C> struct RunSolve {
+  static int run(btmg_problem* P, void* psi, double rtol, int mc, btmg_solve_info* info, cudaStream_t s) {
+    return Impl<T, C>::solve(P, psi, rtol, mc, info, s);
+  }
+};
+template <typename T, typename C> struct RunApply {
+  static int run(btmg_problem* P, const void* psi, void* r, cudaStream_t s) {
+    CK(Impl<T, C>::residual_all(P, reinterpret_cast<const T*>(psi), reinterpret_cast<C*>(r), s));
+    return BTMG_OK;
+  }
+};
+template <typename T, typename C> struct RunFlux {
+  static int run(btmg_problem* P, const void* psi, void* phi, cudaStream_t s) {
+    CK(Impl<T, C>::phi_partials(P, reinterpret_cast<const T*>(psi), s));
+    const size_t npix = P->lev[0].npix();
+    for (int g = 0; g < P->G; ++g)
+      CK(launch_phi_sum<C>(dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * npix, P->nchunk, (int)npix,
+                           reinterpret_cast<C*>(phi) + g * npix, s));
+    return BTMG_OK;
+  }
+};
+template <typename T, typename C> struct RunSmoothPG {
+  static int run(btmg_problem* P, void* psi, int sweeps, cudaStream_t s) {
+    T* ps = reinterpret_cast<T*>(psi);
+    const LevelH& L0 = P->lev[0];
+    CK(Impl<T, C>::phi_partials(P, ps, s));
+    for (int k = 0; k < sweeps; ++k)
+      for (int g = 0; g < P->G; ++g) {
+        CK(Impl<T, C>::source(P, g, s));
+        PgArgs<T, C> j = Impl<T, C>::pg_args(P, g, ps + (size_t)g * L0.n());
+        j.psi_out = dptr<T>(P->d_psi_tmp);
+        j.phi_part = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
+        CK(launch_pg<T, C>(j, PG_JACOBI, P->d.pg != 0, P->nchunk, s));
+        CK(cudaMemcpyAsync(ps + (size_t)g * L0.n(), P->d_psi_tmp, L0.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      }
+    return BTMG_OK;
+  }
+};
+template <typename T, typename C> struct RunSmoothUp {
+  static int run(btmg_problem* P, void* psi, const void* src, int l, int g, int sweeps, cudaStream_t s) {
+    const LevelH& A = P->lev[l];
+    if (!P->d_delta[l]) CK(cudaMalloc(&P->d_delta[l], A.n() * sizeof(C)));
+    int left = sweeps;
+    while (left > 0) {
+      const int k = left > 8 ? 8 : left;
+      UpArgs<T, C> u = Impl<T, C>::up_args(P, l, g);
+      u.nu = k;
+      u.src = reinterpret_cast<const C*>(src);
+      u.init_mode = INIT_SAME;
+      u.init = reinterpret_cast<const C*>(psi);
+      u.delta_out = dptr<C>(P->d_delta[l]);
+      CK(launch_upwind<T, C>(u, UP_CORR, A.nd, s));
+      CK(cudaMemcpyAsync(psi, P->d_delta[l], A.n() * sizeof(C), cudaMemcpyDeviceToDevice, s));
+      left -= k;
+    }
+    return BTMG_OK;
+  }
+};
+
+void destroy(btmg_problem* P) {
+  if (!P) return;
+  free_graphs(P);
+  for (cudaEvent_t e : P->prof_pool) cudaEventDestroy(e);
+  for (auto v : {&P->d_dir, &P->d_rcoef, &P->d_sig, &P->d_s, &P->d_delta})
+    for (void* p : *v)
+      if (p) cudaFree(p);
+  for (void* p : {P->d_sigs, P->d_src, P->d_b, P->d_phi_part, P->d_psi_tmp, (void*)P->d_norm_part,
+                  (void*)P->d_qn2_part, (void*)P->d_rn2, (void*)P->d_qn2})
+    if (p) cudaFree(p);
+  if (P->h_pinned) cudaFreeHost(P->h_pinned);
+  if (P->own_stream) cudaStreamDestroy(P->own_stream);
+  if (P->order_event) cudaEventDestroy(P->order_event);
+  delete P;
+}
+
+template <typename C> void put_dirs(std::vector<char>& buf, const LevelH& A) {
+  buf.resize(sizeof(Dir<C>) * A.nd);
+  Dir<C>* d = reinterpret_cast<Dir<C>*>(buf.data());
+  for (int n = 0; n < A.nd; ++n) {
+    d[n].mu = (C)A.mu[n];
+    d[n].nu = (C)A.nu[n];
+    d[n].w = (C)A.p[n];
+    d[n].ax = (C)(std::fabs(A.mu[n]) / A.dx);
+    d[n].ay = (C)(std::fabs(A.nu[n]) / A.dy);
+  }
+}
+
+template <typename C> void put_vals(std::vector<char>& buf, const std::vector<double>& v) {
+  buf.resize(sizeof(C) * v.size());
+  C* d = reinterpret_cast<C*>(buf.data());
+  for (size_t i = 0; i < v.size(); ++i) d[i] = (C)v[i];
+}
+
+int upload(void** dst, const std::vector<char>& buf) {
+  CK(cudaMalloc(dst, buf.size() ? buf.size() : 8));
+  if (buf.size()) CK(cudaMemcpy(*dst, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  return BTMG_OK;
+}
+
+int create(const btmg_problem_desc* d, btmg_problem** out) {
+  if (!d || !out) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (d->nx < 1 || d->ny < 1 || d->nx > 65536 || d->ny > 65536 || !(d->lx > 0) || !(d->ly > 0))
+    return fail(BTMG_ERR_INVALID_ARG, "bad grid size");
+  if (d->n_polar < 2 || d->n_polar % 2 || d->n_azim < 4 || d->n_azim % 4)
+    return fail(BTMG_ERR_INVALID_ARG, "n_polar must be even and n_azim a multiple of 4");
+  if (d->n_groups < 1 || d->n_regions < 1 || !d->region || !d->sigma_t || !d->sigma_s || !d->source)
+    return fail(BTMG_ERR_INVALID_ARG, "bad material description");
+  if (d->psi_dtype < BTMG_F64 || d->psi_dtype > BTMG_F16) return fail(BTMG_ERR_INVALID_ARG, "bad psi_dtype");
+  if (d->nu_jacobi < 1 || d->nu_jacobi > 8) return fail(BTMG_ERR_INVALID_ARG, "nu_jacobi must be in 1..8");
+  if (d->pg && d->order != 2) return fail(BTMG_ERR_UNSUPPORTED, "the GPU PG operator implements order 2");
+  for (int i = 0; i < 4; ++i)
+    if (d->bc[i] != BTMG_VACUUM && d->bc[i] != BTMG_REFLECTIVE) return fail(BTMG_ERR_INVALID_ARG, "bad bc");
+  const int G = d->n_groups, nx = d->nx, ny = d->ny;
+  const size_t npix = (size_t)nx * ny;
+  for (size_t i = 0; i < npix; ++i)
+    if (d->region[i] < 0 || d->region[i] >= d->n_regions) return fail(BTMG_ERR_INVALID_ARG, "region id out of range");
+
+  btmg_problem* P = new btmg_problem();
+  P->d = *d;
+  P->d.region = nullptr;
+  P->d.sigma_t = P->d.sigma_s = P->d.source = nullptr;
+  if (!(P->d.beta_pg > 0)) P->d.beta_pg = 3.0;
+  P->G = G;
+  P->dtype = d->psi_dtype;
+  P->f64 = d->psi_dtype == BTMG_F64;
+  P->csize = P->f64 ? 8 : 4;
+
+  // finest level
+  LevelH L0;
+  L0.nx = nx;
+  L0.ny = ny;
+  L0.nr = d->n_polar / 2;
+  L0.nc = d->n_azim / 4;
+  L0.nd = 8 * L0.nr * L0.nc;
+  L0.dx = d->lx / nx;
+  L0.dy = d->ly / ny;
+  octahedral_quadrature(L0.nr, L0.nc, L0.mu, L0.nu, L0.p);
+  L0.sig.resize((size_t)G * npix);
+  std::vector<double> sigs((size_t)G * G * npix), src((size_t)G * npix);
+  for (size_t i = 0; i < npix; ++i) {
+    const int rg = d->region[i];
+    for (int g = 0; g < G; ++g) {
+      L0.sig[(size_t)g * npix + i] = d->sigma_t[rg * G + g];
+      src[(size_t)g * npix + i] = d->source[rg * G + g];
+      for (int h = 0; h < G; ++h) sigs[((size_t)g * G + h) * npix + i] = d->sigma_s[((size_t)rg * G + g) * G + h];
+    }
+  }
+  P->lev.push_back(L0);
+  // coarser levels: each of nx, ny, nr, nc halves (ceil) until 1
+  while (true) {
+    LevelH& A = P->lev.back();
+    if (d->max_levels > 0 && (int)P->lev.size() >= d->max_levels) break;
+    if (A.nx == 1 && A.ny == 1 && A.nr == 1 && A.nc == 1) break;
+    A.fx = A.nx > 1 ? 2 : 1;
+    A.fy = A.ny > 1 ? 2 : 1;
+    A.fr = A.nr > 1 ? 2 : 1;
+    A.fc = A.nc > 1 ? 2 : 1;
+    LevelH B;
+    B.nx = (A.nx + A.fx - 1) / A.fx;
+    B.ny = (A.ny + A.fy - 1) / A.fy;
+    B.nr = (A.nr + A.fr - 1) / A.fr;
+    B.nc = (A.nc + A.fc - 1) / A.fc;
+    B.nd = 8 * B.nr * B.nc;
+    B.dx = A.dx * A.fx;
+    B.dy = A.dy * A.fy;
+    B.mu.assign(B.nd, 0.0);
+    B.nu.assign(B.nd, 0.0);
+    B.p.assign(B.nd, 0.0);
+    for (int n = 0; n < A.nd; ++n) {  // merged patches: summed weight, weighted mean direction
+      const int f = n / (A.nr * A.nc), j = (n % (A.nr * A.nc)) / A.nc, i = n % A.nc;
+      const int N = f * B.nr * B.nc + (j / A.fr) * B.nc + i / A.fc;
+      B.p[N] += A.p[n];
+      B.mu[N] += A.p[n] * A.mu[n];
+      B.nu[N] += A.p[n] * A.nu[n];
+    }
+    for (int N = 0; N < B.nd; ++N) {
+      B.mu[N] /= B.p[N];
+      B.nu[N] /= B.p[N];
+    }
+    B.sig.assign((size_t)G * B.npix(), 0.0);
+    for (int g = 0; g < G; ++g)
+      for (int Y = 0; Y < B.ny; ++Y)
+        for (int X = 0; X < B.nx; ++X) {  // harmonic mean of the present children, 0 if any is 0
+          int cnt = 0;
+          bool zero = false;
+          double inv = 0.0;
+          for (int yy = 0; yy < A.fy; ++yy)
+            for (int xx = 0; xx < A.fx; ++xx) {
+              const int x = X * A.fx + xx, y = Y * A.fy + yy;
+              if (x >= A.nx || y >= A.ny) continue;
+              const double v = A.sig[(size_t)g * A.npix() + (size_t)y * A.nx + x];
+              ++cnt;
+              if (v == 0.0) zero = true;
+              else inv += 1.0 / v;
+            }
+          B.sig[(size_t)g * B.npix() + (size_t)Y * B.nx + X] = zero ? 0.0 : cnt / inv;
+        }
+    P->lev.push_back(B);
+  }
+  P->L = (int)P->lev.size();
+  for (int r = 0; r < d->n_regions; ++r)
+    for (int g = 0; g < G; ++g)
+      for (int h = g + 1; h < G; ++h)
+        if (d->sigma_s[((size_t)r * G + g) * G + h] != 0.0) P->upscatter = true;
+  // direction chunks of the fine level: enough CTAs to fill 152 SMs
+  const LevelH& F = P->lev[0];
+  P->tiles_x = (F.nx + kTile - 1) / kTile;
+  P->tiles_y = (F.ny + kTile - 1) / kTile;
+  const int tiles = P->tiles_x * P->tiles_y;
+  int want = (4 * 152 + tiles - 1) / tiles;
+  if (want > F.nd) want = F.nd;
+  int dpc = F.nd / (want < 1 ? 1 : want);
+  if (dpc < 1) dpc = 1;
+  while (F.nd % dpc) --dpc;
+  P->dpc = dpc;
+  P->nchunk = F.nd / dpc;
+  P->graphs.assign(G, nullptr);
+
+  int rc = BTMG_OK;
+  auto bail = [&](int code) {
+    destroy(P);
+    return code;
+  };
+  std::vector<char> buf;
+  P->d_dir.assign(P->L, nullptr);
+  P->d_rcoef.assign(P->L, nullptr);
+  P->d_sig.assign(P->L, nullptr);
+  P->d_s.assign(P->L, nullptr);
+  P->d_delta.assign(P->L, nullptr);
+  for (int l = 0; l < P->L; ++l) {
+    const LevelH& A = P->lev[l];
+    if (P->f64) put_dirs<double>(buf, A);
+    else put_dirs<float>(buf, A);
+    if ((rc = upload(&P->d_dir[l], buf))) return bail(rc);
+    if (P->f64) put_vals<double>(buf, A.sig);
+    else put_vals<float>(buf, A.sig);
+    if ((rc = upload(&P->d_sig[l], buf))) return bail(rc);
+    if (l + 1 < P->L) {  // restriction weights p_n dx dy / (P_N dX dY)
+      const LevelH& B = P->lev[l + 1];
+      std::vector<double> rc_(A.nd);
+      for (int n = 0; n < A.nd; ++n) {
+        const int f = n / (A.nr * A.nc), j = (n % (A.nr * A.nc)) / A.nc, i = n % A.nc;
+        const int N = f * B.nr * B.nc + (j / A.fr) * B.nc + i / A.fc;
+        rc_[n] = A.p[n] * A.dx * A.dy / (B.p[N] * B.dx * B.dy);
+      }
+      if (P->f64) put_vals<double>(buf, rc_);
+      else put_vals<float>(buf, rc_);
+      if ((rc = upload(&P->d_rcoef[l], buf))) return bail(rc);
+    }
+    if (cudaMalloc(&P->d_s[l], A.n() * P->csize) != cudaSuccess) return bail(fail(BTMG_ERR_OOM, "workspace s"));
+    if (l >= 1 && cudaMalloc(&P->d_delta[l], A.n() * P->csize) != cudaSuccess)
+      return bail(fail(BTMG_ERR_OOM, "workspace delta"));
+  }
+  if (P->f64) put_vals<double>(buf, sigs);
+  else put_vals<float>(buf, sigs);
+  if ((rc = upload(&P->d_sigs, buf))) return bail(rc);
+  if (P->f64) put_vals<double>(buf, src);
+  else put_vals<float>(buf, src);
+  if ((rc = upload(&P->d_src, buf))) return bail(rc);
+  if (cudaMalloc(&P->d_b, npix * P->csize) != cudaSuccess ||
+      cudaMalloc(&P->d_phi_part, (size_t)G * P->nchunk * npix * P->csize) != cudaSuccess ||
+      cudaMalloc(&P->d_psi_tmp, F.n() * dtype_size(P->dtype)) != cudaSuccess)
+    return bail(fail(BTMG_ERR_OOM, "workspace"));
+  P->n_norm_part = tiles * P->nchunk;
+  P->n_q_blocks = (int)((npix + 255) / 256 < 1024 ? (npix + 255) / 256 : 1024);
+  if (cudaMalloc(&P->d_norm_part, sizeof(double) * P->n_norm_part) != cudaSuccess ||
+      cudaMalloc(&P->d_qn2_part, sizeof(double) * P->n_q_blocks) != cudaSuccess ||
+      cudaMalloc(&P->d_rn2, sizeof(double) * G) != cudaSuccess ||
+      cudaMalloc(&P->d_qn2, sizeof(double) * G) != cudaSuccess ||
+      cudaMallocHost(&P->h_pinned, sizeof(double) * 2 * G) != cudaSuccess)
+    return bail(fail(BTMG_ERR_OOM, "workspace norms"));
+  if (cudaStreamCreateWithFlags(&P->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->order_event, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(BTMG_ERR_CUDA, "stream creation"));
+  cudaMemset(P->d_rn2, 0, sizeof(double) * G);
+  cudaMemset(P->d_qn2, 0, sizeof(double) * G);
+  *out = P;
+  return BTMG_OK;
+}
+
+int check_level(const btmg_problem* p, int level) {
+  if (!p) return fail(BTMG_ERR_INVALID_ARG, "null problem");
+  if (level < 0 || level >= p->L) return fail(BTMG_ERR_INVALID_ARG, "level out of range");
+  return BTMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int btmg_create_problem(const btmg_problem_desc* desc, void* stream, btmg_problem** out) {
+  (void)stream;
+  try {
+    return create(desc, out);
+  } catch (...) {
+    return fail(BTMG_ERR_OOM, "host allocation failed");
+  }
+}
+
+int btmg_destroy_problem(btmg_problem* p) {
+  destroy(p);
+  return BTMG_OK;
+}
+
+int btmg_num_unknowns(const btmg_problem* p, int64_t* n) {
+  if (!p || !n) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  *n = (int64_t)p->G * (int64_t)p->lev[0].n();
+  return BTMG_OK;
+}
+
+int btmg_get_layout(const btmg_problem* p, int64_t strides[6]) {
+  if (!p || !strides) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  const LevelH& A = p->lev[0];
+  strides[5] = 1;
+  strides[4] = A.nx;
+  strides[3] = (int64_t)A.nx * A.ny;
+  strides[2] = strides[3] * A.nc;
+  strides[1] = strides[2] * A.nr;
+  strides[0] = strides[1] * 8;
+  return BTMG_OK;
+}
+
+int btmg_num_levels(const btmg_problem* p, int32_t* levels) {
+  if (!p || !levels) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  *levels = p->L;
+  return BTMG_OK;
+}
+
+int btmg_level_info(const btmg_problem* p, int32_t level, int32_t dims[5], double dxdy[2]) {
+  if (int rc = check_level(p, level)) return rc;
+  const LevelH& A = p->lev[level];
+  if (dims) {
+    dims[0] = A.nx;
+    dims[1] = A.ny;
+    dims[2] = A.nr;
+    dims[3] = A.nc;
+    dims[4] = A.nd;
+  }
+  if (dxdy) {
+    dxdy[0] = A.dx;
+    dxdy[1] = A.dy;
+  }
+  return BTMG_OK;
+}
+
+int btmg_level_quadrature(const btmg_problem* p, int32_t level, double* mu, double* nu, double* w) {
+  if (int rc = check_level(p, level)) return rc;
+  const LevelH& A = p->lev[level];
+  for (int n = 0; n < A.nd; ++n) {
+    if (mu) mu[n] = A.mu[n];
+    if (nu) nu[n] = A.nu[n];
+    if (w) w[n] = A.p[n];
+  }
+  return BTMG_OK;
+}
+
+int btmg_scalar_flux(btmg_problem* p, const void* psi, void* phi, void* stream) {
+  if (!p || !psi || !phi) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  return dispatch<RunFlux>(p->dtype, p, psi, phi, (cudaStream_t)stream);
+}
+
+int btmg_apply_operator(btmg_problem* p, const void* psi, void* r, void* stream) {
+  if (!p || !psi || !r) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  return dispatch<RunApply>(p->dtype, p, psi, r, (cudaStream_t)stream);
+}
+
+int btmg_smooth(btmg_problem* p, void* psi, const void* src, int32_t level, int32_t group, int32_t sweeps,
+                int32_t kind, void* stream) {
+  if (int rc = check_level(p, level)) return rc;
+  if (!psi || sweeps < 0) return fail(BTMG_ERR_INVALID_ARG, "bad psi or sweeps");
+  if (kind == BTMG_SMOOTH_PG) {
+    if (level != 0 || src) return fail(BTMG_ERR_INVALID_ARG, "PG smoothing is on level 0 with src = NULL");
+    return dispatch<RunSmoothPG>(p->dtype, p, psi, (int)sweeps, (cudaStream_t)stream);
+  }
+  if (kind != BTMG_SMOOTH_UPWIND) return fail(BTMG_ERR_INVALID_ARG, "bad smoother kind");
+  if (!src || group < 0 || group >= p->G) return fail(BTMG_ERR_INVALID_ARG, "upwind smoothing needs src and group");
+  return dispatch<RunSmoothUp>(p->dtype, p, psi, src, (int)level, (int)group, (int)sweeps, (cudaStream_t)stream);
+}
+
+int btmg_restrict(btmg_problem* p, int32_t level, const void* fine, void* coarse, void* stream) {
+  if (int rc = check_level(p, level)) return rc;
+  if (level + 1 >= p->L || !fine || !coarse) return fail(BTMG_ERR_INVALID_ARG, "bad restriction arguments");
+  const LevelH &A = p->lev[level], &B = p->lev[level + 1];
+  cudaError_t e = p->f64 ? launch_restrict<double>((const double*)fine, (double*)coarse, (const double*)p->d_rcoef[level], A.nx,
+                                                   A.ny, A.nr, A.nc, B.nx, B.ny, B.nr, B.nc, A.fx, A.fy, A.fr, A.fc,
+                                                   (cudaStream_t)stream)
+                         : launch_restrict<float>((const float*)fine, (float*)coarse, (const float*)p->d_rcoef[level], A.nx,
+                                                  A.ny, A.nr, A.nc, B.nx, B.ny, B.nr, B.nc, A.fx, A.fy, A.fr, A.fc,
+                                                  (cudaStream_t)stream);
+  CK(e);
+  return BTMG_OK;
+}
+
+int btmg_prolong(btmg_problem* p, int32_t level, const void* coarse, void* fine, void* stream) {
+  if (int rc = check_level(p, level)) return rc;
+  if (level + 1 >= p->L || !fine || !coarse) return fail(BTMG_ERR_INVALID_ARG, "bad prolongation arguments");
+  const LevelH &A = p->lev[level], &B = p->lev[level + 1];
+  cudaError_t e = p->f64 ? launch_prolong<double>((const double*)coarse, (double*)fine, A.nx, A.ny, A.nr, A.nc, B.nx,
+                                                  B.ny, B.nr, B.nc, A.fx, A.fy, A.fr, A.fc, (cudaStream_t)stream)
+                         : launch_prolong<float>((const float*)coarse, (float*)fine, A.nx, A.ny, A.nr, A.nc, B.nx,
+                                                 B.ny, B.nr, B.nc, A.fx, A.fy, A.fr, A.fc, (cudaStream_t)stream);
+  CK(e);
+  return BTMG_OK;
+}
+
+int btmg_mg_cycle(btmg_problem* p, void* psi, double* rel_resid, void* stream) {
+  if (!p || !psi) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  return dispatch<RunCycle>(p->dtype, p, psi, rel_resid, (cudaStream_t)stream);
+}
+
+int btmg_solve(btmg_problem* p, void* psi, double rtol, int32_t max_cycles, btmg_solve_info* info, void* stream) {
+  if (!p || !psi || max_cycles < 1) return fail(BTMG_ERR_INVALID_ARG, "bad solve arguments");
+  return dispatch<RunSolve>(p->dtype, p, psi, rtol, (int)max_cycles, info, (cudaStream_t)stream);
+}
+
+int btmg_profile(btmg_problem* p, int32_t enable) {
+  if (!p) return fail(BTMG_ERR_INVALID_ARG, "null problem");
+  p->prof_on = enable != 0;
+  p->prof_cls.clear();
+  return BTMG_OK;
+}
+
+int btmg_profile_read(btmg_problem* p, double* ms, int64_t* count, int32_t n_classes) {
+  if (!p || !ms || !count || n_classes < 1) return fail(BTMG_ERR_INVALID_ARG, "bad profile arguments");
+  for (int c = 0; c < n_classes; ++c) {
+    ms[c] = 0.0;
+    count[c] = 0;
+  }
+  for (size_t i = 0; i < p->prof_cls.size(); ++i) {
+    CK(cudaEventSynchronize(p->prof_pool[2 * i + 1]));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, p->prof_pool[2 * i], p->prof_pool[2 * i + 1]));
+    const int c = p->prof_cls[i];
+    if (c < n_classes) {
+      ms[c] += t;
+      count[c] += 1;
+    }
+  }
+  p->prof_cls.clear();
+  return BTMG_OK;
+}
+
+int btmg_launch_count(const btmg_problem* p, int64_t* n) {
+  if (!p || !n) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  *n = p->launches;
+  return BTMG_OK;
+}
+
+const char* btmg_error_string(int status) {
+  switch (status) {
+    case BTMG_OK: return "ok";
+    case BTMG_ERR_INVALID_ARG: return "invalid argument";
+    case BTMG_ERR_CUDA: return "CUDA error";
+    case BTMG_ERR_OOM: return "out of memory";
+    case BTMG_ERR_NOT_CONVERGED: return "not converged";
+    case BTMG_ERR_DIVERGED: return "diverged";
+    case BTMG_ERR_TIMEOUT: return "timeout";
+    case BTMG_ERR_NAN: return "NaN in the iteration";
+    case BTMG_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* btmg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// btmg_common.cuh -- types and launcher declarations shared by the CUDA
+// translation units of the btmg library (sm_103a).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace btmg {
+
+// ---------------------------------------------------------------- types ---
+template <typename T> struct Conv;
+template <> struct Conv<double> {
+  __device__ __forceinline__ static double ld(const double* p) { return *p; }
+  template <typename C> __device__ __forceinline__ static void st(double* p, C v) { *p = (double)v; }
+};
+template <> struct Conv<float> {
+  __device__ __forceinline__ static float ld(const float* p) { return *p; }
+  template <typename C> __device__ __forceinline__ static void st(float* p, C v) { *p = (float)v; }
+};
+template <> struct Conv<__nv_bfloat16> {
+  __device__ __forceinline__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  template <typename C> __device__ __forceinline__ static void st(__nv_bfloat16* p, C v) {
+    *p = __float2bfloat16_rn((float)v);
+  }
+};
+template <> struct Conv<__half> {
+  __device__ __forceinline__ static float ld(const __half* p) { return __half2float(*p); }
+  template <typename C> __device__ __forceinline__ static void st(__half* p, C v) {
+    *p = __float2half_rn((float)v);
+  }
+};
+// value of v after a round trip through storage type T (the stored value)
+template <typename T, typename C> __device__ __forceinline__ C stored(C v) {
+  T t;
+  Conv<T>::st(&t, v);
+  return (C)Conv<T>::ld(&t);
+}
+
+// Per-direction constants of one level (mu, nu, p and the upwind factors
+// |mu|/dX, |nu|/dY), in the compute type.
+template <typename C> struct Dir {
+  C mu, nu, w, ax, ay;
+};
+
+enum { BC_VACUUM = 0, BC_REFLECTIVE = 1 };
+
+// Halo rule of Sec. 2.3: an out-of-domain position takes 0 when it lies on
+// an incoming side of a vacuum boundary (mu > 0 at x < 0, mu < 0 at x >= nx,
+// likewise in y), otherwise the value of the nearest interior node.
+struct Bc {
+  int xlo, xhi, ylo, yhi;
+};
+__device__ __forceinline__ bool halo_is_zero(const Bc& bc, int gx, int gy, int nx, int ny, bool sxp,
+                                             bool syp) {
+  return (gx < 0 && bc.xlo == BC_VACUUM && sxp) || (gx >= nx && bc.xhi == BC_VACUUM && !sxp) ||
+         (gy < 0 && bc.ylo == BC_VACUUM && syp) || (gy >= ny && bc.yhi == BC_VACUUM && !syp);
+}
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// ------------------------------------------------------- PG residual -------
+enum { PG_RESID = 0, PG_JACOBI = 1 };
+
+template <typename T, typename C> struct PgArgs {
+  const T* psi;       // one group: [nd][ny][nx]
+  T* psi_out;         // PG_JACOBI: updated angular flux, [nd][ny][nx]
+  C* r_out;           // PG_RESID: residual b - A psi, [nd][ny][nx]
+  const C* b;         // [ny][nx] isotropic right-hand side of this group
+  const C* sigt;      // [ny][nx]
+  const Dir<C>* dir;  // [nd]
+  C* phi_part;        // PG_JACOBI: [nchunk][ny][nx] partial scalar fluxes
+  double* norm_part;  // PG_RESID: [gridDim.x*gridDim.y] partial sum p dx dy r^2
+  int nx, ny, nd, dpc, tiles_x;  // dpc = directions per chunk
+  C inv_dx, inv_dy, inv_dx2, inv_dy2, dx, dy, dxdy;
+  C eps_k, a_kabs, a_ksq, a_r, half, beta;
+  Bc bc;
+};
+
+// ------------------------------------------------------- upwind Jacobi ----
+enum { UP_CORR = 0, UP_UPDATE = 1 };
+enum { INIT_ZERO = 0, INIT_UPSAMPLE = 1, INIT_SAME = 2 };
+
+template <typename T, typename C> struct UpArgs {
+  const C* src;        // [nd][ny][nx] source of the correction equation
+  size_t src_stride;   // elements between direction planes of src (0: isotropic)
+  const C* init;       // INIT_UPSAMPLE: coarse level [ndc][nyc][nxc]; INIT_SAME: [nd][ny][nx]
+  C* delta_out;        // UP_CORR: [nd][ny][nx]
+  const T* psi_in;     // UP_UPDATE
+  T* psi_out;          // UP_UPDATE
+  C* phi_part;         // UP_UPDATE: [nchunk][ny][nx]
+  const C* sig;        // [ny][nx] (harmonic averaged on coarse levels)
+  const Dir<C>* dir;   // [nd]
+  int nx, ny, nr, nc, nd;
+  int nxc, nyc, nrc, ncc;  // coarse dims (INIT_UPSAMPLE)
+  int fx, fy, fr, fc;      // coarsening factors to the coarse level (1 or 2)
+  int nu, init_mode, dpc, tiles_x;
+  Bc bc;
+};
+
+// ----------------------------------------------------------- launchers -----
+// All return cudaError_t of the launch.
+template <typename T, typename C>
+cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cudaStream_t s);
+template <typename T, typename C>
+cudaError_t launch_upwind(const UpArgs<T, C>& a, int mode, int nchunk, cudaStream_t s);
+
+template <typename C>
+cudaError_t launch_restrict(const C* fine, C* coarse, const C* rcoef, int nx, int ny, int nr, int nc,
+                            int nxc, int nyc, int nrc, int ncc, int fx, int fy, int fr, int fc,
+                            cudaStream_t s);
+template <typename C>
+cudaError_t launch_prolong(const C* coarse, C* fine, int nx, int ny, int nr, int nc, int nxc, int nyc,
+                           int nrc, int ncc, int fx, int fy, int fr, int fc, cudaStream_t s);
+template <typename T, typename C>
+cudaError_t launch_phi_partial(const T* psi, C* phi_part, const Dir<C>* dir, int nx, int ny, int nd,
+                               int dpc, int nchunk, cudaStream_t s);
+// b = s_g + sum_h sigma_s[g<-h] phi_h / (4 pi); qn2_part[block] = sum (b_fixed)^2
+template <typename C>
+cudaError_t launch_source(const C* src_g, const C* sigs_g /*[G][ny][nx] from h*/, const C* phi_part,
+                          int G, int g, int nchunk, int npix, C* b, C* qfix_out, double* qn2_part,
+                          int nblocks, cudaStream_t s);
+template <typename C>
+cudaError_t launch_phi_sum(const C* phi_part, int nchunk, int npix, C* phi, cudaStream_t s);
+// out[0] = sum(part[0..n)) (deterministic, one block)
+cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s);
+
+}  // namespace btmg

@@ -1,0 +1,265 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64
+CPU oracle on the same seeded inputs (element by element), at sizes the
+oracle finishes in seconds (several 32x32 tiles plus ragged tails), and at
+the full 256^2 x 512-direction workload on sampled direction planes.
+
+Tolerances (relative L2 unless stated):
+  FP64 storage/compute : operator 1e-12, one cycle 1e-10 (rounding order only)
+  FP32                 : operator 1e-6, cycle sequence 1e-5, converged solve 1e-5
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2301_09991_gb300 import btmg, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev(a, dtype):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+SMALL = [
+    ("checker_72x40", lambda: I.checkerboard(n=72, ny=40, n_polar=8, n_azim=16, blocks=4, seed=11)),
+    ("two_region_32", lambda: I.two_region()),
+    ("tiny_5x3", lambda: I.checkerboard(n=5, ny=3, n_polar=4, n_azim=8, blocks=2, seed=12)),
+    ("one_node", lambda: I.uniform(1, 1, 2, 4, sigma_t=1.3, c=0.4)),
+    ("reflective_33x17", lambda: I.checkerboard(n=33, ny=17, n_polar=4, n_azim=8, blocks=3, seed=13,
+                                                bc=(1, 0, 1, 1))),
+]
+
+
+@pytest.mark.parametrize("name,mk", SMALL)
+def test_quadrature_and_hierarchy_match(name, mk):
+    prob = mk()
+    gp = btmg.Problem(prob, dtype=btmg.F64)
+    op = O.OracleProblem(prob)
+    assert gp.L == op.L
+    for a, b in zip(gp.levels, op.levels):
+        assert (a["nx"], a["ny"], a["nr"], a["nc"]) == (b["nx"], b["ny"], b["nr"], b["nc"])
+        assert abs(a["dx"] - b["dx"]) < 1e-15 and abs(a["dy"] - b["dy"]) < 1e-15
+        np.testing.assert_allclose(a["mu"], b["mu"], atol=1e-14)
+        np.testing.assert_allclose(a["nu"], b["nu"], atol=1e-14)
+        np.testing.assert_allclose(a["p"], b["p"], rtol=1e-13)
+
+
+@pytest.mark.parametrize("name,mk", SMALL)
+@pytest.mark.parametrize("pg", [1, 0])
+def test_apply_operator_fp64(name, mk, pg):
+    prob = mk()
+    gp = btmg.Problem(prob, dtype=btmg.F64, pg=pg)
+    op = O.OracleProblem(prob, pg=pg)
+    psi0 = I.random_field(gp.shape, seed=5)
+    r = host(gp.apply_operator(dev(psi0, torch.float64)))
+    assert rel(r, op.apply(psi0)) < 1e-12
+
+
+@pytest.mark.parametrize("name,mk", SMALL[:3])
+def test_apply_operator_fp32(name, mk):
+    prob = mk()
+    gp = btmg.Problem(prob, dtype=btmg.F32)
+    op = O.OracleProblem(prob)
+    psi0 = I.random_field(gp.shape, seed=6).astype(np.float32)
+    r = host(gp.apply_operator(dev(psi0, torch.float32)))
+    assert rel(r, op.apply(psi0.astype(np.float64))) < 1e-6
+
+
+def test_apply_operator_multigroup_and_half():
+    prob = I.multigroup(n=40, n_polar=4, n_azim=8, G=3, blocks=4, seed=9)
+    for half in (0, 1):
+        gp = btmg.Problem(prob, dtype=btmg.F64, pg_half=half)
+        op = O.OracleProblem(prob, pg_half=half)
+        psi0 = I.random_field(gp.shape, seed=8)
+        assert rel(host(gp.apply_operator(dev(psi0, torch.float64))), op.apply(psi0)) < 1e-12
+
+
+def test_scalar_flux():
+    prob = I.multigroup(n=36, n_polar=4, n_azim=8, G=2, blocks=3, seed=4)
+    gp = btmg.Problem(prob, dtype=btmg.F32)
+    op = O.OracleProblem(prob)
+    psi0 = I.random_field(gp.shape, seed=2).astype(np.float32)
+    phi = host(gp.scalar_flux(dev(psi0, torch.float32)))
+    assert rel(phi, op.scalar_flux(psi0.astype(np.float64))) < 1e-6
+
+
+@pytest.mark.parametrize("name,mk", SMALL)
+def test_restrict_prolong(name, mk):
+    prob = mk()
+    gp = btmg.Problem(prob, dtype=btmg.F64)
+    op = O.OracleProblem(prob)
+    rng = np.random.default_rng(1)
+    for l in range(gp.L - 1):
+        fine = rng.standard_normal(gp.level_shape(l))
+        c = host(gp.restrict(l, dev(fine, torch.float64)))
+        assert rel(c, op.restrict(l, fine)) < 1e-13
+        coarse = rng.standard_normal(gp.level_shape(l + 1))
+        f = host(gp.prolong(l, dev(coarse, torch.float64)))
+        assert np.array_equal(f, op.prolong(l, coarse))
+
+
+@pytest.mark.parametrize("name,mk", SMALL)
+@pytest.mark.parametrize("sweeps", [1, 3, 11])
+def test_upwind_jacobi_every_level(name, mk, sweeps):
+    prob = mk()
+    gp = btmg.Problem(prob, dtype=btmg.F64)
+    op = O.OracleProblem(prob)
+    rng = np.random.default_rng(sweeps)
+    for l in range(gp.L):
+        s = rng.standard_normal(gp.level_shape(l))
+        d0 = rng.standard_normal(gp.level_shape(l))
+        d = dev(d0, torch.float64)
+        gp.smooth_upwind(d, dev(s, torch.float64), l, 0, sweeps)
+        assert rel(host(d), op.jacobi_upwind(l, 0, s, d0, sweeps)) < 1e-13
+
+
+@pytest.mark.parametrize("name,mk", SMALL[:2])
+def test_pg_jacobi_sweeps(name, mk):
+    prob = mk()
+    gp = btmg.Problem(prob, dtype=btmg.F64)
+    op = O.OracleProblem(prob)
+    psi0 = I.random_field(gp.shape, seed=21)
+    psi = dev(psi0, torch.float64)
+    gp.smooth_pg(psi, sweeps=2)
+    assert rel(host(psi), op.pg_jacobi(psi0, 2)) < 1e-12
+
+
+@pytest.mark.parametrize("name,mk", SMALL)
+@pytest.mark.parametrize("pg", [1, 0])
+def test_mg_cycle_sequence_fp64(name, mk, pg):
+    prob = mk()
+    gp = btmg.Problem(prob, dtype=btmg.F64, pg=pg)
+    op = O.OracleProblem(prob, pg=pg)
+    psi = gp.zeros()
+    ref = op.zeros()
+    for k in range(3):
+        rg = gp.mg_cycle(psi)
+        ref, rr, _ = op.mg_cycle(ref)
+        assert abs(rg - rr) <= 1e-9 * max(rr, 1e-30), (k, rg, rr)
+        assert rel(host(psi), ref) < 1e-10, k
+
+
+def test_mg_cycle_multigroup_fp64():
+    prob = I.multigroup(n=24, n_polar=4, n_azim=8, G=3, blocks=3, seed=5)
+    gp = btmg.Problem(prob, dtype=btmg.F64)
+    op = O.OracleProblem(prob)
+    psi = gp.zeros()
+    ref = op.zeros()
+    for _ in range(2):
+        gp.mg_cycle(psi)
+        ref, _, _ = op.mg_cycle(ref)
+    assert rel(host(psi), ref) < 1e-10
+
+
+def test_mg_cycle_fp32_pg_one_cycle():
+    """The nonlinear PG cycle amplifies an input perturbation about 20x per
+    cycle (measured with the FP64 oracle: 1e-7 -> 6e-7, 2e-5, 4e-4), so FP32
+    is compared over one cycle from psi = 0."""
+    prob = I.checkerboard(n=72, ny=40, n_polar=8, n_azim=16, blocks=4, seed=11)
+    gp = btmg.Problem(prob, dtype=btmg.F32)
+    op = O.OracleProblem(prob)
+    psi = gp.zeros()
+    gp.mg_cycle(psi)
+    ref, _, _ = op.mg_cycle(op.zeros())
+    assert rel(host(psi), ref) < 1e-5
+
+
+def test_mg_cycle_sequence_fp32_upwind():
+    prob = I.checkerboard(n=72, ny=40, n_polar=8, n_azim=16, blocks=4, seed=11)
+    gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+    op = O.OracleProblem(prob, pg=0)
+    psi = gp.zeros()
+    ref = op.zeros()
+    for k in range(3):
+        gp.mg_cycle(psi)
+        ref, _, _ = op.mg_cycle(ref)
+        assert rel(host(psi), ref) < 1e-6, k
+
+
+def test_converged_solve_fp64_small_config():
+    """32x32 nodes, 64 directions, two regions, FP64 on the GPU, upwind fine
+    scheme (the PG iteration stagnates, see the design notes) to 1e-8."""
+    prob = I.two_region()
+    gp = btmg.Problem(prob, dtype=btmg.F64, pg=0)
+    op = O.OracleProblem(prob, pg=0)
+    psi = gp.zeros()
+    out = gp.solve(psi, rtol=1e-8, max_cycles=300)
+    ref, n, rr, _ = op.solve(rtol=1e-8, max_cycles=300)
+    assert out["status"] == 0 and out["rel_resid"] < 1e-8
+    assert out["cycles"] == n
+    assert rel(host(psi), ref) < 1e-10
+
+
+def test_converged_solve_fp32_vs_fp64_solution():
+    """FP32 cycles until the FP32 residual stops falling (its rounding floor
+    is near 1e-5 at this resolution); the iterate must be within 1e-5 of
+    the converged FP64 oracle solution."""
+    prob = I.checkerboard(n=64, n_polar=8, n_azim=16, blocks=4, seed=2, c=0.9)
+    gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+    op = O.OracleProblem(prob, pg=0)
+    psi = gp.zeros()
+    out = gp.solve(psi, rtol=1e-7, max_cycles=400)
+    ref, n, rr, _ = op.solve(rtol=1e-11, max_cycles=3000)
+    assert rr < 1e-11
+    assert out["status"] in (btmg.OK, btmg.ERR_NOT_CONVERGED)
+    assert rel(host(psi), ref) < 1e-5, (out["rel_resid"], out["cycles"])
+
+
+def test_solve_multigroup_downscatter_fp64():
+    prob = I.multigroup(n=24, n_polar=4, n_azim=8, G=3, blocks=3, seed=6)
+    gp = btmg.Problem(prob, dtype=btmg.F64, pg=0)
+    op = O.OracleProblem(prob, pg=0)
+    psi = gp.zeros()
+    out = gp.solve(psi, rtol=1e-9, max_cycles=400, max_outer=1)
+    ref, n, rr, _ = op.solve(rtol=1e-9, max_cycles=400, max_outer=1)
+    assert out["cycles"] == n
+    assert rel(host(psi), ref) < 1e-9
+
+
+def test_full_size_apply_sampled_planes():
+    """256^2 nodes x 512 directions (the FP32 single-group workload), launch
+    configuration as in the benchmark; 12 sampled planes from the oracle."""
+    prob = I.checkerboard(n=256, n_polar=16, n_azim=32, blocks=8, seed=2)
+    gp = btmg.Problem(prob, dtype=btmg.F32)
+    op = O.OracleProblem(prob)
+    psi0 = I.random_field(gp.shape, seed=7).astype(np.float32)
+    r = gp.apply_operator(dev(psi0, torch.float32))
+    rng = np.random.default_rng(0)
+    planes = [(0, int(n)) for n in rng.choice(gp.nd, 12, replace=False)]
+    ref = op.apply_planes(psi0.astype(np.float64), planes)
+    got = np.stack([host(r[g, n]) for g, n in planes])
+    assert rel(got, ref) < 1e-6
+
+
+def test_deterministic_bitwise():
+    prob = I.checkerboard(n=72, ny=40, n_polar=8, n_azim=16, blocks=4, seed=11)
+    gp = btmg.Problem(prob, dtype=btmg.F32)
+    a, b = gp.zeros(), gp.zeros()
+    for _ in range(2):
+        ra = gp.mg_cycle(a)
+        rb = gp.mg_cycle(b)
+    assert ra == rb and torch.equal(a, b)
+
+
+def test_invalid_arguments_return_codes():
+    prob = I.uniform(8, 8, 4, 8)
+    with pytest.raises(btmg.BtmgError) as e:
+        btmg.Problem(dict(prob, n_polar=3))
+    assert e.value.code == btmg.ERR_INVALID_ARG
+    with pytest.raises(btmg.BtmgError) as e:
+        btmg.Problem(prob, nu=0)
+    assert e.value.code == btmg.ERR_INVALID_ARG
+    bad = dict(prob, region=np.full((8, 8), 5, dtype=np.int32))
+    with pytest.raises(btmg.BtmgError):
+        btmg.Problem(bad)
