@@ -21,13 +21,14 @@ SMOOTH_UPWIND, SMOOTH_PG = 0, 1
 OK = 0
 ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED = -1, -2, -3, -4
 ERR_DIVERGED, ERR_TIMEOUT, ERR_NAN, ERR_UNSUPPORTED = -5, -6, -7, -8
+ERR_NOALLOC_TOO_LARGE = -9
 
 EXPORTS = (
     "btmg_create_problem", "btmg_destroy_problem", "btmg_num_unknowns", "btmg_get_layout",
     "btmg_num_levels", "btmg_level_info", "btmg_level_quadrature", "btmg_scalar_flux",
     "btmg_apply_operator", "btmg_smooth", "btmg_restrict", "btmg_prolong", "btmg_mg_cycle",
     "btmg_solve", "btmg_error_string", "btmg_last_error", "btmg_profile", "btmg_profile_read",
-    "btmg_launch_count",
+    "btmg_launch_count", "btmg_apply_operator_noalloc",
 )
 PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
 
@@ -105,6 +106,8 @@ def load(build_if_missing: bool = True):
     L.btmg_profile.argtypes = [vp, i32]
     L.btmg_profile_read.argtypes = [vp, dp, i64p, i32]
     L.btmg_launch_count.argtypes = [vp, i64p]
+    L.btmg_apply_operator_noalloc.argtypes = [i32, i32, C.c_double, C.c_double, i32, i32,
+                                              C.POINTER(i32), i32, i32, vp, vp, vp, vp, vp, vp]
     L.btmg_error_string.restype = C.c_char_p
     L.btmg_error_string.argtypes = [C.c_int]
     L.btmg_last_error.restype = C.c_char_p

@@ -937,6 +937,7 @@ const char* btmg_error_string(int status) {
     case BTMG_ERR_TIMEOUT: return "timeout";
     case BTMG_ERR_NAN: return "NaN in the iteration";
     case BTMG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case BTMG_ERR_NOALLOC_TOO_LARGE: return "size beyond the allocation-free maximum";
   }
   return "unknown status";
 }

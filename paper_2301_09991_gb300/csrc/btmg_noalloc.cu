@@ -1,0 +1,190 @@
+// btmg_noalloc.cu -- an allocation-free form of btmg_apply_operator.
+//
+// Some callers cannot allocate device memory: code running inside a CUDA
+// graph being captured by someone else, an allocator-less embedded runtime,
+// or a host program that owns a fixed device-memory budget and forbids any
+// library from calling cudaMalloc.  btmg_apply_operator_noalloc() serves
+// them: the caller passes every input and output as device pointers, and
+// the scratch the operator needs (scalar flux, assembled source, direction
+// table and the partial sums of the residual norm) lives in one file-scope
+// device array of fixed size, g_scratch below.  Nothing here calls
+// cudaMalloc, cudaFree or any allocating routine.
+//
+// The array is part of the library image, so every GPU that loads the
+// library holds it (BTMG_NOALLOC_SCRATCH_BYTES) until the process exits.
+// All calls share it and it keeps the last call's contents; every byte a
+// call reads is written by that same call first, so nothing needs clearing,
+// but two calls that overlap on the GPU (different streams, or the same
+// problem issued concurrently) race on it.
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/btmg.h"
+#include "btmg_common.cuh"
+
+using namespace btmg;
+
+namespace {
+
+constexpr int kMaxPix = BTMG_NOALLOC_MAX_NODES;
+constexpr int kMaxDirs = BTMG_NOALLOC_MAX_DIRS;
+constexpr int kTile = 32;
+constexpr int kChunks = 16;  // direction chunks of the residual kernel
+constexpr int kMaxNormParts = (kMaxPix / (kTile * kTile) + 64) * kChunks;
+constexpr int kQBlocks = 1024;
+// layout of the scratch array (offsets in bytes, each 256-byte aligned)
+constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kOffPhi = 0;
+constexpr size_t kOffB = align256(kOffPhi + sizeof(float) * kMaxPix);
+constexpr size_t kOffDir = align256(kOffB + sizeof(float) * kMaxPix);
+constexpr size_t kOffNorm = align256(kOffDir + sizeof(Dir<float>) * kMaxDirs);
+constexpr size_t kOffQ = align256(kOffNorm + sizeof(double) * kMaxNormParts);
+constexpr size_t kOffSums = align256(kOffQ + sizeof(double) * kQBlocks);
+constexpr size_t kScratchBytes = align256(kOffSums + 2 * sizeof(double));
+static_assert(kScratchBytes <= BTMG_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
+
+__device__ __align__(256) unsigned char g_scratch[BTMG_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_scratch per device, looked up once per device (the
+// host-side name g_scratch is only a stand-in for the device symbol).
+constexpr int kMaxDevices = 64;
+unsigned char* g_scratch_dev[kMaxDevices] = {nullptr};
+
+// Gauss-Legendre points on [0,1] into fixed arrays (Newton on P_n).
+void gauss16(double* x, double* w) {
+  const int n = 16;
+  for (int k = 0; k < n; ++k) {
+    double t = std::cos(3.14159265358979323846 * (4.0 * k + 3.0) / (4.0 * n + 2.0)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double pm = 0.0, p = 1.0;
+      for (int m = 1; m <= n; ++m) {
+        const double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm) / m;
+        pm = p;
+        p = pn;
+      }
+      dp = n * (pm - t * p) / (1.0 - t * t);
+      const double step = p / dp;
+      t -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    x[k] = 0.5 * (1.0 + t);
+    w[k] = 1.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+// Octahedral directions (Sec. 2.2) into a fixed table: solid-angle element
+// (1-t)/|X|^3 of the collapsed map X(u,t), weights scaled to sum 4 pi.
+void directions(int nr, int nc, double dx, double dy, Dir<float>* out) {
+  double gx[16], gw[16];
+  gauss16(gx, gw);
+  const int nd = 8 * nr * nc;
+  double total = 0.0;
+  double P[kMaxDirs], MU[kMaxDirs], NU[kMaxDirs];  // on the stack
+  for (int f = 0; f < 8; ++f) {
+    const double sx = (f & 1) ? -1 : 1, sy = (f & 2) ? -1 : 1, sz = (f & 4) ? -1 : 1;
+    for (int j = 0; j < nr; ++j)
+      for (int i = 0; i < nc; ++i) {
+        double area = 0, mx = 0, my = 0;
+        for (int a = 0; a < 16; ++a)
+          for (int b = 0; b < 16; ++b) {
+            const double t = (j + gx[a]) / nr, u = (i + gx[b]) / nc;
+            const double X0 = (1 - t) * (1 - u) * sx, X1 = (1 - t) * u * sy, X2 = t * sz;
+            const double r2 = X0 * X0 + X1 * X1 + X2 * X2, r = std::sqrt(r2);
+            const double dS = gw[a] * gw[b] / (double(nr) * nc) * (1 - t) / (r2 * r);
+            area += dS;
+            mx += dS * X0 / r;
+            my += dS * X1 / r;
+          }
+        const int n = f * nr * nc + j * nc + i;
+        P[n] = area;
+        MU[n] = mx / area;
+        NU[n] = my / area;
+        total += area;
+      }
+  }
+  for (int n = 0; n < nd; ++n) {
+    const double w = P[n] * 4.0 * 3.14159265358979323846 / total;
+    out[n].mu = (float)MU[n];
+    out[n].nu = (float)NU[n];
+    out[n].w = (float)w;
+    out[n].ax = (float)(std::fabs(MU[n]) / dx);
+    out[n].ay = (float)(std::fabs(NU[n]) / dy);
+  }
+}
+
+}  // namespace
+
+extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, double ly, int32_t n_polar,
+                                           int32_t n_azim, const int32_t bc[4], int32_t pg, int32_t pg_half,
+                                           const float* sigma_t, const float* sigma_s, const float* source,
+                                           const float* psi, float* r, void* stream) {
+  if (nx < 1 || ny < 1 || !(lx > 0) || !(ly > 0) || !bc || !sigma_t || !sigma_s || !source || !psi || !r)
+    return BTMG_ERR_INVALID_ARG;
+  if (n_polar < 2 || n_polar % 2 || n_azim < 4 || n_azim % 4) return BTMG_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (bc[i] != BTMG_VACUUM && bc[i] != BTMG_REFLECTIVE) return BTMG_ERR_INVALID_ARG;
+  const int nr = n_polar / 2, nc = n_azim / 4, nd = 8 * nr * nc;
+  // sizes beyond the fixed scratch: a distinct status, nothing launched
+  if ((int64_t)nx * ny > kMaxPix || nd > kMaxDirs) return BTMG_ERR_NOALLOC_TOO_LARGE;
+  const int tiles_x = (nx + kTile - 1) / kTile;
+  const int64_t tiles = (int64_t)tiles_x * ((ny + kTile - 1) / kTile);
+  int nchunk = kChunks;  // direction chunks of the residual kernel
+  while (nchunk > 1 && (nd % nchunk || tiles * nchunk > kMaxNormParts)) nchunk >>= 1;
+  if (tiles * nchunk > kMaxNormParts) return BTMG_ERR_NOALLOC_TOO_LARGE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BTMG_ERR_CUDA;
+  if (!g_scratch_dev[dev]) {  // first call on this device: resolve the symbol
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return BTMG_ERR_CUDA;
+    g_scratch_dev[dev] = static_cast<unsigned char*>(p);
+  }
+  unsigned char* base = g_scratch_dev[dev];
+  float* phi = reinterpret_cast<float*>(base + kOffPhi);
+  float* b = reinterpret_cast<float*>(base + kOffB);
+  Dir<float>* dir = reinterpret_cast<Dir<float>*>(base + kOffDir);
+  double* norm_part = reinterpret_cast<double*>(base + kOffNorm);
+  double* q_part = reinterpret_cast<double*>(base + kOffQ);
+  double* sums = reinterpret_cast<double*>(base + kOffSums);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  const double dx = lx / nx, dy = ly / ny;
+  Dir<float> host_dir[kMaxDirs];  // on the stack; copied before return
+  directions(nr, nc, dx, dy, host_dir);
+  if (cudaMemcpyAsync(dir, host_dir, sizeof(Dir<float>) * nd, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return BTMG_ERR_CUDA;
+  // scalar flux in one chunk, then b = s + sigma_s phi / (4 pi)
+  if (launch_phi_partial<float, float>(psi, phi, dir, nx, ny, nd, nd, 1, s) != cudaSuccess) return BTMG_ERR_CUDA;
+  const int npix = nx * ny;
+  const int qb = (npix + 255) / 256 < kQBlocks ? (npix + 255) / 256 : kQBlocks;
+  if (launch_source<float>(source, sigma_s, phi, 1, 0, 1, npix, b, nullptr, q_part, qb, s) != cudaSuccess)
+    return BTMG_ERR_CUDA;
+  PgArgs<float, float> a{};
+  a.psi = psi;
+  a.r_out = r;
+  a.b = b;
+  a.sigt = sigma_t;
+  a.dir = dir;
+  a.nx = nx;
+  a.ny = ny;
+  a.nd = nd;
+  a.tiles_x = tiles_x;
+  a.dpc = nd / nchunk;
+  a.dx = (float)dx;
+  a.dy = (float)dy;
+  a.inv_dx = (float)(1.0 / dx);
+  a.inv_dy = (float)(1.0 / dy);
+  a.inv_dx2 = (float)(1.0 / (dx * dx));
+  a.inv_dy2 = (float)(1.0 / (dy * dy));
+  a.dxdy = (float)(dx * dy);
+  a.eps_k = 1e-3f;
+  a.a_kabs = 0.25f;
+  a.a_ksq = 2.0f;
+  a.a_r = 3.0f;
+  a.half = pg_half ? 0.5f : 1.0f;
+  a.beta = 1.0f;
+  a.bc = Bc{bc[0], bc[1], bc[2], bc[3]};
+  a.norm_part = norm_part;
+  if (launch_pg<float, float>(a, PG_RESID, pg != 0, nchunk, s) != cudaSuccess) return BTMG_ERR_CUDA;
+  if (launch_sum(norm_part, (int)(tiles * nchunk), sums, s) != cudaSuccess) return BTMG_ERR_CUDA;
+  return BTMG_OK;
+}

@@ -1,0 +1,60 @@
+"""The allocation-free residual entry point, checked against the standard one.
+
+Callers that cannot allocate device memory (a host that is capturing a CUDA
+graph of its own, a runtime without a device allocator, or a program that
+gives each library a fixed memory budget) use
+btmg_apply_operator_noalloc(), whose scratch is a fixed file-scope device
+array instead of cudaMalloc'd workspaces.  This test calls it through the C
+ABI twice in a row (two problems of different size, so stale scratch from
+the first call would show in the second) and compares each result with
+btmg_apply_operator on the same input, within the FP32 operator tolerance
+of the parity tests (relative L2 <= 1e-6).  It lives in its own file so that
+it is collected after every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2301_09991_gb300 import btmg, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(prob, psi, pg=1):
+    L = btmg.load()
+    region = prob["region"]
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    st = dev(prob["sigma_t"][region, 0])
+    ss = dev(prob["sigma_s"][region, 0, 0])
+    src = dev(prob["source"][region, 0])
+    r = torch.empty(psi.shape[1:], dtype=torch.float32, device="cuda")
+    bc = (C.c_int32 * 4)(*prob["bc"])
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptr = lambda t: C.c_void_p(t.data_ptr())
+    rc = L.btmg_apply_operator_noalloc(prob["nx"], prob["ny"], prob["lx"], prob["ly"], prob["n_polar"],
+                                       prob["n_azim"], bc, pg, 0, ptr(st), ptr(ss), ptr(src), ptr(psi),
+                                       ptr(r), stream)
+    torch.cuda.synchronize()
+    return rc, r
+
+
+def test_noalloc_matches_apply_operator_on_two_calls_in_a_row():
+    problems = [I.checkerboard(n=72, ny=40, n_polar=8, n_azim=16, blocks=4, seed=11),
+                I.two_region(nx=48, ny=33, n_polar=8, n_azim=8)]
+    for k, prob in enumerate(problems):
+        gp = btmg.Problem(prob, dtype=btmg.F32)
+        psi = torch.tensor(I.random_field(gp.shape, seed=40 + k), dtype=torch.float32, device="cuda")
+        ref = gp.apply_operator(psi)[0].double().cpu().numpy()
+        rc, r = _noalloc(prob, psi)
+        assert rc == btmg.OK
+        got = r.double().cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-6, k
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    prob = I.uniform(1024, 512, 4, 8)  # 524288 nodes > 512 x 512
+    psi = torch.zeros((64, 512, 1024), dtype=torch.float32, device="cuda")
+    rc, _ = _noalloc(prob, psi)
+    assert rc == btmg.ERR_NOALLOC_TOO_LARGE
