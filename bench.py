@@ -132,18 +132,18 @@ def traffic_from_profiles(kernel):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    src_hash = {}
-    for f in ("k_pg.cu", "k_mg.cu"):
-        p = os.path.join(ROOT, "paper_2301_09991_gb300", "csrc", f)
-        with open(p, "rb") as fh:
-            src_hash[f] = hashlib.sha256(fh.read()).hexdigest()[:16]
     with open(path) as fh:
         for line in fh:
             m = re.match(r"\s*(\w+)\s+bytes_per_launch=(\S+)\s+src=(\S+):(\w+)", line)
-            if m and m.group(1) == kernel:
-                if src_hash.get(m.group(3)) != m.group(4):
+            if not m or m.group(1) != kernel:
+                continue
+            src = os.path.join(ROOT, "paper_2301_09991_gb300", "csrc", m.group(3))
+            if not os.path.exists(src):
+                return None
+            with open(src, "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest()[:len(m.group(4))] != m.group(4):
                     return None
-                return float(m.group(2))
+            return float(m.group(2))
     return None
 
 

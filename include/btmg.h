@@ -163,6 +163,21 @@ int btmg_mg_cycle(btmg_problem* p, void* psi, double* rel_resid, void* stream);
 int btmg_solve(btmg_problem* p, void* psi, double rtol, int32_t max_cycles,
                btmg_solve_info* info, void* stream);
 
+/* Mixed-precision solve with FP64 iterative refinement.  psi64 is a
+ * caller-owned device FP64 buffer [G][nd][ny][nx] (initial guess in, solution
+ * out).  Each outer step computes r = b - A psi64 in FP64 on the GPU (an
+ * internal FP64 copy of the problem), solves the correction equation
+ * A delta = r / rms(r) with `inner_cycles` sawtooth cycles whose psi is
+ * stored in the problem's psi_dtype (BF16/FP16/FP32, FP32 accumulation), and
+ * adds rms(r) delta to psi64.  Stops when ||r||_W/||q||_W <= rtol or after
+ * max_outer corrections.  Needs pg = 0 (the correction equation of the
+ * nonlinear PG operator is not this linear one): BTMG_ERR_UNSUPPORTED
+ * otherwise.  info->history (optional) receives the FP64 residual of every
+ * outer step; info->cycles the inner cycles.  Synchronises the stream.
+ * The first call allocates the FP64 copy and three full-size workspaces.   */
+int btmg_solve_refined(btmg_problem* p, double* psi64, double rtol, int32_t max_outer,
+                       int32_t inner_cycles, btmg_solve_info* info, void* stream);
+
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * btmg_profile(p, 1) brackets every subsequent kernel launch of the cycle
  * with two CUDA events on the launching stream; btmg_profile_read()

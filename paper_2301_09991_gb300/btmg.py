@@ -28,7 +28,7 @@ EXPORTS = (
     "btmg_num_levels", "btmg_level_info", "btmg_level_quadrature", "btmg_scalar_flux",
     "btmg_apply_operator", "btmg_smooth", "btmg_restrict", "btmg_prolong", "btmg_mg_cycle",
     "btmg_solve", "btmg_error_string", "btmg_last_error", "btmg_profile", "btmg_profile_read",
-    "btmg_launch_count", "btmg_apply_operator_noalloc",
+    "btmg_launch_count", "btmg_apply_operator_noalloc", "btmg_solve_refined",
 )
 PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
 
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
     L.btmg_profile.argtypes = [vp, i32]
     L.btmg_profile_read.argtypes = [vp, dp, i64p, i32]
     L.btmg_launch_count.argtypes = [vp, i64p]
+    L.btmg_solve_refined.argtypes = [vp, vp, C.c_double, i32, i32, C.POINTER(SolveInfo), vp]
     L.btmg_apply_operator_noalloc.argtypes = [i32, i32, C.c_double, C.c_double, i32, i32,
                                               C.POINTER(i32), i32, i32, vp, vp, vp, vp, vp, vp]
     L.btmg_error_string.restype = C.c_char_p
@@ -233,6 +234,24 @@ class Problem:
     def level_shape(self, l):
         lv = self.levels[l]
         return (lv["nd"], lv["ny"], lv["nx"])
+
+    def solve_refined(self, psi64, rtol=1e-10, max_outer=60, inner_cycles=4, stream=None):
+        """Mixed-precision solve: FP64 outer residual, inner cycles in this
+        problem's storage type.  psi64: contiguous CUDA float64 tensor."""
+        torch = _torch()
+        if not (psi64.is_cuda and psi64.dtype == torch.float64 and psi64.is_contiguous()
+                and tuple(psi64.shape) == self.shape):
+            raise ValueError("psi64 must be a contiguous CUDA float64 tensor %s" % (self.shape,))
+        info = SolveInfo()
+        hist = np.zeros(max_outer + 1)
+        info.history = hist.ctypes.data_as(C.POINTER(C.c_double))
+        info.history_len = hist.size
+        rc = load().btmg_solve_refined(self.h, _ptr(psi64), float(rtol), int(max_outer), int(inner_cycles),
+                                       C.byref(info), _stream_ptr(stream))
+        if rc not in (OK, ERR_NOT_CONVERGED):
+            _check(rc)
+        n_outer = int(np.count_nonzero(hist)) if info.rel_resid > 0 else 1
+        return dict(status=rc, cycles=info.cycles, rel_resid=info.rel_resid, history=hist[:max(n_outer, 1)].copy())
 
     def profile(self, enable=True):
         _check(load().btmg_profile(self.h, int(bool(enable))))

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbtmg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["k_pg.cu", "k_mg.cu", "btmg_api.cu", "btmg_noalloc.cu"]
+SOURCES = ["k_pg.cu", "k_mg_f64.cu", "k_mg_f32.cu", "k_mg_lp.cu", "btmg_api.cu", "btmg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"])
+        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
         os.replace(tmp, LIB)
     return LIB
 

@@ -122,7 +122,7 @@ struct btmg_problem {
   int dpc = 1, nchunk = 1, tiles_x = 1, tiles_y = 1;
   bool upscatter = false;
   // device buffers (compute type unless noted)
-  std::vector<void*> d_dir, d_rcoef, d_sig, d_s, d_delta;
+  std::vector<void*> d_dir, d_rcoef, d_sig, d_s, d_delta, d_parent;
   void* d_sigs = nullptr;      // [G][G][npix]
   void* d_src = nullptr;       // [G][npix]
   void* d_b = nullptr;         // [npix]
@@ -134,7 +134,8 @@ struct btmg_problem {
   int n_q_blocks = 0;
   double* d_rn2 = nullptr;  // [G]
   double* d_qn2 = nullptr;  // [G]
-  double* h_pinned = nullptr;  // [2G]
+  double* h_pinned = nullptr;  // [2G + 1]
+  int* d_err = nullptr;        // device error word (bounded waits)
   // captured cycle graphs per group
   std::vector<cudaGraphExec_t> graphs;
   const void* graph_psi = nullptr;
@@ -143,6 +144,17 @@ struct btmg_problem {
   // this stream when the caller passes NULL, ordered after the caller's work
   cudaStream_t own_stream = nullptr;
   cudaEvent_t order_event = nullptr;
+  // host copies of the problem statement (to build the FP64 twin)
+  std::vector<int32_t> h_region;
+  std::vector<double> h_sigma_t, h_sigma_s, h_source;
+  // iterative refinement: FP64 twin (residuals), correction workspaces
+  btmg_problem* twin = nullptr;
+  void* d_zero_src = nullptr;       // [G][npix] zeros (compute type)
+  const void* inner_extra = nullptr;  // [G][nd][ny][nx] anisotropic source or NULL
+  bool zero_src = false;
+  void* d_delta_all = nullptr;      // [G][nd][ny][nx] storage type
+  void* d_extra_all = nullptr;      // [G][nd][ny][nx] compute type
+  double* d_r64 = nullptr;          // [G][nd][ny][nx]
   // per-kernel-class CUDA-event timing (btmg_profile) and launch counting
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_pool;
@@ -160,6 +172,9 @@ void free_graphs(btmg_problem* P) {
   P->graphs.assign(P->G, nullptr);
   P->graph_psi = nullptr;
 }
+
+void destroy(btmg_problem* P);
+int create(const btmg_problem_desc* d, btmg_problem** out);
 
 // --------------------------------------------------------------- launches --
 // Kernel classes reported by btmg_profile_read (BTMG_PROF_*).
@@ -214,6 +229,8 @@ template <typename T, typename C> struct Impl {
     a.half = (C)(P->d.pg_half ? 0.5 : 1.0);
     a.beta = (C)(P->d.pg ? P->d.beta_pg : 1.0);
     a.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
+    a.err = P->d_err;
+    a.extra = P->inner_extra ? reinterpret_cast<const C*>(P->inner_extra) + (size_t)g * L0.n() : nullptr;
     return a;
   }
 
@@ -221,7 +238,8 @@ template <typename T, typename C> struct Impl {
   static cudaError_t source(btmg_problem* P, int g, cudaStream_t s) {
     const size_t npix = P->lev[0].npix();
     cudaError_t e = timed(P, PC_MISC, s, [&] {
-      return launch_source<C>(dptr<C>(P->d_src) + g * npix, dptr<C>(P->d_sigs) + (size_t)g * P->G * npix,
+      const C* src = P->zero_src ? dptr<C>(P->d_zero_src) : dptr<C>(P->d_src);
+      return launch_source<C>(src + g * npix, dptr<C>(P->d_sigs) + (size_t)g * P->G * npix,
                               dptr<C>(P->d_phi_part), P->G, g, P->nchunk, (int)npix, dptr<C>(P->d_b), nullptr,
                               P->d_qn2_part, P->n_q_blocks, s);
     });
@@ -268,6 +286,7 @@ template <typename T, typename C> struct Impl {
       u.fy = A.fy;
       u.fr = A.fr;
       u.fc = A.fc;
+      u.parent = reinterpret_cast<const int*>(P->d_parent[l]);
     }
     return u;
   }
@@ -339,7 +358,9 @@ template <typename T, typename C> struct Impl {
     if (rel) {
       CK(cudaMemcpyAsync(P->h_pinned, P->d_rn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(P->h_pinned + P->G, P->d_qn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(P->h_pinned + 2 * P->G, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (*reinterpret_cast<int*>(P->h_pinned + 2 * P->G)) return fail(BTMG_ERR_TIMEOUT, "a bounded device wait gave up");
       double sr = 0, sq = 0;
       for (int g = 0; g < P->G; ++g) {
         sr += P->h_pinned[g];
@@ -370,7 +391,9 @@ template <typename T, typename C> struct Impl {
   static int read_rel(btmg_problem* P, cudaStream_t s, int g, double* rel_g, double* rel_all) {
     CK(cudaMemcpyAsync(P->h_pinned, P->d_rn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(P->h_pinned + P->G, P->d_qn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(P->h_pinned + 2 * P->G, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (*reinterpret_cast<int*>(P->h_pinned + 2 * P->G)) return fail(BTMG_ERR_TIMEOUT, "a bounded device wait gave up");
     const double w = 4.0 * kPi * P->lev[0].dx * P->lev[0].dy;
     if (rel_g) {
       const double rn = P->h_pinned[g], qn = P->h_pinned[P->G + g];
@@ -463,6 +486,85 @@ template <typename T, typename C> struct Impl {
   }
 };
 
+// Mixed-precision iterative refinement (linear fine operator, pg = 0):
+//   r64 = b - A psi64 in FP64 (the FP64 twin's kernels);
+//   solve A delta = alpha r64 approximately with `inner` low-precision
+//   cycles from delta = 0 (psi stored in the problem's storage type, FP32
+//   accumulation, external source 0, alpha = 1 / rms(r64) so the correction
+//   is O(1) in BF16/FP16 range);  psi64 += delta / alpha.
+template <typename T, typename C>
+int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int inner, btmg_solve_info* info,
+                 cudaStream_t s) {
+  const LevelH& L0 = P->lev[0];
+  const size_t n_all = (size_t)P->G * L0.n(), npix = L0.npix();
+  if (!P->twin) {
+    btmg_problem_desc d2 = P->d;
+    d2.region = P->h_region.data();
+    d2.sigma_t = P->h_sigma_t.data();
+    d2.sigma_s = P->h_sigma_s.data();
+    d2.source = P->h_source.data();
+    d2.psi_dtype = BTMG_F64;
+    d2.max_levels = 1;
+    int rc = create(&d2, &P->twin);
+    if (rc) return rc;
+  }
+  if (!P->d_delta_all) {
+    CK(cudaMalloc(&P->d_delta_all, n_all * sizeof(T)));
+    CK(cudaMalloc(&P->d_extra_all, n_all * sizeof(C)));
+    CK(cudaMalloc(&P->d_r64, n_all * sizeof(double)));
+    CK(cudaMalloc(&P->d_zero_src, (size_t)P->G * npix * sizeof(C)));
+    CK(cudaMemsetAsync(P->d_zero_src, 0, (size_t)P->G * npix * sizeof(C), s));
+  }
+  btmg_problem* Q = P->twin;
+  const double w = 4.0 * kPi * L0.dx * L0.dy;
+  int cycles = 0, status = BTMG_ERR_NOT_CONVERGED;
+  double rel = 0.0;
+  for (int outer = 0; outer <= max_outer; ++outer) {
+    CK(Impl<double, double>::residual_all(Q, psi64, P->d_r64, s));
+    int rc = Impl<double, double>::read_rel(Q, s, 0, nullptr, &rel);
+    if (rc) return rc;
+    if (info && info->history && outer < info->history_len) info->history[outer] = rel;
+    if (std::isnan(rel)) {
+      status = BTMG_ERR_NAN;
+      break;
+    }
+    if (rel <= rtol) {
+      status = BTMG_OK;
+      break;
+    }
+    if (outer == max_outer) break;
+    double rn2 = 0.0;
+    for (int g = 0; g < P->G; ++g) rn2 += Q->h_pinned[g];
+    const double rms = std::sqrt(rn2 / (w * (double)npix * P->G));
+    const double alpha = rms > 0 ? 1.0 / rms : 1.0;
+    CK(launch_scale_to<C>(P->d_r64, dptr<C>(P->d_extra_all), alpha, n_all, s));
+    CK(cudaMemsetAsync(P->d_delta_all, 0, n_all * sizeof(T), s));
+    P->inner_extra = P->d_extra_all;
+    P->zero_src = true;
+    int rc2 = BTMG_OK;
+    for (int k = 0; k < inner && rc2 == BTMG_OK; ++k) rc2 = Impl<T, C>::mg_cycle(P, P->d_delta_all, nullptr, s);
+    P->inner_extra = nullptr;
+    P->zero_src = false;
+    if (rc2) return rc2;
+    cycles += inner;
+    CK(launch_refine_update<T>(psi64, dptr<T>(P->d_delta_all), 1.0 / alpha, n_all, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  if (info) {
+    info->cycles = cycles;
+    info->rel_resid = rel;
+    info->status = status;
+  }
+  return status;
+}
+
+template <typename T, typename C> struct RunRefine {
+  static int run(btmg_problem* P, double* psi64, double rtol, int mo, int inner, btmg_solve_info* info,
+                 cudaStream_t s) {
+    return refine_solve<T, C>(P, psi64, rtol, mo, inner, info, s);
+  }
+};
+
 template <template <typename, typename> class F, typename... Args>
 int dispatch(int dtype, Args&&... args) {
   switch (dtype) {
@@ -539,11 +641,14 @@ template <typename T, typename C> struct RunSmoothUp {
 void destroy(btmg_problem* P) {
   if (!P) return;
   free_graphs(P);
+  if (P->twin) destroy(P->twin);
+  for (void* p : {P->d_zero_src, P->d_delta_all, P->d_extra_all, (void*)P->d_r64})
+    if (p) cudaFree(p);
   for (cudaEvent_t e : P->prof_pool) cudaEventDestroy(e);
-  for (auto v : {&P->d_dir, &P->d_rcoef, &P->d_sig, &P->d_s, &P->d_delta})
+  for (auto v : {&P->d_dir, &P->d_rcoef, &P->d_sig, &P->d_s, &P->d_delta, &P->d_parent})
     for (void* p : *v)
       if (p) cudaFree(p);
-  for (void* p : {P->d_sigs, P->d_src, P->d_b, P->d_phi_part, P->d_psi_tmp, (void*)P->d_norm_part,
+  for (void* p : {P->d_sigs, P->d_src, P->d_b, P->d_phi_part, P->d_psi_tmp, (void*)P->d_norm_part, (void*)P->d_err,
                   (void*)P->d_qn2_part, (void*)P->d_rn2, (void*)P->d_qn2})
     if (p) cudaFree(p);
   if (P->h_pinned) cudaFreeHost(P->h_pinned);
@@ -597,6 +702,10 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
 
   btmg_problem* P = new btmg_problem();
   P->d = *d;
+  P->h_region.assign(d->region, d->region + npix);
+  P->h_sigma_t.assign(d->sigma_t, d->sigma_t + (size_t)d->n_regions * G);
+  P->h_sigma_s.assign(d->sigma_s, d->sigma_s + (size_t)d->n_regions * G * G);
+  P->h_source.assign(d->source, d->source + (size_t)d->n_regions * G);
   P->d.region = nullptr;
   P->d.sigma_t = P->d.sigma_s = P->d.source = nullptr;
   if (!(P->d.beta_pg > 0)) P->d.beta_pg = 3.0;
@@ -687,13 +796,35 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
   P->tiles_x = (F.nx + kTile - 1) / kTile;
   P->tiles_y = (F.ny + kTile - 1) / kTile;
   const int tiles = P->tiles_x * P->tiles_y;
-  int want = (4 * 152 + tiles - 1) / tiles;
-  if (want > F.nd) want = F.nd;
-  int dpc = F.nd / (want < 1 ? 1 : want);
-  if (dpc < 1) dpc = 1;
-  while (F.nd % dpc) --dpc;
-  P->dpc = dpc;
-  P->nchunk = F.nd / dpc;
+  {
+    // Direction chunks: the PG grid is tiles x chunks CTAs; pick the divisor
+    // of nd (at most 64 chunks) whose grid comes closest to whole waves of
+    // resident CTAs, preferring fewer chunks on ties (fewer flux partials).
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int occ = 1;
+    switch (P->dtype) {
+      case BTMG_F64: occ = pg_blocks_per_sm<double, double>(d->pg != 0); break;
+      case BTMG_F32: occ = pg_blocks_per_sm<float, float>(d->pg != 0); break;
+      case BTMG_BF16: occ = pg_blocks_per_sm<__nv_bfloat16, float>(d->pg != 0); break;
+      default: occ = pg_blocks_per_sm<__half, float>(d->pg != 0); break;
+    }
+    const double slots = (double)sms * occ;
+    int best = 1;
+    double best_eff = -1.0;
+    for (int c = 1; c <= F.nd && c <= 64; ++c) {
+      if (F.nd % c) continue;
+      const double items = (double)tiles * c;
+      const double waves = std::ceil(items / slots);
+      const double eff = items / (waves * slots);
+      if (eff > best_eff + 0.02) {
+        best_eff = eff;
+        best = c;
+      }
+    }
+    P->nchunk = best;
+    P->dpc = F.nd / best;
+  }
   P->graphs.assign(G, nullptr);
 
   int rc = BTMG_OK;
@@ -707,6 +838,7 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
   P->d_sig.assign(P->L, nullptr);
   P->d_s.assign(P->L, nullptr);
   P->d_delta.assign(P->L, nullptr);
+  P->d_parent.assign(P->L, nullptr);
   for (int l = 0; l < P->L; ++l) {
     const LevelH& A = P->lev[l];
     if (P->f64) put_dirs<double>(buf, A);
@@ -726,6 +858,14 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
       if (P->f64) put_vals<double>(buf, rc_);
       else put_vals<float>(buf, rc_);
       if ((rc = upload(&P->d_rcoef[l], buf))) return bail(rc);
+      // parent (coarse) direction of every direction, for UpSamp
+      buf.resize(sizeof(int) * A.nd);
+      int* par = reinterpret_cast<int*>(buf.data());
+      for (int n = 0; n < A.nd; ++n) {
+        const int f = n / (A.nr * A.nc), j = (n % (A.nr * A.nc)) / A.nc, i = n % A.nc;
+        par[n] = f * B.nr * B.nc + (j / A.fr) * B.nc + i / A.fc;
+      }
+      if ((rc = upload(&P->d_parent[l], buf))) return bail(rc);
     }
     if (cudaMalloc(&P->d_s[l], A.n() * P->csize) != cudaSuccess) return bail(fail(BTMG_ERR_OOM, "workspace s"));
     if (l >= 1 && cudaMalloc(&P->d_delta[l], A.n() * P->csize) != cudaSuccess)
@@ -747,11 +887,13 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
       cudaMalloc(&P->d_qn2_part, sizeof(double) * P->n_q_blocks) != cudaSuccess ||
       cudaMalloc(&P->d_rn2, sizeof(double) * G) != cudaSuccess ||
       cudaMalloc(&P->d_qn2, sizeof(double) * G) != cudaSuccess ||
-      cudaMallocHost(&P->h_pinned, sizeof(double) * 2 * G) != cudaSuccess)
+      cudaMalloc(&P->d_err, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&P->h_pinned, sizeof(double) * (2 * G + 1)) != cudaSuccess)
     return bail(fail(BTMG_ERR_OOM, "workspace norms"));
   if (cudaStreamCreateWithFlags(&P->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->order_event, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(BTMG_ERR_CUDA, "stream creation"));
+  cudaMemset(P->d_err, 0, sizeof(int));
   cudaMemset(P->d_rn2, 0, sizeof(double) * G);
   cudaMemset(P->d_qn2, 0, sizeof(double) * G);
   *out = P;
@@ -891,6 +1033,14 @@ int btmg_mg_cycle(btmg_problem* p, void* psi, double* rel_resid, void* stream) {
 int btmg_solve(btmg_problem* p, void* psi, double rtol, int32_t max_cycles, btmg_solve_info* info, void* stream) {
   if (!p || !psi || max_cycles < 1) return fail(BTMG_ERR_INVALID_ARG, "bad solve arguments");
   return dispatch<RunSolve>(p->dtype, p, psi, rtol, (int)max_cycles, info, (cudaStream_t)stream);
+}
+
+int btmg_solve_refined(btmg_problem* p, double* psi64, double rtol, int32_t max_outer, int32_t inner_cycles,
+                       btmg_solve_info* info, void* stream) {
+  if (!p || !psi64 || max_outer < 0 || inner_cycles < 1) return fail(BTMG_ERR_INVALID_ARG, "bad refinement arguments");
+  if (p->d.pg) return fail(BTMG_ERR_UNSUPPORTED, "refinement needs the linear (pg = 0) fine operator");
+  cudaStream_t s = (cudaStream_t)stream;
+  return dispatch<RunRefine>(p->dtype, p, psi64, rtol, (int)max_outer, (int)inner_cycles, info, s);
 }
 
 int btmg_profile(btmg_problem* p, int32_t enable) {

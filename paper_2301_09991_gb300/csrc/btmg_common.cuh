@@ -66,6 +66,7 @@ template <typename T, typename C> struct PgArgs {
   T* psi_out;         // PG_JACOBI: updated angular flux, [nd][ny][nx]
   C* r_out;           // PG_RESID: residual b - A psi, [nd][ny][nx]
   const C* b;         // [ny][nx] isotropic right-hand side of this group
+  const C* extra;     // nullable [nd][ny][nx] anisotropic source added to b
   const C* sigt;      // [ny][nx]
   const Dir<C>* dir;  // [nd]
   C* phi_part;        // PG_JACOBI: [nchunk][ny][nx] partial scalar fluxes
@@ -74,6 +75,7 @@ template <typename T, typename C> struct PgArgs {
   C inv_dx, inv_dy, inv_dx2, inv_dy2, dx, dy, dxdy;
   C eps_k, a_kabs, a_ksq, a_r, half, beta;
   Bc bc;
+  int* err;  // set to nonzero when a bounded wait gave up (device word)
 };
 
 // ------------------------------------------------------- upwind Jacobi ----
@@ -90,6 +92,7 @@ template <typename T, typename C> struct UpArgs {
   C* phi_part;         // UP_UPDATE: [nchunk][ny][nx]
   const C* sig;        // [ny][nx] (harmonic averaged on coarse levels)
   const Dir<C>* dir;   // [nd]
+  const int* parent;   // INIT_UPSAMPLE: coarse direction of each direction [nd]
   int nx, ny, nr, nc, nd;
   int nxc, nyc, nrc, ncc;  // coarse dims (INIT_UPSAMPLE)
   int fx, fy, fr, fc;      // coarsening factors to the coarse level (1 or 2)
@@ -101,6 +104,8 @@ template <typename T, typename C> struct UpArgs {
 // All return cudaError_t of the launch.
 template <typename T, typename C>
 cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cudaStream_t s);
+// resident CTAs per SM of the PG kernel (for choosing whole-wave grids)
+template <typename T, typename C> int pg_blocks_per_sm(bool pg);
 template <typename T, typename C>
 cudaError_t launch_upwind(const UpArgs<T, C>& a, int mode, int nchunk, cudaStream_t s);
 
@@ -123,5 +128,11 @@ template <typename C>
 cudaError_t launch_phi_sum(const C* phi_part, int nchunk, int npix, C* phi, cudaStream_t s);
 // out[0] = sum(part[0..n)) (deterministic, one block)
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s);
+// iterative refinement helpers: extra = alpha * r64 (to the compute type);
+// psi64 += delta / alpha (delta in the storage type)
+template <typename C>
+cudaError_t launch_scale_to(const double* r64, C* extra, double alpha, size_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_refine_update(double* psi64, const T* delta, double inv_alpha, size_t n, cudaStream_t s);
 
 }  // namespace btmg

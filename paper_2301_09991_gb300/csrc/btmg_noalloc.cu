@@ -40,7 +40,8 @@ constexpr size_t kOffDir = align256(kOffB + sizeof(float) * kMaxPix);
 constexpr size_t kOffNorm = align256(kOffDir + sizeof(Dir<float>) * kMaxDirs);
 constexpr size_t kOffQ = align256(kOffNorm + sizeof(double) * kMaxNormParts);
 constexpr size_t kOffSums = align256(kOffQ + sizeof(double) * kQBlocks);
-constexpr size_t kScratchBytes = align256(kOffSums + 2 * sizeof(double));
+constexpr size_t kOffErr = kOffSums + 2 * sizeof(double);
+constexpr size_t kScratchBytes = align256(kOffErr + sizeof(int));
 static_assert(kScratchBytes <= BTMG_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
 
 __device__ __align__(256) unsigned char g_scratch[BTMG_NOALLOC_SCRATCH_BYTES];
@@ -145,6 +146,7 @@ extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, do
   double* norm_part = reinterpret_cast<double*>(base + kOffNorm);
   double* q_part = reinterpret_cast<double*>(base + kOffQ);
   double* sums = reinterpret_cast<double*>(base + kOffSums);
+  int* err = reinterpret_cast<int*>(base + kOffErr);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   const double dx = lx / nx, dy = ly / ny;
@@ -184,6 +186,7 @@ extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, do
   a.beta = 1.0f;
   a.bc = Bc{bc[0], bc[1], bc[2], bc[3]};
   a.norm_part = norm_part;
+  a.err = err;
   if (launch_pg<float, float>(a, PG_RESID, pg != 0, nchunk, s) != cudaSuccess) return BTMG_ERR_CUDA;
   if (launch_sum(norm_part, (int)(tiles * nchunk), sums, s) != cudaSuccess) return BTMG_ERR_CUDA;
   return BTMG_OK;

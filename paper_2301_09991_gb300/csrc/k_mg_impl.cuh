@@ -1,4 +1,5 @@
-// k_mg.cu -- the HBM-bound multigrid kernels:
+// k_mg_impl.cuh -- the HBM-bound multigrid kernels (instantiated per
+// storage type in k_mg_f64.cu, k_mg_f32.cu and k_mg_lp.cu):
 //   * upwind Jacobi (Eq. matrix_full with beta = 1, upwind filters of
 //     Sec. 2.4), nu sweeps temporally blocked in one pass: a 32x32 output
 //     tile loads its source and initial correction on the tile extended by
@@ -10,6 +11,7 @@
 //   * restriction (Sec. 2.5): coarse = sum_children p dx dy fine / (P dX dY)
 //   * UpSamp prolongation, scalar-flux partials, source assembly and a
 //     deterministic FP64 sum.
+#pragma once
 #include "btmg_common.cuh"
 
 namespace btmg {
@@ -17,103 +19,171 @@ namespace {
 
 constexpr int UT = 32, UNT = 256, NUMAX = 8;
 
-template <typename T, typename C, int MODE>
-__global__ void __launch_bounds__(UNT) k_upwind(const UpArgs<T, C> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nu = a.nu;
-  const int W = UT + nu;          // loaded region (tile + nu upwind nodes)
-  const int WS = UT + 2 * nu;     // sigma region covering both upwind sides
-  C* D0 = reinterpret_cast<C*>(smem_raw);
-  C* D1 = D0 + W * W;
-  C* S = D1 + W * W;
-  C* SG = S + W * W;
+// Region of one direction: the 32x32 output tile extended by NU nodes on the
+// two upwind sides (W x W), stored with a one-cell zero ring (stride W + 2).
+// Region cell i is owned by thread i mod 256 (slot i / 256): the same cells
+// for every direction, so the next direction's inputs are fetched into
+// registers while the current one sweeps, and each cell keeps its source and
+// inverse diagonal in registers.
+//
+// A sweep updates every owned cell without validity checks: after k sweeps
+// only the cells at least k cells downwind of the region's upwind edge are
+// exact, and the output tile is exactly the set that is exact after NU
+// sweeps.  Cells outside the domain get source 0 and inverse diagonal 0, so
+// they stay 0 (the vacuum halo); on a reflective incoming side the cell next
+// to the boundary is re-copied after every sweep.
+__device__ __forceinline__ float rcp_(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp_(double v) { return 1.0 / v; }
 
-  const int tid = threadIdx.x;
+template <typename T, typename C, int MODE, int NU>
+__global__ void __launch_bounds__(UNT, 4) k_upwind(const UpArgs<T, C> a) {
+  constexpr int W = UT + NU;        // loaded region (tile + NU upwind nodes)
+  constexpr int WP = W + 2;         // stride with the zero ring
+  constexpr int WS = UT + 2 * NU;   // sigma region covering both upwind sides
+  constexpr int NS = (W * W + UNT - 1) / UNT;  // region cells per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* D0 = reinterpret_cast<C*>(smem_raw);
+  C* D1 = D0 + WP * WP;
+  C* SG = D1 + WP * WP;
+
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int tile = blockIdx.x, chunk = blockIdx.y;
   const int x0 = (tile % a.tiles_x) * UT, y0 = (tile / a.tiles_x) * UT;
   const int nx = a.nx, ny = a.ny;
   const size_t npix = (size_t)nx * ny;
 
   for (int i = tid; i < WS * WS; i += UNT) {
-    const int gx = x0 - nu + i % WS, gy = y0 - nu + i / WS;
-    SG[i] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? a.sig[(size_t)gy * nx + gx] : C(0);
+    const int gx = x0 - NU + i % WS, gy = y0 - NU + i / WS;
+    SG[i] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? a.sig[gy * nx + gx] : C(0);
+  }
+  for (int i = tid; i < 2 * WP * WP; i += UNT) D0[i] = C(0);  // zero rings of D0 and D1
+
+  // owned cells: (ly, lx) of slot s, or ly = -1 when the slot is unused
+  int sly[NS], slx[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int i = tid + UNT * s;
+    sly[s] = i < W * W ? i / W : -1;
+    slx[s] = i % W;
   }
 
-  C phi_acc[(UT * UT) / UNT];
+  C phi_acc[4];
 #pragma unroll
-  for (int k = 0; k < (UT * UT) / UNT; ++k) phi_acc[k] = C(0);
+  for (int k = 0; k < 4; ++k) phi_acc[k] = C(0);
 
   const int n_begin = chunk * a.dpc;
   const int n_end = min(n_begin + a.dpc, a.nd);
+
+  // registers holding the next direction's inputs
+  C rs[NS], rd[NS], rp[4];
+  // coarsening factors are 1 or 2: UpSamp indices are shifts
+  const int shx = a.fx >> 1, shy = a.fy >> 1;
+  auto fetch = [&](int n) {
+    const Dir<C> dr = a.dir[n];
+    const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
+    const int ox = x0 - (sxp ? NU : 0), oy = y0 - (syp ? NU : 0);
+    const C* srcn = a.src + (size_t)n * a.src_stride;
+    const C* initn = a.init_mode == INIT_UPSAMPLE ? a.init + (size_t)a.parent[n] * ((size_t)a.nyc * a.nxc)
+                                                  : a.init + (size_t)n * npix;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int gx = ox + slx[s], gy = oy + sly[s];
+      C v = C(0), d = C(0);
+      if (sly[s] >= 0 && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        const int gi = gy * nx + gx;
+        v = srcn[gi];
+        if (a.init_mode == INIT_UPSAMPLE)
+          d = initn[(gy >> shy) * a.nxc + (gx >> shx)];
+        else if (a.init_mode == INIT_SAME)
+          d = initn[gi];
+      }
+      rs[s] = v;
+      rd[s] = d;
+    }
+    if (MODE == UP_UPDATE) {
+      const T* pin_n = a.psi_in + (size_t)n * npix;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int gx = x0 + tx, gy = y0 + ty + 8 * k;
+        rp[k] = (gx < nx && gy < ny) ? (C)Conv<T>::ld(pin_n + gy * nx + gx) : C(0);
+      }
+    }
+  };
+
+  if (n_begin < n_end) fetch(n_begin);
   for (int n = n_begin; n < n_end; ++n) {
     const Dir<C> dr = a.dir[n];
     const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
-    const int ox = x0 - (sxp ? nu : 0), oy = y0 - (syp ? nu : 0);
-    const int sgx = ox - (x0 - nu), sgy = oy - (y0 - nu);  // offset into SG
-    const C* srcn = a.src + (size_t)n * a.src_stride;
-    // parent direction and coarse plane for UpSamp
-    int Np = 0;
-    if (a.init_mode == INIT_UPSAMPLE) {
-      const int per = a.nr * a.nc, f = n / per, j = (n % per) / a.nc, i = n % a.nc;
-      Np = f * a.nrc * a.ncc + (j / a.fr) * a.ncc + i / a.fc;
+    const int ox = x0 - (sxp ? NU : 0), oy = y0 - (syp ? NU : 0);
+    const int sgx = sxp ? 0 : NU, sgy = syp ? 0 : NU;  // offset into SG
+    const C ax = dr.ax, ay = dr.ay, axy = dr.ax + dr.ay;
+    // reflective incoming sides touching this region: column / row to re-copy
+    const bool rx_ = sxp ? (a.bc.xlo == BC_REFLECTIVE && ox < 0) : (a.bc.xhi == BC_REFLECTIVE && ox + W > nx);
+    const bool ry_ = syp ? (a.bc.ylo == BC_REFLECTIVE && oy < 0) : (a.bc.yhi == BC_REFLECTIVE && oy + W > ny);
+    const int bxl = sxp ? -ox : nx - 1 - ox;  // local column of the boundary node
+    const int byl = syp ? -oy : ny - 1 - oy;
+    const int hxl = sxp ? bxl - 1 : bxl + 1;  // its upwind halo cell
+    const int hyl = syp ? byl - 1 : byl + 1;
+    C sreg[NS], ireg[NS];
+    __syncthreads();  // previous direction finished with D0/D1
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int gx = ox + slx[s], gy = oy + sly[s];
+      const bool in = sly[s] >= 0 && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+      sreg[s] = rs[s];
+      ireg[s] = in ? rcp_(axy + SG[(sly[s] + sgy) * WS + slx[s] + sgx]) : C(0);
+      if (sly[s] >= 0) D0[(sly[s] + 1) * WP + slx[s] + 1] = rd[s];
     }
-    __syncthreads();  // previous direction finished with D0/D1/S
-    for (int i = tid; i < W * W; i += UNT) {
-      const int lx = i % W, ly = i / W;
-      const int gx = ox + lx, gy = oy + ly;
-      C s = C(0), d = C(0);
-      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-        const size_t gi = (size_t)gy * nx + gx;
-        s = srcn[gi];
-        if (a.init_mode == INIT_UPSAMPLE)
-          d = a.init[((size_t)Np * a.nyc + gy / a.fy) * a.nxc + gx / a.fx];
-        else if (a.init_mode == INIT_SAME)
-          d = a.init[(size_t)n * npix + gi];
-      }
-      S[i] = s;
-      D0[i] = d;
-    }
+    C pin[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pin[k] = rp[k];
+    if (n + 1 < n_end) fetch(n + 1);  // in flight during the sweeps
     __syncthreads();
     C* Dold = D0;
     C* Dnew = D1;
-    const C ax = dr.ax, ay = dr.ay;
-    const bool zx = sxp ? (a.bc.xlo == BC_VACUUM) : (a.bc.xhi == BC_VACUUM);
-    const bool zy = syp ? (a.bc.ylo == BC_VACUUM) : (a.bc.yhi == BC_VACUUM);
-    for (int k = 1; k <= nu; ++k) {
-      const int xlo = sxp ? k : 0, xhi = sxp ? W : W - k;
-      const int ylo = syp ? k : 0, yhi = syp ? W : W - k;
-      for (int i = tid; i < W * W; i += UNT) {
-        const int lx = i % W, ly = i / W;
-        if (lx < xlo || lx >= xhi || ly < ylo || ly >= yhi) continue;
-        const int gx = ox + lx, gy = oy + ly;
-        if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
-        const C self = Dold[i];
-        const bool bx = sxp ? (gx == 0) : (gx == nx - 1);  // upwind neighbour outside
-        const bool by = syp ? (gy == 0) : (gy == ny - 1);
-        const C ux = bx ? (zx ? C(0) : self) : Dold[i + (sxp ? -1 : 1)];
-        const C uy = by ? (zy ? C(0) : self) : Dold[i + (syp ? -W : W)];
-        const C sg = SG[(ly + sgy) * WS + lx + sgx];
-        Dnew[i] = (S[i] + ax * ux + ay * uy) / (ax + ay + sg);
+    const int ux = sxp ? -1 : 1, uy = syp ? -WP : WP;
+    auto recopy = [&](C* D) {  // reflective halo = adjacent interior node
+      if (rx_)
+        for (int ly = tid; ly < W; ly += UNT)
+          if (hxl >= 0 && hxl < W && bxl >= 0 && bxl < W) D[(ly + 1) * WP + hxl + 1] = D[(ly + 1) * WP + bxl + 1];
+      if (ry_)
+        for (int lx = tid; lx < W; lx += UNT)
+          if (hyl >= 0 && hyl < W && byl >= 0 && byl < W) D[(hyl + 1) * WP + lx + 1] = D[(byl + 1) * WP + lx + 1];
+    };
+    if (rx_ || ry_) {
+      recopy(Dold);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 1; k <= NU; ++k) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (sly[s] < 0) continue;
+        const int i = (sly[s] + 1) * WP + slx[s] + 1;
+        Dnew[i] = (sreg[s] + ax * Dold[i + ux] + ay * Dold[i + uy]) * ireg[s];
       }
       __syncthreads();
+      if (rx_ || ry_) {
+        recopy(Dnew);
+        __syncthreads();
+      }
       C* t = Dold;
       Dold = Dnew;
       Dnew = t;
     }
-    // store the tile
-    const int tx0 = sxp ? nu : 0, ty0 = syp ? nu : 0;
+    // store the tile: column tx, rows ty + 8k
+    const int tx0 = sxp ? NU : 0, ty0 = syp ? NU : 0;
 #pragma unroll
-    for (int k = 0; k < (UT * UT) / UNT; ++k) {
-      const int i = tid + k * UNT;
-      const int rx = i % UT, ry = i / UT;
+    for (int k = 0; k < 4; ++k) {
+      const int rx = tx, ry = ty + 8 * k;
       const int gx = x0 + rx, gy = y0 + ry;
       if (gx >= nx || gy >= ny) continue;
-      const C d = Dold[(ry + ty0) * W + rx + tx0];
-      const size_t gi = (size_t)n * npix + (size_t)gy * nx + gx;
+      const C d = Dold[(ry + ty0 + 1) * WP + rx + tx0 + 1];
+      const size_t gi = (size_t)n * npix + (size_t)(gy * nx + gx);
       if (MODE == UP_CORR) {
         a.delta_out[gi] = d;
       } else {
-        const C pn = Conv<T>::ld(a.psi_in + gi) + d;
+        const C pn = pin[k] + d;
         Conv<T>::st(a.psi_out + gi, pn);
         phi_acc[k] += dr.w * stored<T, C>(pn);
       }
@@ -122,9 +192,8 @@ __global__ void __launch_bounds__(UNT) k_upwind(const UpArgs<T, C> a) {
   if (MODE == UP_UPDATE) {
     C* ph = a.phi_part + (size_t)chunk * npix;
 #pragma unroll
-    for (int k = 0; k < (UT * UT) / UNT; ++k) {
-      const int i = tid + k * UNT;
-      const int gx = x0 + i % UT, gy = y0 + i / UT;
+    for (int k = 0; k < 4; ++k) {
+      const int gx = x0 + tx, gy = y0 + ty + 8 * k;
       if (gx < nx && gy < ny) ph[(size_t)gy * nx + gx] = phi_acc[k];
     }
   }
@@ -251,22 +320,35 @@ inline int grid_for(size_t total, int threads) {
   return g < 1 ? 1 : (int)g;
 }
 
-template <typename T, typename C, int MODE>
-cudaError_t launch_up_mode(const UpArgs<T, C>& a, int nchunk, cudaStream_t s) {
-  if (a.nu < 0 || a.nu > NUMAX) return cudaErrorInvalidValue;
-  const int W = UT + a.nu, WS = UT + 2 * a.nu;
-  const size_t smem = (3 * (size_t)W * W + (size_t)WS * WS) * sizeof(C);
+template <typename T, typename C, int MODE, int NU>
+cudaError_t launch_up_nu(const UpArgs<T, C>& a, int nchunk, cudaStream_t s) {
+  constexpr int WP = UT + NU + 2, WS = UT + 2 * NU;
+  const size_t smem = (2 * (size_t)WP * WP + (size_t)WS * WS) * sizeof(C);
   static bool attr_set = false;
   if (!attr_set) {
-    const size_t maxs = (3 * (size_t)(UT + NUMAX) * (UT + NUMAX) + (size_t)(UT + 2 * NUMAX) * (UT + 2 * NUMAX)) * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(k_upwind<T, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxs);
+    cudaError_t e = cudaFuncSetAttribute(k_upwind<T, C, MODE, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int tiles_y = (a.ny + UT - 1) / UT;
   dim3 grid(a.tiles_x * tiles_y, nchunk);
-  k_upwind<T, C, MODE><<<grid, UNT, smem, s>>>(a);
+  k_upwind<T, C, MODE, NU><<<grid, UNT, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T, typename C, int MODE>
+cudaError_t launch_up_mode(const UpArgs<T, C>& a, int nchunk, cudaStream_t s) {
+  switch (a.nu) {
+    case 1: return launch_up_nu<T, C, MODE, 1>(a, nchunk, s);
+    case 2: return launch_up_nu<T, C, MODE, 2>(a, nchunk, s);
+    case 3: return launch_up_nu<T, C, MODE, 3>(a, nchunk, s);
+    case 4: return launch_up_nu<T, C, MODE, 4>(a, nchunk, s);
+    case 5: return launch_up_nu<T, C, MODE, 5>(a, nchunk, s);
+    case 6: return launch_up_nu<T, C, MODE, 6>(a, nchunk, s);
+    case 7: return launch_up_nu<T, C, MODE, 7>(a, nchunk, s);
+    case 8: return launch_up_nu<T, C, MODE, 8>(a, nchunk, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -315,27 +397,37 @@ cudaError_t launch_phi_sum(const C* part, int nchunk, int npix, C* phi, cudaStre
   return cudaGetLastError();
 }
 
+namespace {
+template <typename C>
+__global__ void k_scale_to(const double* __restrict__ r64, C* __restrict__ out, double alpha, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (C)(alpha * r64[i]);
+}
+template <typename T>
+__global__ void k_refine_update(double* __restrict__ psi64, const T* __restrict__ delta, double inv_alpha, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    psi64[i] += (double)Conv<T>::ld(delta + i) * inv_alpha;
+}
+
+}  // namespace
+
+template <typename C>
+cudaError_t launch_scale_to(const double* r64, C* out, double alpha, size_t n, cudaStream_t s) {
+  k_scale_to<C><<<grid_for(n, 256), 256, 0, s>>>(r64, out, alpha, n);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_refine_update(double* psi64, const T* delta, double inv_alpha, size_t n, cudaStream_t s) {
+  k_refine_update<T><<<grid_for(n, 256), 256, 0, s>>>(psi64, delta, inv_alpha, n);
+  return cudaGetLastError();
+}
+
+#ifdef BTMG_MG_DEFINE_COMMON
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s) {
   k_sum<<<1, 1024, 0, s>>>(part, n, out);
   return cudaGetLastError();
 }
+#endif
 
-#define INST_TC(T, C)                                                                                     \
-  template cudaError_t launch_upwind<T, C>(const UpArgs<T, C>&, int, int, cudaStream_t);                \
-  template cudaError_t launch_phi_partial<T, C>(const T*, C*, const Dir<C>*, int, int, int, int, int, cudaStream_t);
-INST_TC(double, double)
-INST_TC(float, float)
-INST_TC(__nv_bfloat16, float)
-INST_TC(__half, float)
-#define INST_C(C)                                                                                          \
-  template cudaError_t launch_restrict<C>(const C*, C*, const C*, int, int, int, int, int, int, int, int, int, int, \
-                                          int, int, cudaStream_t);                                         \
-  template cudaError_t launch_prolong<C>(const C*, C*, int, int, int, int, int, int, int, int, int, int, int, int, \
-                                         cudaStream_t);                                                    \
-  template cudaError_t launch_source<C>(const C*, const C*, const C*, int, int, int, int, C*, C*, double*, int, \
-                                        cudaStream_t);                                                     \
-  template cudaError_t launch_phi_sum<C>(const C*, int, int, C*, cudaStream_t);
-INST_C(double)
-INST_C(float)
 
 }  // namespace btmg

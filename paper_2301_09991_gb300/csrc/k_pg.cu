@@ -17,255 +17,567 @@
 // Dependency depth: D needs k on +-2, k needs Psi_x on +-2, Psi_x needs psi
 // on +-2, hence the 6-node halo.  Derived fields (Psi_x, Psi_y, k_x, k_y)
 // take the value of the nearest interior node outside the domain.
+//
+// Every pass is register blocked with a compile-time work mapping: a thread
+// produces 4 consecutive x outputs (x passes, two 16-byte shared loads) or a
+// 4-wide block of 2 or 4 rows (y passes).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "btmg_common.cuh"
 
 namespace btmg {
 namespace {
 
+// ---- TMA / mbarrier helpers (inline PTX, sm_90+ async copy engine) -------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after a few million polls (about a second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 constexpr int TX = 32, TY = 32, NT = 256;
-constexpr int W6 = TX + 12, H6 = TY + 12;
-constexpr int W4 = TX + 8, H4 = TY + 8;
-constexpr int W2 = TX + 4, H2 = TY + 4;
+constexpr int W6 = TX + 12, H6 = TY + 12;  // 44
+constexpr int W4 = TX + 8, H4 = TY + 8;    // 40
+constexpr int W2 = TX + 4, H2 = TY + 4;    // 36
 
-template <typename C> struct St {
-  // quadratic ConvFEM 1D stencils (offsets -2..2), h = 1
-  __device__ __forceinline__ static C m1(int k) {
-    return k == 2 ? C(24.0 / 30.0) : ((k == 1 || k == 3) ? C(4.0 / 30.0) : C(-1.0 / 30.0));
-  }
-  __device__ __forceinline__ static C d1(int k) {
-    return k == 0 ? C(1.0 / 12.0) : k == 1 ? C(-8.0 / 12.0) : k == 2 ? C(0) : k == 3 ? C(8.0 / 12.0) : C(-1.0 / 12.0);
-  }
-  __device__ __forceinline__ static C s1(int k) {
-    return k == 2 ? C(30.0 / 12.0) : ((k == 1 || k == 3) ? C(-16.0 / 12.0) : C(1.0 / 12.0));
-  }
-};
+// quadratic ConvFEM 1D stencils (offsets -2..2), h = 1
+template <typename C> __device__ __forceinline__ C M1(int k) {
+  return k == 2 ? C(24.0 / 30.0) : ((k == 1 || k == 3) ? C(4.0 / 30.0) : C(-1.0 / 30.0));
+}
+template <typename C> __device__ __forceinline__ C S1(int k) {
+  return k == 2 ? C(30.0 / 12.0) : ((k == 1 || k == 3) ? C(-16.0 / 12.0) : C(1.0 / 12.0));
+}
+// d1 in difference form on the values at offsets -2, -1, +1, +2
+template <typename C> __device__ __forceinline__ C D1(C p0, C p1, C p3, C p4) {
+  return C(8.0 / 12.0) * (p3 - p1) - C(1.0 / 12.0) * (p4 - p0);
+}
 
-template <typename C> constexpr size_t pg_smem_elems() {
-  return (size_t)H6 * W6 + 2 * (size_t)H4 * W6 + 2 * (size_t)H4 * W4 + 2 * (size_t)H2 * W2 +
-         5 * (size_t)TY * W2;
+// 4 consecutive elements from / to 16-byte aligned shared memory
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&o)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&o)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+}
+// 4 consecutive elements starting on an 8-byte boundary (two pairs)
+__device__ __forceinline__ void ld2x2(const float* p, float (&o)[4]) {
+  const float2 a = *reinterpret_cast<const float2*>(p), b = *reinterpret_cast<const float2*>(p + 2);
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+__device__ __forceinline__ void ld2x2(const double* p, double (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+// 8 consecutive elements (two aligned quads)
+template <typename C> __device__ __forceinline__ void ld8(const C* p, C (&o)[8]) {
+  C a[4], b[4];
+  ld4(p, a);
+  ld4(p + 4, b);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o[k] = a[k], o[k + 4] = b[k];
 }
 
 template <typename C> __device__ __forceinline__ C cmin(C a, C b) { return a < b ? a : b; }
+// FP32: the fast division intrinsic (2 ulp; the PG coefficients and the
+// Jacobi step tolerate it); FP64: exact division.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float cabs_(float v) { return fabsf(v); }
 __device__ __forceinline__ double cabs_(double v) { return fabs(v); }
 
-template <typename T, typename C, int MODE, bool PGON>
-__global__ void __launch_bounds__(NT) k_pg(const PgArgs<T, C> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* P = reinterpret_cast<C*>(smem_raw);  // psi_ext, origin (-6,-6), H6 x W6
-  C* A = P + H6 * W6;                     // d1_x psi, rows -6.., cols -4.. (H6 x W4)
-  C* B = A + H4 * W6;                     // d1_y psi, rows -4.., cols -6.. (H4 x W6)
-  C* Px = B + H4 * W6;                    // origin (-4,-4)
-  C* Py = Px + H4 * W4;
-  C* Kx = Py + H4 * W4;                   // origin (-2,-2)
-  C* Ky = Kx + H2 * W2;
-  C* U1 = Ky + H2 * W2;                   // rows 0.., cols -2..
-  C* U2 = U1 + TY * W2;
-  C* V1 = U2 + TY * W2;
-  C* V2 = V1 + TY * W2;
-  C* V3 = V2 + TY * W2;
-  C* Tx = B;   // m1_y Psi_x (rows -2.., cols -4..), B is dead by then
-  C* Ty = U1;  // m1_y Psi_y, U1/U2 are not live yet
-  C* W1 = A;   // m1_y P (rows 0.., cols -2..), A is dead after stage 2
+// Shared-memory layout in elements; every array starts on a 4-element
+// boundary and every row stride (44, 40, 36) is a multiple of 4.
+//   P   two H6 x PS tiles (double buffer), origin (-6,-8): psi   stages 0-5
+//       (the pointer P used below is offset by 2: P[r * PS + c] is (r-6, c-6))
+//   A   H6 x W4, origin (-6,-4): d1_x P                   stages 1-2
+//   B   H4 x W6, origin (-4,-6): d1_y P                   stages 1-2
+//   Px, Py  H4 x W4, origin (-4,-4)                       stages 2-5
+//   Kx, Ky  H2 x W2, origin (-2,-2)                       stages 3-5
+//   Tx, Ty  H2 x W4, origin (-2,-4): m1_y Psi  (in the dead A/B region)  stage 3
+//   V1..V3  TY x W2, origin (0,-2): s1_y pass  (in the dead A/B region)  stages 4-5
+//   U1, U2, W1  TY x W2, origin (0,-2): m1_y pass (after Ky)          stages 4-5
+constexpr int PS = 48;                 // row stride of the staged psi tile
+constexpr int PBUF = H6 * PS;          // one staged tile: rows -6.., cols -8..
+constexpr int OFF_P = 0;               // two tiles (double buffer)
+constexpr int OFF_A = OFF_P + 2 * PBUF;
+constexpr int OFF_B = OFF_A + H6 * W4;
+constexpr int OFF_PX = OFF_B + H4 * W6;
+constexpr int OFF_PY = OFF_PX + H4 * W4;
+constexpr int OFF_KX = OFF_PY + H4 * W4;
+constexpr int OFF_KY = OFF_KX + H2 * W2;
+constexpr int S4N = TY * W2;
+constexpr int OFF_U = OFF_KY + H2 * W2;
+constexpr int OFF_TX = OFF_A;
+constexpr int OFF_TY = OFF_A + H2 * W4;
+constexpr int OFF_V = OFF_A;
+constexpr int PG_ELEMS = OFF_U + 3 * S4N;
+static_assert(OFF_TY + H2 * W4 <= OFF_PX, "T arrays must stay inside the dead A/B region");
+static_assert(OFF_V + 3 * S4N <= OFF_PX, "V arrays must stay inside the dead A/B region");
+static_assert((PBUF * 4) % 128 == 0, "TMA destinations must be 128-byte aligned");
+static_assert(OFF_A % 4 == 0 && OFF_B % 4 == 0 && OFF_PX % 4 == 0 && OFF_PY % 4 == 0 && OFF_KX % 4 == 0 &&
+                  OFF_KY % 4 == 0 && OFF_U % 4 == 0 && OFF_TY % 4 == 0 && S4N % 4 == 0,
+              "16-byte alignment of the shared arrays");
+
+// 8 consecutive elements from the staged psi tile (8-byte aligned for FP32)
+__device__ __forceinline__ void ldp8(const float* p, float (&o)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 v = *reinterpret_cast<const float2*>(p + 2 * k);
+    o[2 * k] = v.x, o[2 * k + 1] = v.y;
+  }
+}
+__device__ __forceinline__ void ldp8(const double* p, double (&o)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 v = *reinterpret_cast<const double2*>(p + 2 * k);
+    o[2 * k] = v.x, o[2 * k + 1] = v.y;
+  }
+}
+
+template <typename T, typename C, int MODE, bool PGON, bool TMA>
+__global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
+    k_pg(const PgArgs<T, C> a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  C* P = sm + OFF_P + 2;  // current staged tile (+2: origin -6 in x)
+  C* A = sm + OFF_A;
+  C* B = sm + OFF_B;
+  C* Px = sm + OFF_PX;
+  C* Py = sm + OFF_PY;
+  C* Kx = sm + OFF_KX;
+  C* Ky = sm + OFF_KY;
+  C* Tx = sm + OFF_TX;
+  C* Ty = sm + OFF_TY;
+  C* U1 = sm + OFF_U;
+  C* U2 = U1 + S4N;
+  C* W1 = U2 + S4N;
+  C* V1 = sm + OFF_V;
+  C* V2 = V1 + S4N;
+  C* V3 = V2 + S4N;
   __shared__ double red[NT / 32];
+  __shared__ __align__(8) uint64_t bars[2];
 
   const int tid = threadIdx.x;
   const int tile = blockIdx.x, chunk = blockIdx.y;
   const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
   const int nx = a.nx, ny = a.ny;
   const size_t npix = (size_t)nx * ny;
-  using S = St<C>;
+  // tiles whose 4-halo leaves the domain need the derived-field fill passes
+  const bool edge = x0 < 4 || y0 < 4 || x0 + TX + 4 > nx || y0 + TY + 4 > ny;
 
   double nrm = 0.0;
-  C phi_acc[(TX * TY) / NT];
+  C phi_acc[4];
 #pragma unroll
-  for (int k = 0; k < (TX * TY) / NT; ++k) phi_acc[k] = C(0);
+  for (int k = 0; k < 4; ++k) phi_acc[k] = C(0);
+  // stage-5 mapping: one row, four consecutive columns
+  const int r5 = tid >> 3, c5 = (tid & 7) * 4;
 
   const int n_begin = chunk * a.dpc;
   const int n_end = min(n_begin + a.dpc, a.nd);
+  constexpr uint32_t TILE_BYTES = (uint32_t)(PBUF * sizeof(C));
+  uint32_t phase = 0;  // bit b: parity of buffer b's next completion
+  if (TMA) {
+    if (tid == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0 && n_begin < n_end) {
+      mbar_expect_tx(&bars[0], TILE_BYTES);
+      tma_load_3d(sm + OFF_P, &tmap, &bars[0], x0 - 8, y0 - 6, n_begin);
+    }
+  }
   for (int n = n_begin; n < n_end; ++n) {
     const Dir<C> dr = a.dir[n];
     const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
     const T* psin = a.psi + (size_t)n * npix;
-    // ---- stage 0: psi with halo ------------------------------------------
-    // Every derivative term (Psi_x, Psi_y, R, k, f^{k-Diff}) is unchanged by
-    // a constant shift of psi (all those filters sum to zero), so the PG
-    // variant stages psi - c with c = psi at the tile origin: the separable
-    // intermediates then round relative to the local variation of psi, not
-    // to its magnitude.  sigma_t psi and the update use the unshifted psi.
-    const C c0 = PGON ? Conv<T>::ld(psin + (size_t)y0 * nx + x0) : C(0);
-    for (int i = tid; i < H6 * W6; i += NT) {
-      const int gx = x0 + (i % W6) - 6, gy = y0 + (i / W6) - 6;
-      C v;
-      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny)
-        v = Conv<T>::ld(psin + (size_t)gy * nx + gx);
-      else if (halo_is_zero(a.bc, gx, gy, nx, ny, sxp, syp))
-        v = C(0);
-      else
-        v = Conv<T>::ld(psin + (size_t)clampi(gy, 0, ny - 1) * nx + clampi(gx, 0, nx - 1));
-      P[i] = v - c0;
+    // ---- stage 0: psi with halo -------------------------------------------
+    if (TMA) {
+      // The tile of direction n was requested one direction earlier; request
+      // the next one into the other buffer (released by the barrier that
+      // ended the previous direction), then wait for this one.
+      const int b = (n - n_begin) & 1;
+      if (tid == 0 && n + 1 < n_end) {
+        fence_proxy_async();
+        mbar_expect_tx(&bars[b ^ 1], TILE_BYTES);
+        tma_load_3d(sm + OFF_P + (b ^ 1) * PBUF, &tmap, &bars[b ^ 1], x0 - 8, y0 - 6, n + 1);
+      }
+      const bool got = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
+      phase ^= 1u << b;
+      if (!__syncthreads_and(got)) {  // copy engine stalled: flag it and leave together
+        if (tid == 0) {
+          atomicExch(a.err, 1);
+          if (n + 1 < n_end) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u);
+        }
+        return;
+      }
+      P = sm + OFF_P + b * PBUF + 2;
+      // out-of-domain cells arrive as 0 (the vacuum incoming halo); the
+      // others take the nearest interior node (boundary tiles only)
+      if (x0 < 6 || y0 < 6 || x0 + TX + 6 > nx || y0 + TY + 6 > ny) {
+        for (int i = tid; i < H6 * W6; i += NT) {
+          const int r = i / W6, c = i % W6;
+          const int gx = x0 + c - 6, gy = y0 + r - 6;
+          if ((gx < 0 || gx >= nx || gy < 0 || gy >= ny) && !halo_is_zero(a.bc, gx, gy, nx, ny, sxp, syp))
+            P[r * PS + c] = P[(clampi(gy, 0, ny - 1) - y0 + 6) * PS + clampi(gx, 0, nx - 1) - x0 + 6];
+        }
+        __syncthreads();
+      }
+    } else {
+#pragma unroll 2
+      for (int i = tid; i < H6 * W6; i += NT) {
+        const int gx = x0 + (i % W6) - 6, gy = y0 + (i / W6) - 6;
+        C v;
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+          v = Conv<T>::ld(psin + (size_t)gy * nx + gx);
+        else if (halo_is_zero(a.bc, gx, gy, nx, ny, sxp, syp))
+          v = C(0);
+        else
+          v = Conv<T>::ld(psin + (size_t)clampi(gy, 0, ny - 1) * nx + clampi(gx, 0, nx - 1));
+        P[(i / W6) * PS + i % W6] = v;
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    // Every derivative term is unchanged by a constant shift of psi (all
+    // those filters sum to zero).  The derivative passes are evaluated in
+    // difference form; the product terms of stages 4 and 5 use psi - c0
+    // (c0 = psi at the tile origin), so they round relative to the local
+    // variation of psi, not to its magnitude.
+    const C c0 = PGON ? P[6 * PS + 6] : C(0);
     if constexpr (PGON) {
-    // ---- stage 1: derivative passes first, in difference form ------------
-    //   A = d1_x P on rows -6.., cols -4..;  B = d1_y P on rows -4.., cols -6..
-    for (int i = tid; i < H6 * W4; i += NT) {
-      const int ry = i / W4, rx = i % W4;
-      const C* p = P + ry * W6 + rx;
-      A[i] = C(8.0 / 12.0) * (p[3] - p[1]) - C(1.0 / 12.0) * (p[4] - p[0]);
-    }
-    for (int i = tid; i < H4 * W6; i += NT) {
-      const int ry = i / W6, cx = i % W6;
-      const C* p = P + ry * W6 + cx;
-      B[i] = C(8.0 / 12.0) * (p[3 * W6] - p[W6]) - C(1.0 / 12.0) * (p[4 * W6] - p[0]);
-    }
-    __syncthreads();
-    // ---- stage 2: mass passes -> Psi_x = m1_y A / dx, Psi_y = m1_x B / dy -
-    for (int i = tid; i < H4 * W4; i += NT) {
-      const int ry = i / W4, rx = i % W4;
-      C sx = C(0), sy = C(0);
+      // ---- stage 1: derivative passes in difference form --------------------
+      // A = d1_x P: items (row, quad); B = d1_y P: items (row pair, quad)
+      {
+        constexpr int NA = H6 * (W4 / 4), NB = (H4 / 2) * (W6 / 4);
 #pragma unroll
-      for (int u = 0; u < 5; ++u) {
-        sx += S::m1(u) * A[(ry + u) * W4 + rx];
-        sy += S::m1(u) * B[ry * W6 + rx + u];
-      }
-      Px[i] = sx * a.inv_dx;
-      Py[i] = sy * a.inv_dy;
-    }
-    __syncthreads();
-    // derived-field halo: nearest interior node
-    for (int i = tid; i < H4 * W4; i += NT) {
-      const int gx = x0 + (i % W4) - 4, gy = y0 + (i / W4) - 4;
-      if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
-        const int j = (clampi(gy, 0, ny - 1) - y0 + 4) * W4 + (clampi(gx, 0, nx - 1) - x0 + 4);
-        Px[i] = Px[j];
-        Py[i] = Py[j];
-      }
-    }
-    __syncthreads();
-    // ---- stage 3: R_x, R_y and k_x, k_y on the 2-halo region ------------
-    for (int i = tid; i < H2 * W4; i += NT) {
-      const int ry = i / W4, cx = i % W4;
-      C tx = C(0), ty = C(0);
+        for (int it = tid; it < NA + NB; it += NT) {
+          if (it < NA) {
+            const int r = it / (W4 / 4), c = (it % (W4 / 4)) * 4;
+            // inputs at (r-6, c-6 .. c+1) = tile columns c+2 .. c+9: three
+            // aligned quads starting at tile column c (P - 2 is the tile base)
+            C q0[4], q1[4], q2[4], o[4];
+            ld4(P - 2 + r * PS + c, q0);
+            ld4(P - 2 + r * PS + c + 4, q1);
+            ld4(P - 2 + r * PS + c + 8, q2);
+            const C p[8] = {q0[2], q0[3], q1[0], q1[1], q1[2], q1[3], q2[0], q2[1]};
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        tx += S::m1(v) * Px[(ry + v) * W4 + cx];
-        ty += S::m1(v) * Py[(ry + v) * W4 + cx];
-      }
-      Tx[i] = tx;
-      Ty[i] = ty;
-    }
-    __syncthreads();
-    {
-      const C amu = cabs_(dr.mu), anu = cabs_(dr.nu);
-      const C kxmax = a.dx * amu, kymax = a.dy * anu;
-      for (int i = tid; i < H2 * W2; i += NT) {
-        const int ry = i / W2, rx = i % W2;
-        C mx = C(0), my = C(0);
+            for (int k = 0; k < 4; ++k) o[k] = D1<C>(p[k], p[k + 1], p[k + 3], p[k + 4]);
+            st4(A + r * W4 + c, o);
+          } else {
+            const int j = it - NA;
+            const int r = (j / (W6 / 4)) * 2, c = (j % (W6 / 4)) * 4;
+            C p[6][4];
 #pragma unroll
-        for (int u = 0; u < 5; ++u) {
-          mx += S::m1(u) * Tx[ry * W4 + rx + u];
-          my += S::m1(u) * Ty[ry * W4 + rx + u];
+            for (int v = 0; v < 6; ++v) ld2x2(P + (r + v) * PS + c, p[v]);
+            C o0[4], o1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              o0[k] = D1<C>(p[0][k], p[1][k], p[3][k], p[4][k]);
+              o1[k] = D1<C>(p[1][k], p[2][k], p[4][k], p[5][k]);
+            }
+            st4(B + r * W6 + c, o0);
+            st4(B + (r + 1) * W6 + c, o1);
+          }
         }
-        const C pxc = Px[(ry + 2) * W4 + rx + 2], pyc = Py[(ry + 2) * W4 + rx + 2];
-        const C Rx = a.a_r * dr.mu * (mx - pxc), Ry = a.a_r * dr.nu * (my - pyc);
-        const C kxa = a.a_kabs * cabs_(Rx) * a.dx / (a.eps_k + cabs_(pxc));
-        const C kya = a.a_kabs * cabs_(Ry) * a.dy / (a.eps_k + cabs_(pyc));
-        const C kxs = a.a_ksq * Rx * Rx * a.dx / (a.eps_k + amu * pxc * pxc);
-        const C kys = a.a_ksq * Ry * Ry * a.dy / (a.eps_k + anu * pyc * pyc);
-        Kx[i] = cmin(cmin(kxmax, kxa), kxs);
-        Ky[i] = cmin(cmin(kymax, kya), kys);
       }
-    }
-    __syncthreads();
-    for (int i = tid; i < H2 * W2; i += NT) {
-      const int gx = x0 + (i % W2) - 2, gy = y0 + (i / W2) - 2;
-      if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
-        const int j = (clampi(gy, 0, ny - 1) - y0 + 2) * W2 + (clampi(gx, 0, nx - 1) - x0 + 2);
-        Kx[i] = Kx[j];
-        Ky[i] = Ky[j];
-      }
-    }
-    __syncthreads();
-    // ---- stage 4: y passes of the k-Diff terms ---------------------------
-    for (int i = tid; i < TY * W2; i += NT) {
-      const int ry = i / W2, rx = i % W2;
-      C u1 = C(0), u2 = C(0), w1 = C(0), v1 = C(0), v2 = C(0), v3 = C(0);
+      __syncthreads();
+      // ---- stage 2: mass passes: Psi_x = m1_y A / dx, Psi_y = m1_x B / dy ---
+      {
+        constexpr int NX = (H4 / 2) * (W4 / 4), NY = H4 * (W4 / 4);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const C kx = Kx[(ry + v) * W2 + rx], ky = Ky[(ry + v) * W2 + rx];
-        const C p = P[(ry + 4 + v) * W6 + rx + 4];
-        u1 += S::m1(v) * kx * p;
-        u2 += S::m1(v) * kx;
-        w1 += S::m1(v) * p;
-        v1 += S::s1(v) * ky * p;
-        v2 += S::s1(v) * ky;
-        v3 += S::s1(v) * p;
+        for (int it = tid; it < NX + NY; it += NT) {
+          if (it < NX) {
+            const int r = (it / (W4 / 4)) * 2, c = (it % (W4 / 4)) * 4;
+            C p[6][4];
+#pragma unroll
+            for (int v = 0; v < 6; ++v) ld4(A + (r + v) * W4 + c, p[v]);
+            C o0[4], o1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              C s0 = C(0), s1 = C(0);
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                s0 += M1<C>(v) * p[v][k];
+                s1 += M1<C>(v) * p[v + 1][k];
+              }
+              o0[k] = s0 * a.inv_dx;
+              o1[k] = s1 * a.inv_dx;
+            }
+            st4(Px + r * W4 + c, o0);
+            st4(Px + (r + 1) * W4 + c, o1);
+          } else {
+            const int j = it - NX;
+            const int r = j / (W4 / 4), c = (j % (W4 / 4)) * 4;
+            C p[8], o[4];
+            ld8(B + r * W6 + c, p);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              C s = C(0);
+#pragma unroll
+              for (int u = 0; u < 5; ++u) s += M1<C>(u) * p[k + u];
+              o[k] = s * a.inv_dy;
+            }
+            st4(Py + r * W4 + c, o);
+          }
+        }
       }
-      U1[i] = u1;
-      U2[i] = u2;
-      W1[i] = w1;
-      V1[i] = v1;
-      V2[i] = v2;
-      V3[i] = v3;
-    }
-    __syncthreads();
+      __syncthreads();
+      if (edge) {  // derived-field halo: nearest interior node
+        for (int i = tid; i < H4 * W4; i += NT) {
+          const int gx = x0 + (i % W4) - 4, gy = y0 + (i / W4) - 4;
+          if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
+            const int j = (clampi(gy, 0, ny - 1) - y0 + 4) * W4 + (clampi(gx, 0, nx - 1) - x0 + 4);
+            Px[i] = Px[j];
+            Py[i] = Py[j];
+          }
+        }
+        __syncthreads();
+      }
+      // ---- stage 3: T = m1_y Psi (4-row blocks), then k on the 2-halo -------
+      {
+        constexpr int NT3 = (H2 / 4) * (W4 / 4);  // per array
+#pragma unroll
+        for (int it = tid; it < 2 * NT3; it += NT) {
+          const bool isx = it < NT3;
+          const int j = isx ? it : it - NT3;
+          const int r = (j / (W4 / 4)) * 4, c = (j % (W4 / 4)) * 4;
+          const C* src = isx ? Px : Py;
+          C* dst = isx ? Tx : Ty;
+          C p[8][4];
+#pragma unroll
+          for (int v = 0; v < 8; ++v) ld4(src + (r + v) * W4 + c, p[v]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            C o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              C s = C(0);
+#pragma unroll
+              for (int v = 0; v < 5; ++v) s += M1<C>(v) * p[q + v][k];
+              o[k] = s;
+            }
+            st4(dst + (r + q) * W4 + c, o);
+          }
+        }
+      }
+      __syncthreads();
+      {
+        const C amu = cabs_(dr.mu), anu = cabs_(dr.nu);
+        const C kxmax = a.dx * amu, kymax = a.dy * anu;
+        const C cx = a.a_r * dr.mu, cy = a.a_r * dr.nu;
+        constexpr int NK = H2 * (W2 / 4);
+#pragma unroll
+        for (int it = tid; it < NK; it += NT) {
+          const int r = it / (W2 / 4), c = (it % (W2 / 4)) * 4;
+          C tx[8], ty[8];
+          ld8(Tx + r * W4 + c, tx);
+          ld8(Ty + r * W4 + c, ty);
+          C kxo[4], kyo[4], pxv[4], pyv[4];
+          ld2x2(Px + (r + 2) * W4 + c + 2, pxv);
+          ld2x2(Py + (r + 2) * W4 + c + 2, pyv);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            C mx = C(0), my = C(0);
+#pragma unroll
+            for (int u = 0; u < 5; ++u) {
+              mx += M1<C>(u) * tx[k + u];
+              my += M1<C>(u) * ty[k + u];
+            }
+            const C pxc = pxv[k], pyc = pyv[k];
+            const C Rx = cx * (mx - pxc), Ry = cy * (my - pyc);
+            const C kxa = fdiv(a.a_kabs * cabs_(Rx) * a.dx, a.eps_k + cabs_(pxc));
+            const C kya = fdiv(a.a_kabs * cabs_(Ry) * a.dy, a.eps_k + cabs_(pyc));
+            const C kxs = fdiv(a.a_ksq * Rx * Rx * a.dx, a.eps_k + amu * pxc * pxc);
+            const C kys = fdiv(a.a_ksq * Ry * Ry * a.dy, a.eps_k + anu * pyc * pyc);
+            kxo[k] = cmin(cmin(kxmax, kxa), kxs);
+            kyo[k] = cmin(cmin(kymax, kya), kys);
+          }
+          st4(Kx + r * W2 + c, kxo);
+          st4(Ky + r * W2 + c, kyo);
+        }
+      }
+      __syncthreads();
+      if (edge) {
+        for (int i = tid; i < H2 * W2; i += NT) {
+          const int gx = x0 + (i % W2) - 2, gy = y0 + (i / W2) - 2;
+          if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
+            const int j = (clampi(gy, 0, ny - 1) - y0 + 2) * W2 + (clampi(gx, 0, nx - 1) - x0 + 2);
+            Kx[i] = Kx[j];
+            Ky[i] = Ky[j];
+          }
+        }
+        __syncthreads();
+      }
+      // ---- stage 4: y passes of the k-Diff terms (2-row blocks) -------------
+      //   x group: u1 = m1_y (k_x P), u2 = m1_y k_x, w1 = m1_y P
+      //   y group: v1 = s1_y (k_y P), v2 = s1_y k_y, v3 = s1_y P
+      {
+        constexpr int N4 = (TY / 2) * (W2 / 4);  // per group
+#pragma unroll
+        for (int it = tid; it < 2 * N4; it += NT) {
+          const bool xg = it < N4;
+          const int j = xg ? it : it - N4;
+          const int r = (j / (W2 / 4)) * 2, c = (j % (W2 / 4)) * 4;
+          const C* K = xg ? Kx : Ky;
+          C kk[6][4], pp[6][4];
+#pragma unroll
+          for (int v = 0; v < 6; ++v) {
+            ld4(K + (r + v) * W2 + c, kk[v]);
+            ld2x2(P + (r + 4 + v) * PS + c + 4, pp[v]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pp[v][k] -= c0;
+          }
+          C* d0 = xg ? U1 : V1;
+          C* d1 = xg ? U2 : V2;
+          C* d2 = xg ? W1 : V3;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            C o0[4], o1[4], o2[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              C s0 = C(0), s1 = C(0), s2 = C(0);
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                const C w = xg ? M1<C>(v) : S1<C>(v);
+                s0 += w * kk[q + v][k] * pp[q + v][k];
+                s1 += w * kk[q + v][k];
+                s2 += w * pp[q + v][k];
+              }
+              o0[k] = s0;
+              o1[k] = s1;
+              o2[k] = s2;
+            }
+            st4(d0 + (r + q) * W2 + c, o0);
+            st4(d1 + (r + q) * W2 + c, o1);
+            st4(d2 + (r + q) * W2 + c, o2);
+          }
+        }
+      }
+      __syncthreads();
     }  // PGON
-    // ---- stage 5: assemble r on the tile ---------------------------------
-    T* outn = (MODE == PG_JACOBI) ? a.psi_out + (size_t)n * npix : nullptr;
-    C* rn = (MODE == PG_RESID) ? a.r_out + (size_t)n * npix : nullptr;
-#pragma unroll
-    for (int k = 0; k < (TX * TY) / NT; ++k) {
-      const int i = tid + k * NT;
-      const int ry = i / TX, rx = i % TX;
-      const int gx = x0 + rx, gy = y0 + ry;
-      if (gx >= nx || gy >= ny) continue;
-      const C pc = P[(ry + 6) * W6 + rx + 6];  // psi - c0
-      const size_t gi = (size_t)gy * nx + gx;
-      const C psi_c = Conv<T>::ld(psin + gi);  // unshifted psi of this node
-      const C sig = a.sigt[gi];
-      C Apsi;
+    // ---- stage 5: assemble r on the tile (one row, four columns) -----------
+    {
+      const int ry = r5, rx = c5;
+      const int gy = y0 + ry;
+      C fkp[4], fp[4], fk[4], gkp[4], gp[4], gk[4];
       if constexpr (PGON) {
-        C fkp = C(0), fp = C(0), fk = C(0), gkp = C(0), gp = C(0), gk = C(0);
+        C u1[8], u2[8], w1[8], v1[8], v2[8], v3[8];
+        ld8(U1 + ry * W2 + rx, u1);
+        ld8(U2 + ry * W2 + rx, u2);
+        ld8(W1 + ry * W2 + rx, w1);
+        ld8(V1 + ry * W2 + rx, v1);
+        ld8(V2 + ry * W2 + rx, v2);
+        ld8(V3 + ry * W2 + rx, v3);
 #pragma unroll
-        for (int u = 0; u < 5; ++u) {
-          fkp += S::s1(u) * U1[ry * W2 + rx + u];
-          fp += S::s1(u) * W1[ry * W2 + rx + u];
-          fk += S::s1(u) * U2[ry * W2 + rx + u];
-          gkp += S::m1(u) * V1[ry * W2 + rx + u];
-          gp += S::m1(u) * V3[ry * W2 + rx + u];
-          gk += S::m1(u) * V2[ry * W2 + rx + u];
+        for (int k = 0; k < 4; ++k) {
+          fkp[k] = fp[k] = fk[k] = gkp[k] = gp[k] = gk[k] = C(0);
+#pragma unroll
+          for (int u = 0; u < 5; ++u) {
+            fkp[k] += S1<C>(u) * u1[k + u];
+            fk[k] += S1<C>(u) * u2[k + u];
+            fp[k] += S1<C>(u) * w1[k + u];
+            gkp[k] += M1<C>(u) * v1[k + u];
+            gk[k] += M1<C>(u) * v2[k + u];
+            gp[k] += M1<C>(u) * v3[k + u];
+          }
         }
-        const C kxc = Kx[(ry + 2) * W2 + rx + 2], kyc = Ky[(ry + 2) * W2 + rx + 2];
-        const C Dx = (fkp + kxc * fp - pc * fk) * a.inv_dx2;
-        const C Dy = (gkp + kyc * gp - pc * gk) * a.inv_dy2;
-        Apsi = dr.mu * Px[(ry + 4) * W4 + rx + 4] + dr.nu * Py[(ry + 4) * W4 + rx + 4] +
-               a.half * (Dx + Dy) + sig * psi_c;
-      } else {
-        // upwind filters of Sec. 2.4 (one-sided by the signs of mu and nu)
-        const C ux = sxp ? (pc - P[(ry + 6) * W6 + rx + 5]) : (P[(ry + 6) * W6 + rx + 7] - pc);
-        const C uy = syp ? (pc - P[(ry + 5) * W6 + rx + 6]) : (P[(ry + 7) * W6 + rx + 6] - pc);
-        Apsi = dr.mu * ux * a.inv_dx + dr.nu * uy * a.inv_dy + sig * psi_c;
       }
-      const C r = a.b[gi] - Apsi;
-      if (MODE == PG_RESID) {
-        rn[gi] = r;
-        nrm += (double)dr.w * (double)a.dxdy * (double)r * (double)r;
-      } else {
-        const C d = a.beta * (dr.ax + dr.ay + sig);
-        const C pn = psi_c + r / d;
-        Conv<T>::st(outn + gi, pn);
-        phi_acc[k] += dr.w * stored<T, C>(pn);
+      C pcv[4], pxv[4], pyv[4], kxv[4], kyv[4];
+      ld2x2(P + (ry + 6) * PS + rx + 6, pcv);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pcv[k] -= c0;  // psi - c0
+      if constexpr (PGON) {
+        ld4(Px + (ry + 4) * W4 + rx + 4, pxv);
+        ld4(Py + (ry + 4) * W4 + rx + 4, pyv);
+        ld2x2(Kx + (ry + 2) * W2 + rx + 2, kxv);
+        ld2x2(Ky + (ry + 2) * W2 + rx + 2, kyv);
       }
+      C nrm_dir = C(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int gx = x0 + rx + k;
+        if (gx >= nx || gy >= ny) continue;
+        const C pc = pcv[k];
+        const size_t gi = (size_t)gy * nx + gx;
+        const C psi_c = Conv<T>::ld(psin + gi);  // unshifted psi of this node
+        const C sig = a.sigt[gi];
+        C Apsi;
+        if constexpr (PGON) {
+          const C Dx = (fkp[k] + kxv[k] * fp[k] - pc * fk[k]) * a.inv_dx2;
+          const C Dy = (gkp[k] + kyv[k] * gp[k] - pc * gk[k]) * a.inv_dy2;
+          Apsi = dr.mu * pxv[k] + dr.nu * pyv[k] + a.half * (Dx + Dy) + sig * psi_c;
+        } else {
+          // upwind filters of Sec. 2.4 (one-sided by the signs of mu and nu)
+          const C ux = sxp ? (pc - P[(ry + 6) * PS + rx + k + 5]) : (P[(ry + 6) * PS + rx + k + 7] - pc);
+          const C uy = syp ? (pc - P[(ry + 5) * PS + rx + k + 6]) : (P[(ry + 7) * PS + rx + k + 6] - pc);
+          Apsi = dr.mu * ux * a.inv_dx + dr.nu * uy * a.inv_dy + sig * psi_c;
+        }
+        const C r = a.b[gi] + (a.extra ? a.extra[(size_t)n * npix + gi] : C(0)) - Apsi;
+        if (MODE == PG_RESID) {
+          a.r_out[(size_t)n * npix + gi] = r;
+          nrm_dir += r * r;
+        } else {
+          const C d = a.beta * (dr.ax + dr.ay + sig);
+          const C pn = psi_c + fdiv(r, d);
+          Conv<T>::st(a.psi_out + (size_t)n * npix + gi, pn);
+          phi_acc[k] += dr.w * stored<T, C>(pn);
+        }
+      }
+      // one FP64 accumulation per direction (the FP64 pipe is narrow)
+      if (MODE == PG_RESID) nrm += (double)dr.w * (double)nrm_dir;
     }
     __syncthreads();
   }
   if (MODE == PG_JACOBI) {
     C* ph = a.phi_part + (size_t)chunk * npix;
+    const int gy = y0 + r5;
 #pragma unroll
-    for (int k = 0; k < (TX * TY) / NT; ++k) {
-      const int i = tid + k * NT;
-      const int gx = x0 + i % TX, gy = y0 + i / TX;
+    for (int k = 0; k < 4; ++k) {
+      const int gx = x0 + c5 + k;
       if (gx < nx && gy < ny) ph[(size_t)gy * nx + gx] = phi_acc[k];
     }
   } else {
@@ -275,26 +587,89 @@ __global__ void __launch_bounds__(NT) k_pg(const PgArgs<T, C> a) {
     if (tid == 0) {
       double s = 0.0;
       for (int w = 0; w < NT / 32; ++w) s += red[w];
-      a.norm_part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+      a.norm_part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s * (double)a.dxdy;
     }
   }
 }
 
-template <typename T, typename C, int MODE, bool PGON>
-cudaError_t launch_mode(const PgArgs<T, C>& a, int nchunk, cudaStream_t s) {
-  // the upwind variant only needs the psi tile
-  const size_t smem = (PGON ? pg_smem_elems<C>() : (size_t)H6 * W6) * sizeof(C);
+template <typename C, bool PGON> constexpr size_t smem_bytes() {
+  // the upwind variant only needs the staged psi tiles
+  return (PGON ? (size_t)PG_ELEMS : (size_t)(2 * PBUF)) * sizeof(C);
+}
+
+// 3D tensor map over psi (x, y, direction) with a 48 x 44 x 1 box; the box
+// starts at x0 - 8, a multiple of 8 elements (the innermost coordinate of a
+// TMA copy must be 16-byte aligned).  Used when psi is stored in the compute
+// type, its base is 16-byte aligned and a row is a multiple of 16 bytes.
+// The encoder is a driver entry point; it is looked up through the runtime
+// so that the library does not link against the driver library.
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+template <typename T, typename C> bool make_tmap(CUtensorMap* m, const PgArgs<T, C>& a) {
+  if (sizeof(T) != sizeof(C)) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
+  if (!encode) return false;
+  const size_t es = sizeof(T);
+  if ((reinterpret_cast<uintptr_t>(a.psi) % 16) != 0 || ((size_t)a.nx * es) % 16 != 0) return false;
+  const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nd};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.nx * es, (cuuint64_t)a.nx * a.ny * es};
+  const cuuint32_t box[3] = {(cuuint32_t)PS, (cuuint32_t)H6, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return encode(m, dt, 3, const_cast<T*>(a.psi), dims, strides, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T, typename C, int MODE, bool PGON, bool TMA>
+cudaError_t launch_variant(const PgArgs<T, C>& a, const CUtensorMap& tm, int nchunk, cudaStream_t s) {
+  constexpr size_t smem = smem_bytes<C, PGON>();
   static bool attr_set = false;  // per instantiation, once per process
   if (!attr_set) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_pg<T, C, MODE, PGON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_pg<T, C, MODE, PGON, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int tiles_y = (a.ny + TY - 1) / TY;
   dim3 grid(a.tiles_x * tiles_y, nchunk);
-  k_pg<T, C, MODE, PGON><<<grid, NT, smem, s>>>(a);
+  k_pg<T, C, MODE, PGON, TMA><<<grid, NT, smem, s>>>(a, tm);
   return cudaGetLastError();
+}
+
+template <typename T, typename C, int MODE, bool PGON>
+cudaError_t launch_mode(const PgArgs<T, C>& a, int nchunk, cudaStream_t s) {
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  if constexpr (sizeof(T) == sizeof(C)) {
+    if (make_tmap(&tm, a)) return launch_variant<T, C, MODE, PGON, true>(a, tm, nchunk, s);
+  }
+  return launch_variant<T, C, MODE, PGON, false>(a, tm, nchunk, s);
+}
+
+template <typename T, typename C, int MODE, bool PGON> int occupancy_mode() {
+  constexpr size_t smem = smem_bytes<C, PGON>();
+  if (cudaFuncSetAttribute(k_pg<T, C, MODE, PGON, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 1;
+  int blocks = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_pg<T, C, MODE, PGON, false>, NT, smem) !=
+      cudaSuccess)
+    return 1;
+  return blocks < 1 ? 1 : blocks;
 }
 
 }  // namespace
@@ -308,11 +683,18 @@ cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cuda
                           : launch_mode<T, C, PG_JACOBI, false>(a, nchunk, s);
 }
 
+template <typename T, typename C> int pg_blocks_per_sm(bool pg) {
+  return pg ? occupancy_mode<T, C, PG_JACOBI, true>() : occupancy_mode<T, C, PG_JACOBI, false>();
+}
+
 template cudaError_t launch_pg<double, double>(const PgArgs<double, double>&, int, bool, int, cudaStream_t);
 template cudaError_t launch_pg<float, float>(const PgArgs<float, float>&, int, bool, int, cudaStream_t);
-template cudaError_t launch_pg<__nv_bfloat16, float>(const PgArgs<__nv_bfloat16, float>&, int, bool, int, cudaStream_t);
+template cudaError_t launch_pg<__nv_bfloat16, float>(const PgArgs<__nv_bfloat16, float>&, int, bool, int,
+                                                     cudaStream_t);
 template cudaError_t launch_pg<__half, float>(const PgArgs<__half, float>&, int, bool, int, cudaStream_t);
-
-int pg_tile() { return TX; }
+template int pg_blocks_per_sm<double, double>(bool);
+template int pg_blocks_per_sm<float, float>(bool);
+template int pg_blocks_per_sm<__nv_bfloat16, float>(bool);
+template int pg_blocks_per_sm<__half, float>(bool);
 
 }  // namespace btmg
