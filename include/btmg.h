@@ -178,6 +178,30 @@ int btmg_solve(btmg_problem* p, void* psi, double rtol, int32_t max_cycles,
 int btmg_solve_refined(btmg_problem* p, double* psi64, double rtol, int32_t max_outer,
                        int32_t inner_cycles, btmg_solve_info* info, void* stream);
 
+/* ---- Learned correction: U-net (no counterpart in the paper's solver;
+ * the paper's "U-net" is the multigrid cycle itself with fixed weights).
+ * A small U-net (4 levels, 16/32/48/64 channels, 3x3 convolutions, average
+ * pooling, nearest upsampling with skip concatenation; 196k parameters) run
+ * and trained by the library's own BF16 kernels (tensor-core implicit-GEMM
+ * convolutions, FP32 accumulation, FP32 master weights, Adam).
+ * Inputs are device FP32 [N][H][W][in_channels] (H, W multiples of 8),
+ * outputs device FP32 [N][H][W].  Parameters are one flat FP32 vector:
+ * per layer weights [cout][ks][ks][cin] then biases [cout].               */
+typedef struct btmg_unet btmg_unet;
+int btmg_unet_create(int32_t in_channels, uint64_t seed, btmg_unet** out);
+int btmg_unet_destroy(btmg_unet* u);
+int btmg_unet_num_params(const btmg_unet* u, int64_t* n);
+int btmg_unet_get_params(const btmg_unet* u, float* host, int64_t n);
+int btmg_unet_set_params(btmg_unet* u, const float* host, int64_t n);
+int btmg_unet_get_grads(const btmg_unet* u, float* host, int64_t n);
+int btmg_unet_forward(btmg_unet* u, const float* x, float* y, int32_t n, int32_t h, int32_t w, void* stream);
+/* One Adam step on the mean squared error against target [N][H][W]
+ * (lr = 0: gradients only).  loss (nullable, host) receives the loss before
+ * the step; when non-NULL the call synchronises the stream.               */
+int btmg_unet_train_step(btmg_unet* u, const float* x, const float* target, int32_t n, int32_t h, int32_t w,
+                         float lr, double* loss, void* stream);
+const char* btmg_unet_last_error(void);
+
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * btmg_profile(p, 1) brackets every subsequent kernel launch of the cycle
  * with two CUDA events on the launching stream; btmg_profile_read()

@@ -29,6 +29,9 @@ EXPORTS = (
     "btmg_apply_operator", "btmg_smooth", "btmg_restrict", "btmg_prolong", "btmg_mg_cycle",
     "btmg_solve", "btmg_error_string", "btmg_last_error", "btmg_profile", "btmg_profile_read",
     "btmg_launch_count", "btmg_apply_operator_noalloc", "btmg_solve_refined",
+    "btmg_unet_create", "btmg_unet_destroy", "btmg_unet_num_params", "btmg_unet_get_params",
+    "btmg_unet_set_params", "btmg_unet_get_grads", "btmg_unet_forward", "btmg_unet_train_step",
+    "btmg_unet_last_error",
 )
 PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
 
@@ -109,6 +112,16 @@ def load(build_if_missing: bool = True):
     L.btmg_solve_refined.argtypes = [vp, vp, C.c_double, i32, i32, C.POINTER(SolveInfo), vp]
     L.btmg_apply_operator_noalloc.argtypes = [i32, i32, C.c_double, C.c_double, i32, i32,
                                               C.POINTER(i32), i32, i32, vp, vp, vp, vp, vp, vp]
+    L.btmg_unet_create.argtypes = [i32, C.c_uint64, C.POINTER(vp)]
+    L.btmg_unet_destroy.argtypes = [vp]
+    L.btmg_unet_num_params.argtypes = [vp, i64p]
+    fp = C.POINTER(C.c_float)
+    L.btmg_unet_get_params.argtypes = [vp, fp, C.c_int64]
+    L.btmg_unet_set_params.argtypes = [vp, fp, C.c_int64]
+    L.btmg_unet_get_grads.argtypes = [vp, fp, C.c_int64]
+    L.btmg_unet_forward.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+    L.btmg_unet_train_step.argtypes = [vp, vp, vp, i32, i32, i32, C.c_float, dp, vp]
+    L.btmg_unet_last_error.restype = C.c_char_p
     L.btmg_error_string.restype = C.c_char_p
     L.btmg_error_string.argtypes = [C.c_int]
     L.btmg_last_error.restype = C.c_char_p
@@ -341,3 +354,64 @@ class Problem:
         if hist is not None:
             out["history"] = hist[:min(info.cycles, hist.size)].copy()
         return out
+
+
+def _ucheck(rc):
+    if rc != OK:
+        raise BtmgError(rc, load().btmg_unet_last_error().decode())
+
+
+class UNet:
+    """The learned-correction U-net held on the GPU (see btmg.h)."""
+
+    def __init__(self, in_channels=3, seed=1):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("btmg needs a CUDA device (sm_103a); there is no CPU path")
+        h = C.c_void_p()
+        _ucheck(load().btmg_unet_create(int(in_channels), int(seed), C.byref(h)))
+        self.h = h
+        self.in_channels = in_channels
+        n = C.c_int64()
+        _ucheck(load().btmg_unet_num_params(self.h, C.byref(n)))
+        self.nparam = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().btmg_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        a = np.zeros(self.nparam, dtype=np.float32)
+        _ucheck(load().btmg_unet_get_params(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), self.nparam))
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        _ucheck(load().btmg_unet_set_params(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), self.nparam))
+
+    def get_grads(self):
+        a = np.zeros(self.nparam, dtype=np.float32)
+        _ucheck(load().btmg_unet_get_grads(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), self.nparam))
+        return a
+
+    def forward(self, x, stream=None):
+        """x: CUDA float32 [N][H][W][in_channels] -> CUDA float32 [N][H][W]."""
+        n, h, w, c = x.shape
+        y = _torch().empty((n, h, w), dtype=_torch().float32, device="cuda")
+        _ucheck(load().btmg_unet_forward(self.h, _ptr(x.contiguous()), _ptr(y), n, h, w, _stream_ptr(stream)))
+        return y
+
+    def train_step(self, x, target, lr, want_loss=True, stream=None):
+        n, h, w, c = x.shape
+        loss = C.c_double(0.0)
+        _ucheck(load().btmg_unet_train_step(self.h, _ptr(x.contiguous()), _ptr(target.contiguous()), n, h, w,
+                                            float(lr), C.byref(loss) if want_loss else None,
+                                            _stream_ptr(stream)))
+        return loss.value if want_loss else None
