@@ -202,6 +202,25 @@ int btmg_unet_train_step(btmg_unet* u, const float* x, const float* target, int3
                          float lr, double* loss, void* stream);
 const char* btmg_unet_last_error(void);
 
+/* Attach a trained U-net as a learned correction after every `every`-th
+ * cycle of btmg_solve and of the inner cycles of btmg_solve_refined (NULL
+ * detaches).  The step: rho = sum_n p_n r_n of the cycle's input residual;
+ * features (rho / rms(rho), log(sigma_t dx + 1e-3) / 4, sigma_s / sigma_t)
+ * on a canvas padded to multiples of 8; the U-net predicts the scalar-flux
+ * error left by the cycle in units of rms(rho); psi_n += omega * rms(rho) *
+ * prediction / (4 pi) for every direction.  A step is kept only when the
+ * next cycle's input residual is below the previous cycle's; otherwise the
+ * iterate before the step is restored and the cycle redone without it
+ * (plain multigrid is the fallback).  Solves with a learned correction run
+ * their cycles eagerly (no graph).  The U-net must outlive its use.        */
+int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every, float omega);
+int btmg_learn_stats(const btmg_problem* p, int64_t* accepted, int64_t* rejected);
+/* Canvas size of the learned features (ny, nx rounded up to multiples of 8). */
+int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8);
+/* Features of the learned step for psi (training pairs): feat device FP32
+ * [G][H8][W8][3], scale device FP32 [G] = rms(rho) of each group.          */
+int btmg_learn_features(btmg_problem* p, const void* psi, float* feat, float* scale, void* stream);
+
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * btmg_profile(p, 1) brackets every subsequent kernel launch of the cycle
  * with two CUDA events on the launching stream; btmg_profile_read()

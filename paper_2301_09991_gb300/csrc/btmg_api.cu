@@ -155,6 +155,19 @@ struct btmg_problem {
   void* d_delta_all = nullptr;      // [G][nd][ny][nx] storage type
   void* d_extra_all = nullptr;      // [G][nd][ny][nx] compute type
   double* d_r64 = nullptr;          // [G][nd][ny][nx]
+  // learned correction (btmg_set_learned)
+  btmg_unet* learned = nullptr;
+  int learn_every = 1;
+  float learn_omega = 1.f;
+  int H8 = 8, W8 = 8;
+  void* d_rho_part = nullptr;   // [G][nchunk][npix] compute type
+  float* d_feat = nullptr;      // [H8][W8][3]
+  float* d_dimg = nullptr;      // [H8][W8]
+  float* d_lscale = nullptr;    // [1]
+  double* d_lsum = nullptr;
+  double* d_lpart = nullptr;    // [n_q_blocks]
+  void* d_backup = nullptr;     // one group of psi (storage type)
+  int64_t learn_accepted = 0, learn_rejected = 0;
   // per-kernel-class CUDA-event timing (btmg_profile) and launch counting
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_pool;
@@ -231,6 +244,7 @@ template <typename T, typename C> struct Impl {
     a.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
     a.err = P->d_err;
     a.extra = P->inner_extra ? reinterpret_cast<const C*>(P->inner_extra) + (size_t)g * L0.n() : nullptr;
+    a.rho_part = nullptr;
     return a;
   }
 
@@ -293,22 +307,29 @@ template <typename T, typename C> struct Impl {
 
   // One sawtooth cycle of group g (Fig. multi_grid_it); the scalar-flux
   // partials of every group must describe the current psi on entry and
-  // describe the updated psi on exit.
-  static cudaError_t cycle_group(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
+  // describe the updated psi on exit.  Part A evaluates the residual of the
+  // input (and its norm, and the residual moment when a learned correction
+  // is attached); part B does the rest of the cycle.
+  static cudaError_t cycle_part_a(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
     cudaError_t e;
-    const int L = P->L;
     const LevelH& L0 = P->lev[0];
     // 1. r_1 = b - A psi  (Eq. Petrov), weighted norm
     if ((e = source(P, g, s)) != cudaSuccess) return e;
     PgArgs<T, C> a = pg_args(P, g, psi_g);
     a.r_out = dptr<C>(P->d_s[0]);
     a.norm_part = P->d_norm_part;
+    if (P->learned) a.rho_part = dptr<C>(P->d_rho_part) + (size_t)g * P->nchunk * L0.npix();
     if ((e = timed(P, PC_PG_RESID, s, [&] { return launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s); })) !=
         cudaSuccess)
       return e;
     const int nblk = P->tiles_x * P->tiles_y * P->nchunk;
-    if ((e = timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, nblk, P->d_rn2 + g, s); })) != cudaSuccess)
-      return e;
+    return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, nblk, P->d_rn2 + g, s); });
+  }
+
+  static cudaError_t cycle_part_b(btmg_problem* P, T* psi_g, int g, cudaStream_t s, bool learn = false) {
+    cudaError_t e;
+    const int L = P->L;
+    const LevelH& L0 = P->lev[0];
     // 2. restriction to every coarser level
     for (int l = 0; l + 1 < L; ++l) {
       const LevelH &A = P->lev[l], &B = P->lev[l + 1];
@@ -343,12 +364,97 @@ template <typename T, typename C> struct Impl {
           cudaSuccess)
         return e;
     }
+    // learned correction (before the post-smoothing sweep, which damps the
+    // small-scale part of the prediction)
+    if (learn && learn_step(P, dptr<T>(P->d_psi_tmp), g, s) != BTMG_OK) return cudaErrorUnknown;
     // 6. fine PG Jacobi sweep with diagonal beta d (Eq. matrix_full)
     if ((e = source(P, g, s)) != cudaSuccess) return e;
     PgArgs<T, C> j = pg_args(P, g, dptr<T>(P->d_psi_tmp));
     j.psi_out = psi_g;
     j.phi_part = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
     return timed(P, PC_PG_JACOBI, s, [&] { return launch_pg<T, C>(j, PG_JACOBI, P->d.pg != 0, P->nchunk, s); });
+  }
+
+  static cudaError_t cycle_group(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
+    cudaError_t e = cycle_part_a(P, psi_g, g, s);
+    if (e != cudaSuccess) return e;
+    return cycle_part_b(P, psi_g, g, s);
+  }
+
+  // The learned step inside a cycle of group g: features from the residual
+  // moment of the cycle's input, U-net prediction of the scalar-flux error,
+  // psi_n += omega * delta / (4 pi) for every direction.
+  static int learn_step(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
+    const LevelH& L0 = P->lev[0];
+    const size_t npix = L0.npix();
+    CK(launch_learn_features<C>(dptr<C>(P->d_rho_part) + (size_t)g * P->nchunk * npix, P->nchunk,
+                                dptr<C>(P->d_sig[0]) + (size_t)g * npix,
+                                dptr<C>(P->d_sigs) + ((size_t)g * P->G + g) * npix, L0.dx, L0.nx, L0.ny, P->W8,
+                                P->H8, P->d_lsum, P->d_lpart, P->n_q_blocks, P->d_feat, P->d_lscale, s));
+    if (int rc = btmg_unet_forward(P->learned, P->d_feat, P->d_dimg, 1, P->H8, P->W8, s))
+      return fail(rc, std::string("learned correction: ") + btmg_unet_last_error());
+    CK(launch_learn_apply<T, C>(psi_g, L0.nd, L0.nx, L0.ny, P->W8, P->d_dimg, P->d_lscale, P->learn_omega,
+                                dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * npix, s));
+    return BTMG_OK;
+  }
+
+  // One cycle of group g with the learned step and its acceptance test: a
+  // cycle with the learned step is kept only if the residual of its output
+  // is below the residual of its input; otherwise its input is restored and
+  // it is redone as a plain cycle (plain multigrid is the fallback), and the
+  // learned step pauses for a few cycles.  Returns the relative residual of
+  // the input of the cycle it ran.
+  struct LearnState {
+    bool pending = false;
+    double prev = 1e300;    // residual of the previous cycle's input
+    double ratio = 1.0;     // running contraction factor of plain cycles
+    int plain_seen = 0;
+    int cooldown = 0, backoff = 2;
+    int count = 0;
+    int redone = 0;         // plain cycles redone after a rejected learned cycle
+  };
+  // A learned cycle is kept when it contracts the residual more than plain
+  // cycles do (their running contraction factor); otherwise its input is
+  // restored, the cycle is redone as a plain cycle (plain multigrid is the
+  // fallback) and the learned step pauses, for longer after each rejection.
+  static int cycle_learned(btmg_problem* P, T* psi_g, int g, LearnState& st, double* rel_out, cudaStream_t s) {
+    const LevelH& L0 = P->lev[0];
+    CK(cycle_part_a(P, psi_g, g, s));
+    double rel;
+    if (int rc = read_rel(P, s, g, &rel, nullptr)) return rc;
+    if (st.pending) {
+      st.pending = false;
+      const double bar = st.prev * (st.plain_seen ? st.ratio : 1.0);
+      if (!(rel < bar)) {
+        ++P->learn_rejected;
+        ++st.redone;
+        CK(cudaMemcpyAsync(psi_g, P->d_backup, L0.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CK(launch_phi_partial<T, C>(psi_g, dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix(),
+                                    reinterpret_cast<const Dir<C>*>(P->d_dir[0]), L0.nx, L0.ny, L0.nd, P->dpc,
+                                    P->nchunk, s));
+        CK(cycle_group(P, psi_g, g, s));  // the plain cycle instead
+        CK(cycle_part_a(P, psi_g, g, s));
+        if (int rc = read_rel(P, s, g, &rel, nullptr)) return rc;
+        st.cooldown = st.backoff;
+        st.backoff = st.backoff < 64 ? 2 * st.backoff : 64;
+      } else {
+        ++P->learn_accepted;
+        st.backoff = 2;
+      }
+    } else if (st.prev < 1e299 && st.prev > 0) {  // a plain cycle: update its contraction factor
+      const double q = rel / st.prev;
+      st.ratio = st.plain_seen ? 0.7 * st.ratio + 0.3 * q : q;
+      ++st.plain_seen;
+    }
+    st.prev = rel;
+    bool learn = false;
+    if (st.cooldown > 0) --st.cooldown;
+    else learn = (st.count++ % P->learn_every) == 0;
+    if (learn) CK(cudaMemcpyAsync(P->d_backup, psi_g, L0.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    CK(cycle_part_b(P, psi_g, g, s, learn));
+    st.pending = learn;
+    *rel_out = rel;
+    return BTMG_OK;
   }
 
   static int mg_cycle(btmg_problem* P, void* psi, double* rel, cudaStream_t s) {
@@ -428,6 +534,28 @@ template <typename T, typename C> struct Impl {
       for (int g = 0; g < P->G; ++g) {
         T* pg = ps + (size_t)g * P->lev[0].n();
         double best = 1e300;
+        if (P->learned) {  // eager cycles with the learned step and its acceptance test
+          LearnState st;
+          for (int c = 0; c < max_cycles; ++c) {
+            double rel;
+            const int before = st.redone;
+            if (int rc = cycle_learned(P, pg, g, st, &rel, s)) return rc;
+            cycles += 1 + (st.redone - before);
+            if (info && info->history && cycles - 1 < info->history_len) info->history[cycles - 1] = rel;
+            if (std::isnan(rel)) {
+              status = BTMG_ERR_NAN;
+              break;
+            }
+            if (rel > 1e3 * best && best < 1e299) {
+              status = BTMG_ERR_DIVERGED;
+              break;
+            }
+            if (rel < best) best = rel;
+            if (rel <= rtol) break;
+          }
+          if (status != BTMG_OK) break;
+          continue;
+        }
         for (int c = 0; c < max_cycles; ++c) {
           if (!P->graphs[g]) {
             if (c == 0) {
@@ -542,7 +670,30 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
     P->inner_extra = P->d_extra_all;
     P->zero_src = true;
     int rc2 = BTMG_OK;
-    for (int k = 0; k < inner && rc2 == BTMG_OK; ++k) rc2 = Impl<T, C>::mg_cycle(P, P->d_delta_all, nullptr, s);
+    if (P->learned) {
+      T* dl = dptr<T>(P->d_delta_all);
+      CK(Impl<T, C>::phi_partials(P, dl, s));
+      for (int g = 0; g < P->G && rc2 == BTMG_OK; ++g) {
+        typename Impl<T, C>::LearnState st;
+        for (int k = 0; k < inner && rc2 == BTMG_OK; ++k) {
+          double r_in;
+          rc2 = Impl<T, C>::cycle_learned(P, dl + (size_t)g * L0.n(), g, st, &r_in, s);
+        }
+        if (rc2 == BTMG_OK && st.pending) {  // judge the last step by one more residual
+          double r_in;
+          CK(Impl<T, C>::cycle_part_a(P, dl + (size_t)g * L0.n(), g, s));
+          rc2 = Impl<T, C>::read_rel(P, s, g, &r_in, nullptr);
+          if (rc2 == BTMG_OK && !(r_in < st.prev)) {
+            ++P->learn_rejected;
+            CK(cudaMemcpyAsync(dl + (size_t)g * L0.n(), P->d_backup, L0.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
+          } else if (rc2 == BTMG_OK) {
+            ++P->learn_accepted;
+          }
+        }
+      }
+    } else {
+      for (int k = 0; k < inner && rc2 == BTMG_OK; ++k) rc2 = Impl<T, C>::mg_cycle(P, P->d_delta_all, nullptr, s);
+    }
     P->inner_extra = nullptr;
     P->zero_src = false;
     if (rc2) return rc2;
@@ -557,6 +708,29 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
   }
   return status;
 }
+
+// features of the learned step for psi (training pairs), per group
+template <typename T, typename C> struct RunFeatures {
+  static int run(btmg_problem* P, const void* psi, float* feat, float* scale, cudaStream_t s) {
+    const T* ps = reinterpret_cast<const T*>(psi);
+    const LevelH& L0 = P->lev[0];
+    const size_t npix = L0.npix();
+    CK(Impl<T, C>::phi_partials(P, ps, s));
+    for (int g = 0; g < P->G; ++g) {
+      CK(Impl<T, C>::source(P, g, s));
+      PgArgs<T, C> a = Impl<T, C>::pg_args(P, g, ps + (size_t)g * L0.n());
+      a.r_out = dptr<C>(P->d_s[0]);
+      a.norm_part = P->d_norm_part;
+      a.rho_part = dptr<C>(P->d_rho_part) + (size_t)g * P->nchunk * npix;
+      CK(launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s));
+      CK(launch_learn_features<C>(a.rho_part, P->nchunk, dptr<C>(P->d_sig[0]) + (size_t)g * npix,
+                                  dptr<C>(P->d_sigs) + ((size_t)g * P->G + g) * npix, L0.dx, L0.nx, L0.ny, P->W8,
+                                  P->H8, P->d_lsum, P->d_lpart, P->n_q_blocks,
+                                  feat + (size_t)g * P->H8 * P->W8 * 3, scale + g, s));
+    }
+    return BTMG_OK;
+  }
+};
 
 template <typename T, typename C> struct RunRefine {
   static int run(btmg_problem* P, double* psi64, double rtol, int mo, int inner, btmg_solve_info* info,
@@ -642,7 +816,8 @@ void destroy(btmg_problem* P) {
   if (!P) return;
   free_graphs(P);
   if (P->twin) destroy(P->twin);
-  for (void* p : {P->d_zero_src, P->d_delta_all, P->d_extra_all, (void*)P->d_r64})
+  for (void* p : {P->d_zero_src, P->d_delta_all, P->d_extra_all, (void*)P->d_r64, P->d_rho_part, (void*)P->d_feat,
+                  (void*)P->d_dimg, (void*)P->d_lscale, (void*)P->d_lsum, (void*)P->d_lpart, P->d_backup})
     if (p) cudaFree(p);
   for (cudaEvent_t e : P->prof_pool) cudaEventDestroy(e);
   for (auto v : {&P->d_dir, &P->d_rcoef, &P->d_sig, &P->d_s, &P->d_delta, &P->d_parent})
@@ -1033,6 +1208,58 @@ int btmg_mg_cycle(btmg_problem* p, void* psi, double* rel_resid, void* stream) {
 int btmg_solve(btmg_problem* p, void* psi, double rtol, int32_t max_cycles, btmg_solve_info* info, void* stream) {
   if (!p || !psi || max_cycles < 1) return fail(BTMG_ERR_INVALID_ARG, "bad solve arguments");
   return dispatch<RunSolve>(p->dtype, p, psi, rtol, (int)max_cycles, info, (cudaStream_t)stream);
+}
+
+namespace {
+int ensure_learn_ws(btmg_problem* P) {
+  if (P->d_rho_part) return BTMG_OK;
+  const LevelH& L0 = P->lev[0];
+  P->W8 = (L0.nx + 7) / 8 * 8;
+  P->H8 = (L0.ny + 7) / 8 * 8;
+  if (P->W8 < 8) P->W8 = 8;
+  if (P->H8 < 8) P->H8 = 8;
+  const size_t es = dtype_size(P->dtype);
+  CK(cudaMalloc(&P->d_rho_part, (size_t)P->G * P->nchunk * L0.npix() * P->csize));
+  CK(cudaMalloc(&P->d_feat, sizeof(float) * 3 * P->H8 * P->W8));
+  CK(cudaMalloc(&P->d_dimg, sizeof(float) * P->H8 * P->W8));
+  CK(cudaMalloc(&P->d_lscale, sizeof(float)));
+  CK(cudaMalloc(&P->d_lsum, sizeof(double)));
+  CK(cudaMalloc(&P->d_lpart, sizeof(double) * P->n_q_blocks));
+  CK(cudaMalloc(&P->d_backup, L0.n() * es));
+  return BTMG_OK;
+}
+}  // namespace
+
+int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every, float omega) {
+  if (!p || every < 1) return fail(BTMG_ERR_INVALID_ARG, "bad learned-correction arguments");
+  if (unet) {
+    if (int rc = ensure_learn_ws(p)) return rc;
+  }
+  free_graphs(p);
+  p->learned = unet;
+  p->learn_every = every;
+  p->learn_omega = omega;
+  return BTMG_OK;
+}
+
+int btmg_learn_stats(const btmg_problem* p, int64_t* accepted, int64_t* rejected) {
+  if (!p) return fail(BTMG_ERR_INVALID_ARG, "null problem");
+  if (accepted) *accepted = p->learn_accepted;
+  if (rejected) *rejected = p->learn_rejected;
+  return BTMG_OK;
+}
+
+int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8) {
+  if (!p) return fail(BTMG_ERR_INVALID_ARG, "null problem");
+  if (h8) *h8 = (p->lev[0].ny + 7) / 8 * 8;
+  if (w8) *w8 = (p->lev[0].nx + 7) / 8 * 8;
+  return BTMG_OK;
+}
+
+int btmg_learn_features(btmg_problem* p, const void* psi, float* feat, float* scale, void* stream) {
+  if (!p || !psi || !feat || !scale) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  if (int rc = ensure_learn_ws(p)) return rc;
+  return dispatch<RunFeatures>(p->dtype, p, psi, feat, scale, (cudaStream_t)stream);
 }
 
 int btmg_solve_refined(btmg_problem* p, double* psi64, double rtol, int32_t max_outer, int32_t inner_cycles,

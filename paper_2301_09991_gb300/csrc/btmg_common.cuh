@@ -70,6 +70,7 @@ template <typename T, typename C> struct PgArgs {
   const C* sigt;      // [ny][nx]
   const Dir<C>* dir;  // [nd]
   C* phi_part;        // PG_JACOBI: [nchunk][ny][nx] partial scalar fluxes
+  C* rho_part;        // PG_RESID, nullable: [nchunk][ny][nx] partial sums of p_n r_n
   double* norm_part;  // PG_RESID: [gridDim.x*gridDim.y] partial sum p dx dy r^2
   int nx, ny, nd, dpc, tiles_x;  // dpc = directions per chunk
   C inv_dx, inv_dy, inv_dx2, inv_dy2, dx, dy, dxdy;
@@ -130,6 +131,16 @@ cudaError_t launch_phi_sum(const C* phi_part, int nchunk, int npix, C* phi, cuda
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s);
 // iterative refinement helpers: extra = alpha * r64 (to the compute type);
 // psi64 += delta / alpha (delta in the storage type)
+// learned correction: features [H8][W8][3] = (rho / rms(rho), log optical
+// thickness, scattering ratio) from the residual-moment partials; apply
+// psi_n += omega * scale * delta / (4 pi) and the flux partial of chunk 0
+template <typename C>
+cudaError_t launch_learn_features(const C* rho_part, int nchunk, const C* sigt, const C* sigs_gg, double dx, int nx,
+                                  int ny, int W8, int H8, double* d_sum, double* d_part, int nblk, float* feat,
+                                  float* scale_out, cudaStream_t s);
+template <typename T, typename C>
+cudaError_t launch_learn_apply(T* psi, int nd, int nx, int ny, int W8, const float* delta, const float* scale,
+                               float omega, C* phi_chunk0, cudaStream_t s);
 template <typename C>
 cudaError_t launch_scale_to(const double* r64, C* extra, double alpha, size_t n, cudaStream_t s);
 template <typename T>

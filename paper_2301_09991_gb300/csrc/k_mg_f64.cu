@@ -17,4 +17,6 @@ INST_TC(double, double)
 INST_C(double)
 template cudaError_t launch_scale_to<double>(const double*, double*, double, size_t, cudaStream_t);
 template cudaError_t launch_refine_update<double>(double*, const double*, double, size_t, cudaStream_t);
+template cudaError_t launch_learn_features<double>(const double*, int, const double*, const double*, double, int, int, int, int, double*, double*, int, float*, float*, cudaStream_t);
+template cudaError_t launch_learn_apply<double, double>(double*, int, int, int, int, const float*, const float*, float, double*, cudaStream_t);
 }  // namespace btmg

@@ -314,6 +314,22 @@ __global__ void k_sum(const double* __restrict__ part, int n, double* __restrict
   }
 }
 
+// one-block deterministic sum (the same reduction as launch_sum, local to each TU)
+__global__ void k_sum_local(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    out[0] = s;
+  }
+}
+inline void k_sum_fwd(const double* part, int n, double* out, cudaStream_t s) { k_sum_local<<<1, 1024, 0, s>>>(part, n, out); }
+
 inline int grid_for(size_t total, int threads) {
   size_t g = (total + threads - 1) / threads;
   if (g > 152 * 32) g = 152 * 32;
@@ -398,6 +414,66 @@ cudaError_t launch_phi_sum(const C* part, int nchunk, int npix, C* phi, cudaStre
 }
 
 namespace {
+// sum over the padded canvas of rho^2 (per-block partials), rho = sum of chunks
+template <typename C>
+__global__ void k_rho_norm(const C* __restrict__ rho_part, int nchunk, int npix, double* __restrict__ part) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    C v = C(0);
+    for (int c = 0; c < nchunk; ++c) v += rho_part[(size_t)c * npix + p];
+    acc += (double)v * (double)v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+// features of the learned correction on a W8 x H8 canvas (zeros outside)
+template <typename C>
+__global__ void k_learn_features(const C* __restrict__ rho_part, int nchunk, const C* __restrict__ sigt,
+                                 const C* __restrict__ sigs_gg, double dx, int nx, int ny, int W8, int H8,
+                                 const double* __restrict__ d_sum, float* __restrict__ feat,
+                                 float* __restrict__ scale_out) {
+  const int npix = nx * ny;
+  const double rms = sqrt(d_sum[0] / (double)npix);
+  const double inv = rms > 0 ? 1.0 / rms : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) scale_out[0] = (float)rms;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < W8 * H8; q += gridDim.x * blockDim.x) {
+    const int x = q % W8, y = q / W8;
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    if (x < nx && y < ny) {
+      const int p = y * nx + x;
+      C v = C(0);
+      for (int c = 0; c < nchunk; ++c) v += rho_part[(size_t)c * npix + p];
+      const double st = (double)sigt[p];
+      f0 = (float)((double)v * inv);
+      f1 = (float)(0.25 * log(st * dx + 1e-3));
+      f2 = st > 0 ? (float)((double)sigs_gg[p] / st) : 0.f;
+    }
+    feat[(size_t)q * 3 + 0] = f0;
+    feat[(size_t)q * 3 + 1] = f1;
+    feat[(size_t)q * 3 + 2] = f2;
+  }
+}
+template <typename T, typename C>
+__global__ void k_learn_apply(T* __restrict__ psi, int nd, int nx, int ny, int W8, const float* __restrict__ delta,
+                              const float* __restrict__ scale, float omega, C* __restrict__ phi0) {
+  const size_t npix = (size_t)nx * ny, total = (size_t)nd * npix;
+  const C a = (C)(omega * scale[0]);
+  const C inv4pi = C(0.07957747154594767);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = i % npix;
+    const int x = (int)(p % nx), y = (int)(p / nx);
+    const C d = a * (C)delta[(size_t)y * W8 + x];
+    Conv<T>::st(psi + i, (C)Conv<T>::ld(psi + i) + d * inv4pi);
+    if (i < npix) phi0[p] += d;  // sum_n p_n / (4 pi) = 1
+  }
+}
 template <typename C>
 __global__ void k_scale_to(const double* __restrict__ r64, C* __restrict__ out, double alpha, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -411,6 +487,23 @@ __global__ void k_refine_update(double* __restrict__ psi64, const T* __restrict_
 
 }  // namespace
 
+template <typename C>
+cudaError_t launch_learn_features(const C* rho_part, int nchunk, const C* sigt, const C* sigs_gg, double dx, int nx,
+                                  int ny, int W8, int H8, double* d_sum, double* d_part, int nblk, float* feat,
+                                  float* scale_out, cudaStream_t s) {
+  k_rho_norm<C><<<nblk, 256, 0, s>>>(rho_part, nchunk, nx * ny, d_part);
+  k_sum_fwd(d_part, nblk, d_sum, s);
+  k_learn_features<C><<<grid_for((size_t)W8 * H8, 256), 256, 0, s>>>(rho_part, nchunk, sigt, sigs_gg, dx, nx, ny,
+                                                                       W8, H8, d_sum, feat, scale_out);
+  return cudaGetLastError();
+}
+template <typename T, typename C>
+cudaError_t launch_learn_apply(T* psi, int nd, int nx, int ny, int W8, const float* delta, const float* scale,
+                               float omega, C* phi0, cudaStream_t s) {
+  k_learn_apply<T, C><<<grid_for((size_t)nd * nx * ny, 256), 256, 0, s>>>(psi, nd, nx, ny, W8, delta, scale, omega,
+                                                                         phi0);
+  return cudaGetLastError();
+}
 template <typename C>
 cudaError_t launch_scale_to(const double* r64, C* out, double alpha, size_t n, cudaStream_t s) {
   k_scale_to<C><<<grid_for(n, 256), 256, 0, s>>>(r64, out, alpha, n);

@@ -17,4 +17,6 @@ INST_TC(__nv_bfloat16, float)
 INST_TC(__half, float)
 template cudaError_t launch_refine_update<__nv_bfloat16>(double*, const __nv_bfloat16*, double, size_t, cudaStream_t);
 template cudaError_t launch_refine_update<__half>(double*, const __half*, double, size_t, cudaStream_t);
+template cudaError_t launch_learn_apply<__nv_bfloat16, float>(__nv_bfloat16*, int, int, int, int, const float*, const float*, float, float*, cudaStream_t);
+template cudaError_t launch_learn_apply<__half, float>(__half*, int, int, int, int, const float*, const float*, float, float*, cudaStream_t);
 }  // namespace btmg

@@ -560,6 +560,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
         if (MODE == PG_RESID) {
           a.r_out[(size_t)n * npix + gi] = r;
           nrm_dir += r * r;
+          phi_acc[k] += dr.w * r;  // residual moment (used when rho_part is set)
         } else {
           const C d = a.beta * (dr.ax + dr.ay + sig);
           const C pn = psi_c + fdiv(r, d);
@@ -581,6 +582,15 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
       if (gx < nx && gy < ny) ph[(size_t)gy * nx + gx] = phi_acc[k];
     }
   } else {
+    if (a.rho_part) {
+      C* rh = a.rho_part + (size_t)chunk * npix;
+      const int gy = y0 + r5;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int gx = x0 + c5 + k;
+        if (gx < nx && gy < ny) rh[(size_t)gy * nx + gx] = phi_acc[k];
+      }
+    }
     for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
     if ((tid & 31) == 0) red[tid >> 5] = nrm;
     __syncthreads();

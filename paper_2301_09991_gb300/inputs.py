@@ -67,11 +67,12 @@ def two_region(nx=32, ny=32, n_polar=8, n_azim=8, sig_in=1.0, sig_out=0.1,
 
 
 def checkerboard(n=256, n_polar=16, n_azim=32, blocks=8, seed=2, c=0.9,
-                 sig_lo=0.1, sig_hi=10.0, ny=None, bc=(VACUUM,) * 4):
+                 sig_lo=0.1, sig_hi=10.0, ny=None, bc=(VACUUM,) * 4, length=1.0):
     """One-group checkerboard: blocks x blocks regions, each with its own
     sigma_t ~ logU[sig_lo, sig_hi]; sigma_s = c sigma_t; source 1 everywhere.
     (256^2 nodes, 16x32 directions, seed 2 is the FP32 single-group
-    workload; ragged sizes are allowed.)"""
+    workload; ragged sizes are allowed.)  `length` is the side of the domain
+    in x (the y side keeps the cell aspect ratio 1)."""
     nx = int(n)
     ny = int(ny if ny is not None else n)
     rng = np.random.default_rng(seed)
@@ -82,7 +83,7 @@ def checkerboard(n=256, n_polar=16, n_azim=32, blocks=8, seed=2, c=0.9,
     region = by[:, None] * blocks + bx[None, :]
     ss = (c * st).reshape(R, 1, 1)
     src = np.ones((R, 1))
-    return _prob(nx, ny, n_polar, n_azim, region, st, ss, src, bc=bc,
+    return _prob(nx, ny, n_polar, n_azim, region, st, ss, src, bc=bc, lx=length, ly=length * ny / nx,
                  name="checkerboard_%dx%d_%dx%d_s%d" % (nx, ny, n_polar, n_azim, seed))
 
 

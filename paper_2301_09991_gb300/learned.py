@@ -1,0 +1,208 @@
+"""Learned correction of the space-angle multigrid: training pairs generated
+by the solver, training of the U-net with the library's own GPU kernels, and
+evaluation against plain multigrid.
+
+A training pair is taken at cycle k of plain multigrid on a seeded
+checkerboard problem (upwind fine scheme, FP32):
+  input  = the features of the learned step computed from the residual of
+           psi_k (btmg_learn_features: rho / rms(rho), log optical
+           thickness, scattering ratio);
+  target = (phi* - phi_{k+1}) / rms(rho): the scalar-flux error left after
+           cycle k, phi* from an FP64-refined solve of the same problem.
+The pairs are augmented by the eight symmetries of the square (the features
+and the target are isotropic quantities and the cycle is D4-symmetric).
+
+Command line (on a GPU):
+  python -m paper_2301_09991_gb300.learned train --out weights.npy
+  python -m paper_2301_09991_gb300.learned eval --weights weights.npy
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import btmg
+from . import inputs as I
+
+CYCLES = (0, 2, 5, 10, 20, 40, 70, 100, 140, 180)
+
+
+def training_problem(seed, n=64, n_polar=8, n_azim=16, c=None, length=None):
+    """Config-2-class problem in the scattering-dominated regime: checkerboard
+    of sigma_t ~ logU[0.1, 10] with a seeded block count (4 or 8 per side),
+    scattering ratio c ~ U[0.95, 0.995] and domain side ~ logU[3, 30] (or the
+    given c and side)."""
+    rng = np.random.default_rng(10_000 + seed)
+    blocks = int(rng.choice([4, 8]))
+    cc = float(rng.uniform(0.95, 0.995))
+    ll = float(np.exp(rng.uniform(np.log(3.0), np.log(30.0))))
+    c = cc if c is None else c
+    length = ll if length is None else length
+    return I.checkerboard(n=n, n_polar=n_polar, n_azim=n_azim, blocks=blocks, seed=seed, c=c, length=length)
+
+
+def reference_flux(prob, rtol=1e-9):
+    """Scalar flux of an FP64-refined solve (upwind fine scheme)."""
+    import torch
+    gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+    psi64 = torch.zeros(gp.shape, dtype=torch.float64, device="cuda")
+    out = gp.solve_refined(psi64, rtol=rtol, max_outer=400, inner_cycles=8)
+    p = torch.tensor(gp.levels[0]["p"], dtype=torch.float64, device="cuda")
+    phi = torch.einsum("n,gnyx->gyx", p, psi64)
+    return phi, out["rel_resid"]
+
+
+def pairs_for_problem(prob, cycles=CYCLES):
+    """Features and targets [m][H8][W8][3], [m][H8][W8] (torch, CUDA)."""
+    import torch
+    phi_star, _ = reference_flux(prob)
+    gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+    psi = gp.zeros()
+    X, Y = [], []
+    ny, nx = gp.shape[2], gp.shape[3]
+    for k in range(max(cycles) + 1):
+        if k in cycles:
+            feat, scale = gp.learn_features(psi)
+        gp.mg_cycle(psi, want_residual=False)
+        if k in cycles:
+            phi = gp.scalar_flux(psi).double()
+            err = (phi_star - phi)[0] / max(float(scale[0]), 1e-30)
+            tgt = torch.zeros(feat.shape[1:3], dtype=torch.float32, device="cuda")
+            tgt[:ny, :nx] = err.float()
+            X.append(feat[0].clone())
+            Y.append(tgt)
+    return torch.stack(X), torch.stack(Y)
+
+
+def d4(X, Y):
+    """The eight symmetries of the square applied to images [m][H][W](...)."""
+    import torch
+    xs, ys = [], []
+    for flip in (False, True):
+        x0 = torch.flip(X, dims=[2]) if flip else X
+        y0 = torch.flip(Y, dims=[2]) if flip else Y
+        for r in range(4):
+            xs.append(torch.rot90(x0, r, dims=[1, 2]))
+            ys.append(torch.rot90(y0, r, dims=[1, 2]))
+    return torch.cat(xs), torch.cat(ys)
+
+
+def make_dataset(seeds, n=64, n_polar=8, n_azim=16, augment=True, log=None):
+    import torch
+    Xs, Ys = [], []
+    t0 = time.time()
+    for i, s in enumerate(seeds):
+        X, Y = pairs_for_problem(training_problem(s, n, n_polar, n_azim))
+        Xs.append(X)
+        Ys.append(Y)
+        if log and (i + 1) % 50 == 0:
+            log("pairs from %d problems (%.0f s)" % (i + 1, time.time() - t0))
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    if augment:
+        X, Y = d4(X, Y)
+    return X.contiguous(), Y.contiguous()
+
+
+def train(net, X, Y, steps=2000, batch=32, lr=1e-3, lr_min=1e-4, seed=0, log=None):
+    """Adam on the mean squared error, cosine learning-rate decay."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    m = X.shape[0]
+    hist = []
+    for it in range(steps):
+        idx = torch.randint(0, m, (batch,), generator=g).cuda()
+        a = lr_min + 0.5 * (lr - lr_min) * (1 + np.cos(np.pi * it / steps))
+        want = (it % 100 == 0) or it == steps - 1
+        loss = net.train_step(X[idx].contiguous(), Y[idx].contiguous(), a, want_loss=want)
+        if want:
+            hist.append((it, loss))
+            if log:
+                log("step %d loss %.4e" % (it, loss))
+    return hist
+
+
+def solve_cycles(prob, net=None, rtol=1e-5, max_cycles=2000, dtype=btmg.F32, every=1):
+    """Cycles and seconds of btmg_solve (upwind fine scheme) to rtol."""
+    import torch
+    gp = btmg.Problem(prob, dtype=dtype, pg=0)
+    if net is not None:
+        gp.set_learned(net, every=every)
+    psi = gp.zeros()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = gp.solve(psi, rtol=rtol, max_cycles=max_cycles)
+    torch.cuda.synchronize()
+    out["seconds"] = time.perf_counter() - t0
+    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0)
+    return out, psi
+
+
+def refined_cycles(prob, net=None, rtol=1e-6, inner=4, dtype=btmg.F32, max_outer=400, every=1):
+    """FP64-refined solve to rtol: inner cycles and seconds."""
+    import torch
+    gp = btmg.Problem(prob, dtype=dtype, pg=0)
+    if net is not None:
+        gp.set_learned(net, every=every)
+    psi64 = torch.zeros(gp.shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = gp.solve_refined(psi64, rtol=rtol, max_outer=max_outer, inner_cycles=inner)
+    torch.cuda.synchronize()
+    out["seconds"] = time.perf_counter() - t0
+    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0)
+    return out, psi64
+
+
+def load_net(path):
+    net = btmg.UNet(in_channels=3, seed=1)
+    net.set_params(np.load(path))
+    return net
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["train", "eval"])
+    ap.add_argument("--out", default="learned_unet.npy")
+    ap.add_argument("--weights", default=None)
+    ap.add_argument("--problems", type=int, default=250)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--n", type=int, default=64)
+    args = ap.parse_args()
+    log = lambda m: print(m, flush=True)
+    if args.cmd == "train":
+        t0 = time.time()
+        X, Y = make_dataset(range(1000, 1000 + args.problems), n=args.n, log=log)
+        log("dataset: %d pairs of %s (%.0f s)" % (X.shape[0], tuple(X.shape[1:]), time.time() - t0))
+        net = btmg.UNet(in_channels=3, seed=1)
+        t1 = time.time()
+        hist = train(net, X, Y, steps=args.steps, log=log)
+        log("training: %d steps in %.0f s" % (args.steps, time.time() - t1))
+        np.save(args.out, net.get_params())
+        print(json.dumps({"pairs": int(X.shape[0]), "loss_first": hist[0][1], "loss_last": hist[-1][1]}))
+    else:
+        import torch
+        net = load_net(args.weights)
+        for s, c, L, n in ((5000, 0.99, 10.0, 64), (5001, 0.99, 30.0, 64), (5002, 0.98, 20.0, 128),
+                           (5003, 0.99, 30.0, 128)):
+            prob = training_problem(s, n=n, c=c, length=L)
+            plain, p0 = solve_cycles(prob, None)
+            for every, omega in ((1, 1.0), (2, 1.0)):
+                gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+                gp.set_learned(net, every=every, omega=omega)
+                psi = gp.zeros()
+                t0 = time.perf_counter()
+                learn = gp.solve(psi, rtol=1e-5, max_cycles=2000)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                diff = float(torch.linalg.norm(psi - p0) / torch.linalg.norm(p0))
+                log("seed %d n %d L %g c %.2f every %d omega %.1f: plain %d cycles %.3f s, learned %d cycles "
+                    "%.3f s (accepted %d, rejected %d), solution diff %.1e"
+                    % (s, n, L, c, every, omega, plain["cycles"], plain["seconds"], learn["cycles"], dt,
+                       *gp.learn_stats(), diff))
+
+
+if __name__ == "__main__":
+    main()
