@@ -202,24 +202,42 @@ int btmg_unet_train_step(btmg_unet* u, const float* x, const float* target, int3
                          float lr, double* loss, void* stream);
 const char* btmg_unet_last_error(void);
 
-/* Attach a trained U-net as a learned correction after every `every`-th
- * cycle of btmg_solve and of the inner cycles of btmg_solve_refined (NULL
- * detaches).  The step: rho = sum_n p_n r_n of the cycle's input residual;
- * features (rho / rms(rho), log(sigma_t dx + 1e-3) / 4, sigma_s / sigma_t)
- * on a canvas padded to multiples of 8; the U-net predicts the scalar-flux
- * error left by the cycle in units of rms(rho); psi_n += omega * rms(rho) *
- * prediction / (4 pi) for every direction.  A step is kept only when the
- * next cycle's input residual is below the previous cycle's; otherwise the
- * iterate before the step is restored and the cycle redone without it
- * (plain multigrid is the fallback).  Solves with a learned correction run
- * their cycles eagerly (no graph).  The U-net must outlive its use.        */
-int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every, float omega);
-int btmg_learn_stats(const btmg_problem* p, int64_t* accepted, int64_t* rejected);
+/* Attach a trained U-net as a learned correction (NULL detaches); the
+ * paper's U-net has fixed weights, the learned step is an extension.  It
+ * runs in every `every`-th cycle of btmg_solve, btmg_mg_cycle and the inner
+ * cycles of btmg_solve_refined.  Such a cycle of group g:
+ *   1. phi0 = scalar flux of psi; psi' = the plain cycle of psi;
+ *   2. r' = residual of psi', rho' = sum_n p_n r'_n;
+ *   3. the U-net (4 input channels, see btmg_learn_features) predicts the
+ *      shape e of the scalar-flux error of psi' from rho', the materials
+ *      and phi(psi') - phi0;
+ *      c_n = (e - (mu_n de/dx + nu_n de/dy) / max(sigma_t, 1/L)) / (4 pi),
+ *      the P1 angular flux of e (L = max(lx, ly));
+ *   4. c' = M c, the plain cycle applied to c with zero external source;
+ *   5. rc = residual of c' (= -L c');
+ *   6. psi' += alpha c' with alpha = -<r', rc>_W / <rc, rc>_W (W = p_n dx dy,
+ *      |alpha| <= 1e6, 0 when undefined), the minimiser of the residual norm
+ *      of psi' + alpha c'.
+ * The step cannot raise the residual norm of the linear (pg = 0) operator;
+ * alpha = 0 is the plain cycle (plain multigrid is the fallback and the
+ * judge).  Everything runs on the device and solves capture cycles with and
+ * without the step as CUDA graphs.  The U-net must outlive its use.
+ * Errors: INVALID_ARG (null problem, every < 1), OOM.                      */
+int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every);
+/* Learned steps since btmg_set_learned, their mean residual reduction
+ * factor ||r1 + alpha rc|| / ||r1|| and the last alpha (synchronises the
+ * device).                                                                  */
+int btmg_learn_stats(btmg_problem* p, int64_t* steps, double* mean_factor, double* last_alpha);
 /* Canvas size of the learned features (ny, nx rounded up to multiples of 8). */
 int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8);
 /* Features of the learned step for psi (training pairs): feat device FP32
- * [G][H8][W8][3], scale device FP32 [G] = rms(rho) of each group.          */
-int btmg_learn_features(btmg_problem* p, const void* psi, float* feat, float* scale, void* stream);
+ * [G][H8][W8][4] = (rho / rms(rho), log(sigma_t dx + 1e-3) / 4,
+ * sigma_s / sigma_t, (phi - phi_prev) / rms(phi - phi_prev)) with rho =
+ * sum_n p_n r_n of the residual of psi and phi, phi_prev the scalar fluxes of
+ * psi and psi_prev (nullable: channel 3 = 0); zero outside the grid.
+ * scale device FP32 [G] = rms(rho) of each group.                          */
+int btmg_learn_features(btmg_problem* p, const void* psi, const void* psi_prev, float* feat, float* scale,
+                        void* stream);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * btmg_profile(p, 1) brackets every subsequent kernel launch of the cycle

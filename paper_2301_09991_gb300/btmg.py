@@ -34,6 +34,7 @@ EXPORTS = (
     "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_learn_canvas",
     "btmg_learn_features",
 )
+LEARN_FEATURES = 4  # input channels of the learned correction
 PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
 
 
@@ -113,10 +114,10 @@ def load(build_if_missing: bool = True):
     L.btmg_solve_refined.argtypes = [vp, vp, C.c_double, i32, i32, C.POINTER(SolveInfo), vp]
     L.btmg_apply_operator_noalloc.argtypes = [i32, i32, C.c_double, C.c_double, i32, i32,
                                               C.POINTER(i32), i32, i32, vp, vp, vp, vp, vp, vp]
-    L.btmg_set_learned.argtypes = [vp, vp, i32, C.c_float]
-    L.btmg_learn_stats.argtypes = [vp, i64p, i64p]
+    L.btmg_set_learned.argtypes = [vp, vp, i32]
+    L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
-    L.btmg_learn_features.argtypes = [vp, vp, vp, vp, vp]
+    L.btmg_learn_features.argtypes = [vp, vp, vp, vp, vp, vp]
     L.btmg_unet_create.argtypes = [i32, C.c_uint64, C.POINTER(vp)]
     L.btmg_unet_destroy.argtypes = [vp]
     L.btmg_unet_num_params.argtypes = [vp, i64p]
@@ -271,23 +272,27 @@ class Problem:
         n_outer = int(np.count_nonzero(hist)) if info.rel_resid > 0 else 1
         return dict(status=rc, cycles=info.cycles, rel_resid=info.rel_resid, history=hist[:max(n_outer, 1)].copy())
 
-    def set_learned(self, unet, every=1, omega=1.0):
+    def set_learned(self, unet, every=1):
+        """Attach (or with None detach) a learned correction, see btmg.h."""
         self._unet = unet  # keep the network alive while attached
-        _check(load().btmg_set_learned(self.h, unet.h if unet is not None else None, int(every), float(omega)))
+        _check(load().btmg_set_learned(self.h, unet.h if unet is not None else None, int(every)))
 
     def learn_stats(self):
-        a, r = C.c_int64(), C.c_int64()
-        _check(load().btmg_learn_stats(self.h, C.byref(a), C.byref(r)))
-        return a.value, r.value
+        """(learned steps, mean residual reduction factor, last alpha)."""
+        n, f, a = C.c_int64(), C.c_double(), C.c_double()
+        _check(load().btmg_learn_stats(self.h, C.byref(n), C.byref(f), C.byref(a)))
+        return n.value, f.value, a.value
 
-    def learn_features(self, psi, stream=None):
-        """(features [G][H8][W8][3], scale [G]) of the learned step for psi."""
+    def learn_features(self, psi, psi_prev=None, stream=None):
+        """(features [G][H8][W8][4], scale [G]) of the learned step for psi
+        (psi_prev: the iterate one cycle earlier, or None)."""
         torch = _torch()
         h8, w8 = C.c_int32(), C.c_int32()
         _check(load().btmg_learn_canvas(self.h, C.byref(h8), C.byref(w8)))
-        feat = torch.empty((self.G, h8.value, w8.value, 3), dtype=torch.float32, device="cuda")
+        feat = torch.empty((self.G, h8.value, w8.value, LEARN_FEATURES), dtype=torch.float32, device="cuda")
         scale = torch.empty((self.G,), dtype=torch.float32, device="cuda")
-        _check(load().btmg_learn_features(self.h, _ptr(psi), _ptr(feat), _ptr(scale), _stream_ptr(stream)))
+        prev = _ptr(psi_prev) if psi_prev is not None else None
+        _check(load().btmg_learn_features(self.h, _ptr(psi), prev, _ptr(feat), _ptr(scale), _stream_ptr(stream)))
         return feat, scale
 
     def profile(self, enable=True):

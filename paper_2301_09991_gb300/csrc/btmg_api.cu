@@ -14,6 +14,8 @@
 
 using namespace btmg;
 
+int unet_in_channels(const btmg_unet* u);  // defined with the U-net kernels
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -33,6 +35,7 @@ int fail(int code, const std::string& msg) {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTile = 32;  // tile edge of the PG and upwind kernels
+constexpr int kDotBlocks = 4 * 152;  // blocks of the learned-step dot product (4 per SM)
 
 // ------------------------------------------------- quadrature (Sec. 2.2) --
 // Gauss-Legendre on [0,1]: Newton iteration on the three-term recurrence.
@@ -137,7 +140,8 @@ struct btmg_problem {
   double* h_pinned = nullptr;  // [2G + 1]
   int* d_err = nullptr;        // device error word (bounded waits)
   // captured cycle graphs per group
-  std::vector<cudaGraphExec_t> graphs;
+  std::vector<cudaGraphExec_t> graphs;   // plain cycle
+  std::vector<cudaGraphExec_t> lgraphs;  // cycle with the learned step
   const void* graph_psi = nullptr;
   cudaStream_t graph_stream = nullptr;
   // graphs cannot be captured on the legacy default stream: solve() runs on
@@ -158,7 +162,6 @@ struct btmg_problem {
   // learned correction (btmg_set_learned)
   btmg_unet* learned = nullptr;
   int learn_every = 1;
-  float learn_omega = 1.f;
   int H8 = 8, W8 = 8;
   void* d_rho_part = nullptr;   // [G][nchunk][npix] compute type
   float* d_feat = nullptr;      // [H8][W8][3]
@@ -166,8 +169,17 @@ struct btmg_problem {
   float* d_lscale = nullptr;    // [1]
   double* d_lsum = nullptr;
   double* d_lpart = nullptr;    // [n_q_blocks]
-  void* d_backup = nullptr;     // one group of psi (storage type)
-  int64_t learn_accepted = 0, learn_rejected = 0;
+  void* d_lc = nullptr;         // [nd][ny][nx] P1 correction c (storage type)
+  void* d_lr = nullptr;         // [nd][ny][nx] residual of c, -L c (compute type)
+  void* d_lb = nullptr;         // [ny][nx] scattering source of c (compute type)
+  double* d_ldot = nullptr;     // [2] <r1, rc>, <rc, rc>
+  double* d_ldpart = nullptr;   // [kDotBlocks]
+  double* d_lstat = nullptr;    // [3] sum of residual reduction factors, steps, last alpha
+  void* d_lphi = nullptr;       // [nchunk][ny][nx] scalar-flux partials of c (compute type)
+  void* d_lzero = nullptr;      // [ny][nx] zeros (compute type)
+  void* d_lphi0 = nullptr;      // [ny][nx] scalar flux before the cycle (compute type)
+  void* d_lprev_all = nullptr;  // [G][ny][nx] scalar flux of psi_prev (btmg_learn_features)
+  int64_t learn_count = 0;      // mg_cycle calls since the net was attached
   // per-kernel-class CUDA-event timing (btmg_profile) and launch counting
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_pool;
@@ -180,9 +192,11 @@ namespace {
 template <typename C> C* dptr(void* p) { return reinterpret_cast<C*>(p); }
 
 void free_graphs(btmg_problem* P) {
-  for (auto& g : P->graphs)
-    if (g) cudaGraphExecDestroy(g);
-  P->graphs.assign(P->G, nullptr);
+  for (auto* v : {&P->graphs, &P->lgraphs}) {
+    for (auto& g : *v)
+      if (g) cudaGraphExecDestroy(g);
+    v->assign(P->G, nullptr);
+  }
   P->graph_psi = nullptr;
 }
 
@@ -261,6 +275,17 @@ template <typename T, typename C> struct Impl {
     return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_qn2_part, P->n_q_blocks, P->d_qn2 + g, s); });
   }
 
+  // In-group scattering source of the learned correction from its partials
+  // d_lphi: d_lb = (sigma_s,gg / 4 pi) phi_c (no external source).
+  static cudaError_t homog_source(btmg_problem* P, int g, cudaStream_t s) {
+    const size_t npix = P->lev[0].npix();
+    return timed(P, PC_MISC, s, [&] {
+      return launch_source<C>(dptr<C>(P->d_lzero), dptr<C>(P->d_sigs) + ((size_t)g * P->G + g) * npix,
+                              dptr<C>(P->d_lphi), 1, 0, P->nchunk, (int)npix, dptr<C>(P->d_lb), nullptr, P->d_lpart,
+                              P->n_q_blocks, s);
+    });
+  }
+
   static cudaError_t phi_partials(btmg_problem* P, const T* psi, cudaStream_t s) {
     const LevelH& L0 = P->lev[0];
     for (int g = 0; g < P->G; ++g) {
@@ -326,7 +351,10 @@ template <typename T, typename C> struct Impl {
     return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, nblk, P->d_rn2 + g, s); });
   }
 
-  static cudaError_t cycle_part_b(btmg_problem* P, T* psi_g, int g, cudaStream_t s, bool learn = false) {
+  // With `homog`, the cycle of the learned correction c (in P->d_lc, its
+  // residual in d_s[0]): zero external source, no inner-refinement source,
+  // scalar-flux partials in d_lphi, result back in d_lc.
+  static cudaError_t cycle_part_b(btmg_problem* P, T* psi_g, int g, cudaStream_t s, bool homog = false) {
     cudaError_t e;
     const int L = P->L;
     const LevelH& L0 = P->lev[0];
@@ -358,109 +386,112 @@ template <typename T, typename C> struct Impl {
       u.init = (L > 1) ? dptr<C>(P->d_delta[1]) : nullptr;
       u.psi_in = psi_g;
       u.psi_out = dptr<T>(P->d_psi_tmp);
-      u.phi_part = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
+      u.phi_part = homog ? dptr<C>(P->d_lphi) : dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
       u.dpc = P->dpc;
       if ((e = timed(P, PC_UP_FINE, s, [&] { return launch_upwind<T, C>(u, UP_UPDATE, P->nchunk, s); })) !=
           cudaSuccess)
         return e;
     }
-    // learned correction (before the post-smoothing sweep, which damps the
-    // small-scale part of the prediction)
-    if (learn && learn_step(P, dptr<T>(P->d_psi_tmp), g, s) != BTMG_OK) return cudaErrorUnknown;
     // 6. fine PG Jacobi sweep with diagonal beta d (Eq. matrix_full)
-    if ((e = source(P, g, s)) != cudaSuccess) return e;
+    if ((e = homog ? homog_source(P, g, s) : source(P, g, s)) != cudaSuccess) return e;
     PgArgs<T, C> j = pg_args(P, g, dptr<T>(P->d_psi_tmp));
     j.psi_out = psi_g;
     j.phi_part = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
+    if (homog) {
+      j.b = dptr<C>(P->d_lb);
+      j.extra = nullptr;
+      j.phi_part = dptr<C>(P->d_lphi);
+    }
     return timed(P, PC_PG_JACOBI, s, [&] { return launch_pg<T, C>(j, PG_JACOBI, P->d.pg != 0, P->nchunk, s); });
   }
 
-  static cudaError_t cycle_group(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
-    cudaError_t e = cycle_part_a(P, psi_g, g, s);
-    if (e != cudaSuccess) return e;
-    return cycle_part_b(P, psi_g, g, s);
-  }
-
-  // The learned step inside a cycle of group g: features from the residual
-  // moment of the cycle's input, U-net prediction of the scalar-flux error,
-  // psi_n += omega * delta / (4 pi) for every direction.
-  static int learn_step(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
-    const LevelH& L0 = P->lev[0];
-    const size_t npix = L0.npix();
-    CK(launch_learn_features<C>(dptr<C>(P->d_rho_part) + (size_t)g * P->nchunk * npix, P->nchunk,
-                                dptr<C>(P->d_sig[0]) + (size_t)g * npix,
-                                dptr<C>(P->d_sigs) + ((size_t)g * P->G + g) * npix, L0.dx, L0.nx, L0.ny, P->W8,
-                                P->H8, P->d_lsum, P->d_lpart, P->n_q_blocks, P->d_feat, P->d_lscale, s));
-    if (int rc = btmg_unet_forward(P->learned, P->d_feat, P->d_dimg, 1, P->H8, P->W8, s))
-      return fail(rc, std::string("learned correction: ") + btmg_unet_last_error());
-    CK(launch_learn_apply<T, C>(psi_g, L0.nd, L0.nx, L0.ny, P->W8, P->d_dimg, P->d_lscale, P->learn_omega,
-                                dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * npix, s));
+  static int cycle_group(btmg_problem* P, T* psi_g, int g, cudaStream_t s, bool learn = false) {
+    if (learn) return cycle_learned(P, psi_g, g, s);
+    CK(cycle_part_a(P, psi_g, g, s));
+    CK(cycle_part_b(P, psi_g, g, s));
     return BTMG_OK;
   }
 
-  // One cycle of group g with the learned step and its acceptance test: a
-  // cycle with the learned step is kept only if the residual of its output
-  // is below the residual of its input; otherwise its input is restored and
-  // it is redone as a plain cycle (plain multigrid is the fallback), and the
-  // learned step pauses for a few cycles.  Returns the relative residual of
-  // the input of the cycle it ran.
-  struct LearnState {
-    bool pending = false;
-    double prev = 1e300;    // residual of the previous cycle's input
-    double ratio = 1.0;     // running contraction factor of plain cycles
-    int plain_seen = 0;
-    int cooldown = 0, backoff = 2;
-    int count = 0;
-    int redone = 0;         // plain cycles redone after a rejected learned cycle
-  };
-  // A learned cycle is kept when it contracts the residual more than plain
-  // cycles do (their running contraction factor); otherwise its input is
-  // restored, the cycle is redone as a plain cycle (plain multigrid is the
-  // fallback) and the learned step pauses, for longer after each rejection.
-  static int cycle_learned(btmg_problem* P, T* psi_g, int g, LearnState& st, double* rel_out, cudaStream_t s) {
-    const LevelH& L0 = P->lev[0];
-    CK(cycle_part_a(P, psi_g, g, s));
-    double rel;
-    if (int rc = read_rel(P, s, g, &rel, nullptr)) return rc;
-    if (st.pending) {
-      st.pending = false;
-      const double bar = st.prev * (st.plain_seen ? st.ratio : 1.0);
-      if (!(rel < bar)) {
-        ++P->learn_rejected;
-        ++st.redone;
-        CK(cudaMemcpyAsync(psi_g, P->d_backup, L0.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
-        CK(launch_phi_partial<T, C>(psi_g, dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix(),
-                                    reinterpret_cast<const Dir<C>*>(P->d_dir[0]), L0.nx, L0.ny, L0.nd, P->dpc,
-                                    P->nchunk, s));
-        CK(cycle_group(P, psi_g, g, s));  // the plain cycle instead
-        CK(cycle_part_a(P, psi_g, g, s));
-        if (int rc = read_rel(P, s, g, &rel, nullptr)) return rc;
-        st.cooldown = st.backoff;
-        st.backoff = st.backoff < 64 ? 2 * st.backoff : 64;
-      } else {
-        ++P->learn_accepted;
-        st.backoff = 2;
-      }
-    } else if (st.prev < 1e299 && st.prev > 0) {  // a plain cycle: update its contraction factor
-      const double q = rel / st.prev;
-      st.ratio = st.plain_seen ? 0.7 * st.ratio + 0.3 * q : q;
-      ++st.plain_seen;
+  // residual of the correction in d_lc (zero external source) into r_out;
+  // with `norm_to`, its weighted squared norm there
+  static int homog_residual(btmg_problem* P, int g, C* r_out, double* norm_to, cudaStream_t s) {
+    PgArgs<T, C> a = pg_args(P, g, dptr<T>(P->d_lc));
+    a.b = dptr<C>(P->d_lb);
+    a.extra = nullptr;
+    a.r_out = r_out;
+    a.norm_part = P->d_norm_part;
+    CK(timed(P, PC_PG_RESID, s, [&] { return launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s); }));
+    if (norm_to) {
+      const int nblk = P->tiles_x * P->tiles_y * P->nchunk;
+      CK(timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, nblk, norm_to, s); }));
     }
-    st.prev = rel;
-    bool learn = false;
-    if (st.cooldown > 0) --st.cooldown;
-    else learn = (st.count++ % P->learn_every) == 0;
-    if (learn) CK(cudaMemcpyAsync(P->d_backup, psi_g, L0.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    CK(cycle_part_b(P, psi_g, g, s, learn));
-    st.pending = learn;
-    *rel_out = rel;
+    return BTMG_OK;
+  }
+
+  // A cycle of group g with the learned step (plain multigrid stays the
+  // judge and the fallback):
+  //  1. phi0 = scalar flux of psi; psi' = the plain cycle of psi;
+  //  2. r' = residual of psi', rho' = sum_n p_n r'_n;
+  //  3. the U-net predicts the shape of the scalar-flux error e of psi' from
+  //     rho', the materials and the cycle's update phi(psi') - phi0; c = the
+  //     P1 angular flux of e, b_c its scattering source;
+  //  4. c' = M c, the plain cycle applied to c with zero source (M = the
+  //     cycle's error propagation, which damps the small-scale part of the
+  //     prediction as it damps the error of psi);
+  //  5. rc = residual of c' (= -L c');
+  //  6. psi' += alpha c' with alpha = -<r', rc>_W / <rc, rc>_W, which
+  //     minimises the weighted residual norm of psi' + alpha c' (alpha = 0:
+  //     the plain cycle).
+  // Everything runs on the device, so the cycle can be graph-captured.  With
+  // the nonlinear PG operator, step 6 uses the linearisation; the next cycle
+  // evaluates the true residual.
+  static int cycle_learned(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
+    const LevelH& L0 = P->lev[0];
+    const size_t npix = L0.npix();
+    const C* sigt = dptr<C>(P->d_sig[0]) + (size_t)g * npix;
+    const C* sigs = dptr<C>(P->d_sigs) + ((size_t)g * P->G + g) * npix;
+    const Dir<C>* dir = reinterpret_cast<const Dir<C>*>(P->d_dir[0]);
+    C* phi_g = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * npix;
+    CK(timed(P, PC_MISC, s, [&] { return launch_phi_sum<C>(phi_g, P->nchunk, (int)npix, dptr<C>(P->d_lphi0), s); }));
+    CK(cycle_part_a(P, psi_g, g, s));
+    CK(cycle_part_b(P, psi_g, g, s));
+    CK(cycle_part_a(P, psi_g, g, s));
+    CK(timed(P, PC_MISC, s, [&] {
+      return launch_learn_features<C>(dptr<C>(P->d_rho_part) + (size_t)g * P->nchunk * npix, P->nchunk, phi_g,
+                                      dptr<C>(P->d_lphi0), sigt, sigs, L0.dx, L0.nx, L0.ny, P->W8, P->H8, P->d_lsum,
+                                      P->d_lpart, P->n_q_blocks, P->d_feat, P->d_lscale, s);
+    }));
+    if (int rc = btmg_unet_forward(P->learned, P->d_feat, P->d_dimg, 1, P->H8, P->W8, s))
+      return fail(rc, std::string("learned correction: ") + btmg_unet_last_error());
+    const double len = std::max(P->d.lx, P->d.ly);
+    CK(timed(P, PC_MISC, s, [&] {
+      return launch_learn_build<T, C>(dptr<T>(P->d_lc), dptr<C>(P->d_lb), P->d_dimg, nullptr, sigt, sigs, dir,
+                                      L0.nd, L0.nx, L0.ny, P->W8, L0.dx, L0.dy, len > 0 ? 1.0 / len : 0.0, s);
+    }));
+    // r' stays in d_lr while the cycle of c uses the level-0 residual buffer
+    CK(cudaMemcpyAsync(P->d_lr, P->d_s[0], L0.n() * sizeof(C), cudaMemcpyDeviceToDevice, s));
+    if (int rc = homog_residual(P, g, dptr<C>(P->d_s[0]), nullptr, s)) return rc;
+    CK(cycle_part_b(P, dptr<T>(P->d_lc), g, s, true));
+    CK(homog_source(P, g, s));
+    if (int rc = homog_residual(P, g, dptr<C>(P->d_s[0]), P->d_ldot + 1, s)) return rc;
+    CK(timed(P, PC_MISC, s, [&] {
+      return launch_learn_dot<C>(dptr<C>(P->d_lr), dptr<C>(P->d_s[0]), dir, L0.nx, L0.ny, L0.nd, L0.dx * L0.dy,
+                                 P->d_ldpart, kDotBlocks, P->d_ldot, s);
+    }));
+    CK(timed(P, PC_MISC, s, [&] {
+      return launch_learn_update<T, C>(psi_g, dptr<T>(P->d_lc), L0.n(), phi_g, dptr<C>(P->d_lphi),
+                                       (size_t)P->nchunk * npix, P->d_ldot, P->d_rn2 + g, P->d_lstat, s);
+    }));
     return BTMG_OK;
   }
 
   static int mg_cycle(btmg_problem* P, void* psi, double* rel, cudaStream_t s) {
     T* ps = reinterpret_cast<T*>(psi);
     CK(phi_partials(P, ps, s));
-    for (int g = 0; g < P->G; ++g) CK(cycle_group(P, ps + (size_t)g * P->lev[0].n(), g, s));
+    const bool learn = P->learned && (P->learn_count++ % P->learn_every) == 0;
+    for (int g = 0; g < P->G; ++g) {
+      if (int rc = cycle_group(P, ps + (size_t)g * P->lev[0].n(), g, s, learn)) return rc;
+    }
     if (rel) {
       CK(cudaMemcpyAsync(P->h_pinned, P->d_rn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(P->h_pinned + P->G, P->d_qn2, sizeof(double) * P->G, cudaMemcpyDeviceToHost, s));
@@ -534,48 +565,32 @@ template <typename T, typename C> struct Impl {
       for (int g = 0; g < P->G; ++g) {
         T* pg = ps + (size_t)g * P->lev[0].n();
         double best = 1e300;
-        if (P->learned) {  // eager cycles with the learned step and its acceptance test
-          LearnState st;
-          for (int c = 0; c < max_cycles; ++c) {
-            double rel;
-            const int before = st.redone;
-            if (int rc = cycle_learned(P, pg, g, st, &rel, s)) return rc;
-            cycles += 1 + (st.redone - before);
-            if (info && info->history && cycles - 1 < info->history_len) info->history[cycles - 1] = rel;
-            if (std::isnan(rel)) {
-              status = BTMG_ERR_NAN;
-              break;
-            }
-            if (rel > 1e3 * best && best < 1e299) {
-              status = BTMG_ERR_DIVERGED;
-              break;
-            }
-            if (rel < best) best = rel;
-            if (rel <= rtol) break;
-          }
-          if (status != BTMG_OK) break;
-          continue;
-        }
+        bool warm[2] = {false, false};
         for (int c = 0; c < max_cycles; ++c) {
-          if (!P->graphs[g]) {
-            if (c == 0) {
-              CK(cycle_group(P, pg, g, s));  // eager first cycle (sets kernel attributes)
+          // the learned step runs in every learn_every-th cycle (from the first)
+          const bool learn = P->learned && (c % P->learn_every) == 0;
+          cudaGraphExec_t& ge = learn ? P->lgraphs[g] : P->graphs[g];
+          if (!ge) {
+            if (!warm[learn]) {
+              // eager first cycle of each kind (sets kernel attributes, sizes workspaces)
+              warm[learn] = true;
+              if (int rc = cycle_group(P, pg, g, s, learn)) return rc;
             } else {
               cudaGraph_t graph;
               CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-              cudaError_t ec = cycle_group(P, pg, g, s);
+              int rc = cycle_group(P, pg, g, s, learn);
               cudaError_t ee = cudaStreamEndCapture(s, &graph);
-              CK(ec);
+              if (rc) return rc;
               CK(ee);
-              cudaError_t ei = cudaGraphInstantiate(&P->graphs[g], graph, 0);
+              cudaError_t ei = cudaGraphInstantiate(&ge, graph, 0);
               cudaGraphDestroy(graph);
               CK(ei);
               P->graph_psi = psi;
               P->graph_stream = s;
-              CK(cudaGraphLaunch(P->graphs[g], s));
+              CK(cudaGraphLaunch(ge, s));
             }
           } else {
-            CK(cudaGraphLaunch(P->graphs[g], s));
+            CK(cudaGraphLaunch(ge, s));
           }
           ++cycles;
           if ((c + 1) % check == 0 || c + 1 == max_cycles) {
@@ -670,30 +685,7 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
     P->inner_extra = P->d_extra_all;
     P->zero_src = true;
     int rc2 = BTMG_OK;
-    if (P->learned) {
-      T* dl = dptr<T>(P->d_delta_all);
-      CK(Impl<T, C>::phi_partials(P, dl, s));
-      for (int g = 0; g < P->G && rc2 == BTMG_OK; ++g) {
-        typename Impl<T, C>::LearnState st;
-        for (int k = 0; k < inner && rc2 == BTMG_OK; ++k) {
-          double r_in;
-          rc2 = Impl<T, C>::cycle_learned(P, dl + (size_t)g * L0.n(), g, st, &r_in, s);
-        }
-        if (rc2 == BTMG_OK && st.pending) {  // judge the last step by one more residual
-          double r_in;
-          CK(Impl<T, C>::cycle_part_a(P, dl + (size_t)g * L0.n(), g, s));
-          rc2 = Impl<T, C>::read_rel(P, s, g, &r_in, nullptr);
-          if (rc2 == BTMG_OK && !(r_in < st.prev)) {
-            ++P->learn_rejected;
-            CK(cudaMemcpyAsync(dl + (size_t)g * L0.n(), P->d_backup, L0.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
-          } else if (rc2 == BTMG_OK) {
-            ++P->learn_accepted;
-          }
-        }
-      }
-    } else {
-      for (int k = 0; k < inner && rc2 == BTMG_OK; ++k) rc2 = Impl<T, C>::mg_cycle(P, P->d_delta_all, nullptr, s);
-    }
+    for (int k = 0; k < inner && rc2 == BTMG_OK; ++k) rc2 = Impl<T, C>::mg_cycle(P, P->d_delta_all, nullptr, s);
     P->inner_extra = nullptr;
     P->zero_src = false;
     if (rc2) return rc2;
@@ -711,10 +703,17 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
 
 // features of the learned step for psi (training pairs), per group
 template <typename T, typename C> struct RunFeatures {
-  static int run(btmg_problem* P, const void* psi, float* feat, float* scale, cudaStream_t s) {
+  static int run(btmg_problem* P, const void* psi, const void* psi_prev, float* feat, float* scale, cudaStream_t s) {
     const T* ps = reinterpret_cast<const T*>(psi);
     const LevelH& L0 = P->lev[0];
     const size_t npix = L0.npix();
+    const size_t nf = (size_t)P->H8 * P->W8 * kLearnFeatures;
+    if (psi_prev) {  // scalar flux of psi_prev per group into the (G-sized) zero-source scratch
+      CK(Impl<T, C>::phi_partials(P, reinterpret_cast<const T*>(psi_prev), s));
+      for (int g = 0; g < P->G; ++g)
+        CK(launch_phi_sum<C>(dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * npix, P->nchunk, (int)npix,
+                             dptr<C>(P->d_lprev_all) + (size_t)g * npix, s));
+    }
     CK(Impl<T, C>::phi_partials(P, ps, s));
     for (int g = 0; g < P->G; ++g) {
       CK(Impl<T, C>::source(P, g, s));
@@ -723,10 +722,11 @@ template <typename T, typename C> struct RunFeatures {
       a.norm_part = P->d_norm_part;
       a.rho_part = dptr<C>(P->d_rho_part) + (size_t)g * P->nchunk * npix;
       CK(launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s));
-      CK(launch_learn_features<C>(a.rho_part, P->nchunk, dptr<C>(P->d_sig[0]) + (size_t)g * npix,
+      CK(launch_learn_features<C>(a.rho_part, P->nchunk, dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * npix,
+                                  psi_prev ? dptr<C>(P->d_lprev_all) + (size_t)g * npix : nullptr,
+                                  dptr<C>(P->d_sig[0]) + (size_t)g * npix,
                                   dptr<C>(P->d_sigs) + ((size_t)g * P->G + g) * npix, L0.dx, L0.nx, L0.ny, P->W8,
-                                  P->H8, P->d_lsum, P->d_lpart, P->n_q_blocks,
-                                  feat + (size_t)g * P->H8 * P->W8 * 3, scale + g, s));
+                                  P->H8, P->d_lsum, P->d_lpart, P->n_q_blocks, feat + (size_t)g * nf, scale + g, s));
     }
     return BTMG_OK;
   }
@@ -817,7 +817,9 @@ void destroy(btmg_problem* P) {
   free_graphs(P);
   if (P->twin) destroy(P->twin);
   for (void* p : {P->d_zero_src, P->d_delta_all, P->d_extra_all, (void*)P->d_r64, P->d_rho_part, (void*)P->d_feat,
-                  (void*)P->d_dimg, (void*)P->d_lscale, (void*)P->d_lsum, (void*)P->d_lpart, P->d_backup})
+                  (void*)P->d_dimg, (void*)P->d_lscale, (void*)P->d_lsum, (void*)P->d_lpart, P->d_lc, P->d_lr, P->d_lb,
+                  (void*)P->d_ldot, (void*)P->d_ldpart, (void*)P->d_lstat, P->d_lphi, P->d_lzero, P->d_lphi0,
+                  P->d_lprev_all})
     if (p) cudaFree(p);
   for (cudaEvent_t e : P->prof_pool) cudaEventDestroy(e);
   for (auto v : {&P->d_dir, &P->d_rcoef, &P->d_sig, &P->d_s, &P->d_delta, &P->d_parent})
@@ -1220,32 +1222,52 @@ int ensure_learn_ws(btmg_problem* P) {
   if (P->H8 < 8) P->H8 = 8;
   const size_t es = dtype_size(P->dtype);
   CK(cudaMalloc(&P->d_rho_part, (size_t)P->G * P->nchunk * L0.npix() * P->csize));
-  CK(cudaMalloc(&P->d_feat, sizeof(float) * 3 * P->H8 * P->W8));
+  CK(cudaMalloc(&P->d_feat, sizeof(float) * kLearnFeatures * P->H8 * P->W8));
   CK(cudaMalloc(&P->d_dimg, sizeof(float) * P->H8 * P->W8));
   CK(cudaMalloc(&P->d_lscale, sizeof(float)));
-  CK(cudaMalloc(&P->d_lsum, sizeof(double)));
+  CK(cudaMalloc(&P->d_lsum, sizeof(double) * 2));
   CK(cudaMalloc(&P->d_lpart, sizeof(double) * P->n_q_blocks));
-  CK(cudaMalloc(&P->d_backup, L0.n() * es));
+  CK(cudaMalloc(&P->d_lc, L0.n() * es));
+  CK(cudaMalloc(&P->d_lr, L0.n() * P->csize));
+  CK(cudaMalloc(&P->d_lb, L0.npix() * P->csize));
+  CK(cudaMalloc(&P->d_ldot, sizeof(double) * 2));
+  CK(cudaMalloc(&P->d_ldpart, sizeof(double) * kDotBlocks));
+  CK(cudaMalloc(&P->d_lstat, sizeof(double) * 3));
+  CK(cudaMalloc(&P->d_lphi, (size_t)P->nchunk * L0.npix() * P->csize));
+  CK(cudaMalloc(&P->d_lzero, L0.npix() * P->csize));
+  CK(cudaMalloc(&P->d_lphi0, L0.npix() * P->csize));
+  CK(cudaMalloc(&P->d_lprev_all, (size_t)P->G * L0.npix() * P->csize));
+  CK(cudaMemset(P->d_lzero, 0, L0.npix() * P->csize));
+  CK(cudaMemset(P->d_lstat, 0, sizeof(double) * 3));
   return BTMG_OK;
 }
 }  // namespace
 
-int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every, float omega) {
+int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every) {
   if (!p || every < 1) return fail(BTMG_ERR_INVALID_ARG, "bad learned-correction arguments");
   if (unet) {
+    if (unet_in_channels(unet) != kLearnFeatures)
+      return fail(BTMG_ERR_INVALID_ARG, "the learned correction needs a U-net with 4 input channels");
     if (int rc = ensure_learn_ws(p)) return rc;
   }
   free_graphs(p);
   p->learned = unet;
   p->learn_every = every;
-  p->learn_omega = omega;
+  p->learn_count = 0;
+  if (p->d_lstat) CK(cudaMemset(p->d_lstat, 0, sizeof(double) * 3));
   return BTMG_OK;
 }
 
-int btmg_learn_stats(const btmg_problem* p, int64_t* accepted, int64_t* rejected) {
+int btmg_learn_stats(btmg_problem* p, int64_t* steps, double* mean_factor, double* last_alpha) {
   if (!p) return fail(BTMG_ERR_INVALID_ARG, "null problem");
-  if (accepted) *accepted = p->learn_accepted;
-  if (rejected) *rejected = p->learn_rejected;
+  double st[3] = {0.0, 0.0, 0.0};
+  if (p->d_lstat) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(st, p->d_lstat, sizeof st, cudaMemcpyDeviceToHost));
+  }
+  if (steps) *steps = (int64_t)st[1];
+  if (mean_factor) *mean_factor = st[1] > 0 ? st[0] / st[1] : 0.0;
+  if (last_alpha) *last_alpha = st[2];
   return BTMG_OK;
 }
 
@@ -1256,10 +1278,11 @@ int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8) {
   return BTMG_OK;
 }
 
-int btmg_learn_features(btmg_problem* p, const void* psi, float* feat, float* scale, void* stream) {
+int btmg_learn_features(btmg_problem* p, const void* psi, const void* psi_prev, float* feat, float* scale,
+                        void* stream) {
   if (!p || !psi || !feat || !scale) return fail(BTMG_ERR_INVALID_ARG, "null argument");
   if (int rc = ensure_learn_ws(p)) return rc;
-  return dispatch<RunFeatures>(p->dtype, p, psi, feat, scale, (cudaStream_t)stream);
+  return dispatch<RunFeatures>(p->dtype, p, psi, psi_prev, feat, scale, (cudaStream_t)stream);
 }
 
 int btmg_solve_refined(btmg_problem* p, double* psi64, double rtol, int32_t max_outer, int32_t inner_cycles,

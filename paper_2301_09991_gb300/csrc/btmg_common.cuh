@@ -134,13 +134,21 @@ cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s);
 // learned correction: features [H8][W8][3] = (rho / rms(rho), log optical
 // thickness, scattering ratio) from the residual-moment partials; apply
 // psi_n += omega * scale * delta / (4 pi) and the flux partial of chunk 0
+constexpr int kLearnFeatures = 4;  // input channels of the learned correction
 template <typename C>
-cudaError_t launch_learn_features(const C* rho_part, int nchunk, const C* sigt, const C* sigs_gg, double dx, int nx,
-                                  int ny, int W8, int H8, double* d_sum, double* d_part, int nblk, float* feat,
-                                  float* scale_out, cudaStream_t s);
+cudaError_t launch_learn_features(const C* rho_part, int nchunk, const C* phi_part, const C* phi_prev, const C* sigt,
+                                  const C* sigs_gg, double dx, int nx, int ny, int W8, int H8, double* d_sum,
+                                  double* d_part, int nblk, float* feat, float* scale_out, cudaStream_t s);
 template <typename T, typename C>
-cudaError_t launch_learn_apply(T* psi, int nd, int nx, int ny, int W8, const float* delta, const float* scale,
-                               float omega, C* phi_chunk0, cudaStream_t s);
+cudaError_t launch_learn_build(T* c_out, C* b_out, const float* delta, const float* scale, const C* sigt,
+                               const C* sigs_gg, const Dir<C>* dir, int nd, int nx, int ny, int W8, double dx,
+                               double dy, double inv_len, cudaStream_t s);
+template <typename C>
+cudaError_t launch_learn_dot(const C* r1, const C* rc, const Dir<C>* dir, int nx, int ny, int nd, double dxdy,
+                             double* part, int nblk, double* out, cudaStream_t s);
+template <typename T, typename C>
+cudaError_t launch_learn_update(T* psi, const T* c, size_t n, C* phi, const C* phi_c, size_t nphi, const double* ldot,
+                                const double* rn2, double* stat, cudaStream_t s);
 template <typename C>
 cudaError_t launch_scale_to(const double* r64, C* extra, double alpha, size_t n, cudaStream_t s);
 template <typename T>

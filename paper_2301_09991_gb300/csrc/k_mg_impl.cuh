@@ -433,45 +433,141 @@ __global__ void k_rho_norm(const C* __restrict__ rho_part, int nchunk, int npix,
     part[blockIdx.x] = s;
   }
 }
-// features of the learned correction on a W8 x H8 canvas (zeros outside)
+// sum over the grid of (phi - phi_prev)^2 (per-block partials), phi = sum of chunks
 template <typename C>
-__global__ void k_learn_features(const C* __restrict__ rho_part, int nchunk, const C* __restrict__ sigt,
+__global__ void k_dphi_norm(const C* __restrict__ phi_part, int nchunk, const C* __restrict__ phi_prev, int npix,
+                            double* __restrict__ part) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    C v = C(0);
+    for (int c = 0; c < nchunk; ++c) v += phi_part[(size_t)c * npix + p];
+    const double d = (double)v - (double)phi_prev[p];
+    acc += d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+// features of the learned correction on a W8 x H8 canvas (zeros outside):
+// rho / rms(rho), log(sigma_t dx + 1e-3) / 4, sigma_s / sigma_t and
+// (phi - phi_prev) / rms(phi - phi_prev) (0 without phi_prev)
+template <typename C>
+__global__ void k_learn_features(const C* __restrict__ rho_part, int nchunk, const C* __restrict__ phi_part,
+                                 const C* __restrict__ phi_prev, const C* __restrict__ sigt,
                                  const C* __restrict__ sigs_gg, double dx, int nx, int ny, int W8, int H8,
                                  const double* __restrict__ d_sum, float* __restrict__ feat,
                                  float* __restrict__ scale_out) {
   const int npix = nx * ny;
   const double rms = sqrt(d_sum[0] / (double)npix);
   const double inv = rms > 0 ? 1.0 / rms : 0.0;
+  const double rms_d = phi_prev ? sqrt(d_sum[1] / (double)npix) : 0.0;
+  const double inv_d = rms_d > 0 ? 1.0 / rms_d : 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) scale_out[0] = (float)rms;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < W8 * H8; q += gridDim.x * blockDim.x) {
     const int x = q % W8, y = q / W8;
-    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
     if (x < nx && y < ny) {
       const int p = y * nx + x;
-      C v = C(0);
+      C v = C(0), ph = C(0);
       for (int c = 0; c < nchunk; ++c) v += rho_part[(size_t)c * npix + p];
       const double st = (double)sigt[p];
       f0 = (float)((double)v * inv);
       f1 = (float)(0.25 * log(st * dx + 1e-3));
       f2 = st > 0 ? (float)((double)sigs_gg[p] / st) : 0.f;
+      if (phi_prev) {
+        for (int c = 0; c < nchunk; ++c) ph += phi_part[(size_t)c * npix + p];
+        f3 = (float)(((double)ph - (double)phi_prev[p]) * inv_d);
+      }
     }
-    feat[(size_t)q * 3 + 0] = f0;
-    feat[(size_t)q * 3 + 1] = f1;
-    feat[(size_t)q * 3 + 2] = f2;
+    float* f = feat + (size_t)q * kLearnFeatures;
+    f[0] = f0;
+    f[1] = f1;
+    f[2] = f2;
+    f[3] = f3;
   }
 }
+// Learned correction as a P1 angular flux (Sec. 2.5 scalar flux, Fick's law
+// closure): the predicted scalar-flux error e (U-net output times the input
+// scale) becomes c_n = (e - (mu_n de/dx + nu_n de/dy) / sigma) / (4 pi), with
+// sigma = max(sigma_t, 1 / domain length) and central differences (one-sided
+// at the edges).  b_out = (sigma_s,gg / 4 pi) e is the in-group scattering
+// source of c, so that a residual evaluation of c with b_out gives -L c.
 template <typename T, typename C>
-__global__ void k_learn_apply(T* __restrict__ psi, int nd, int nx, int ny, int W8, const float* __restrict__ delta,
-                              const float* __restrict__ scale, float omega, C* __restrict__ phi0) {
+__global__ void k_learn_build(T* __restrict__ c_out, C* __restrict__ b_out, const float* __restrict__ delta,
+                              const float* __restrict__ scale, const C* __restrict__ sigt,
+                              const C* __restrict__ sigs_gg, const Dir<C>* __restrict__ dir, int nd, int nx, int ny,
+                              int W8, double inv_dx, double inv_dy, double inv_len) {
   const size_t npix = (size_t)nx * ny, total = (size_t)nd * npix;
-  const C a = (C)(omega * scale[0]);
-  const C inv4pi = C(0.07957747154594767);
+  const double a = scale ? (double)scale[0] : 1.0;
+  const double inv4pi = 0.07957747154594767;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t p = i % npix;
+    const int n = (int)(i / npix);
     const int x = (int)(p % nx), y = (int)(p / nx);
-    const C d = a * (C)delta[(size_t)y * W8 + x];
-    Conv<T>::st(psi + i, (C)Conv<T>::ld(psi + i) + d * inv4pi);
-    if (i < npix) phi0[p] += d;  // sum_n p_n / (4 pi) = 1
+    auto E = [&](int xx, int yy) { return a * (double)delta[(size_t)yy * W8 + xx]; };
+    const double e = E(x, y);
+    const int xl = x > 0 ? x - 1 : x, xr = x + 1 < nx ? x + 1 : x;
+    const int yl = y > 0 ? y - 1 : y, yr = y + 1 < ny ? y + 1 : y;
+    const double ex = xr > xl ? (E(xr, y) - E(xl, y)) * inv_dx / (double)(xr - xl) : 0.0;
+    const double ey = yr > yl ? (E(x, yr) - E(x, yl)) * inv_dy / (double)(yr - yl) : 0.0;
+    const double st = (double)sigt[p];
+    const double sg = st > inv_len ? st : inv_len;
+    const double v = (e - ((double)dir[n].mu * ex + (double)dir[n].nu * ey) / sg) * inv4pi;
+    Conv<T>::st(c_out + i, (C)v);
+    if (n == 0) b_out[p] = (C)((double)sigs_gg[p] * e * inv4pi);
+  }
+}
+// partial sums of sum_n p_n dx dy r1 rc over one group (the residual weight)
+template <typename C>
+__global__ void k_learn_dot(const C* __restrict__ r1, const C* __restrict__ rc, const Dir<C>* __restrict__ dir,
+                            size_t npix, int nd, double dxdy, double* __restrict__ part) {
+  __shared__ double red[32];
+  const size_t total = (size_t)nd * npix;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    acc += (double)dir[i / npix].w * (double)r1[i] * (double)rc[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    part[blockIdx.x] = s * dxdy;
+  }
+}
+// Step length minimising the weighted residual norm along c:
+// r(psi + alpha c) = r + alpha rc, alpha = -<r, rc> / <rc, rc>, |alpha| <= 1e6
+// (0 if <rc, rc> is 0 or not finite); psi += alpha c and the scalar-flux
+// partials phi += alpha phi_c.  ldot = {<r, rc>, <rc, rc>}; rn2 = <r, r>;
+// stat accumulates the residual reduction factor of the step, the step
+// count and the last alpha.
+__device__ __forceinline__ double learn_alpha(const double* ldot) {
+  const double d = ldot[0], nn = ldot[1];
+  double al = (nn > 0.0 && isfinite(nn) && isfinite(d)) ? -d / nn : 0.0;
+  return al > 1e6 ? 1e6 : (al < -1e6 ? -1e6 : al);
+}
+template <typename T, typename C>
+__global__ void k_learn_update(T* __restrict__ psi, const T* __restrict__ c, size_t n, C* __restrict__ phi,
+                               const C* __restrict__ phi_c, size_t nphi, const double* __restrict__ ldot,
+                               const double* __restrict__ rn2, double* __restrict__ stat) {
+  const double al = learn_alpha(ldot);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double rr = rn2[0];
+    const double after = rr + 2.0 * al * ldot[0] + al * al * ldot[1];
+    stat[0] += (rr > 0.0 && after > 0.0) ? sqrt(after / rr) : 0.0;
+    stat[1] += 1.0;
+    stat[2] = al;
+  }
+  const C a = (C)al;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    Conv<T>::st(psi + i, (C)Conv<T>::ld(psi + i) + a * (C)Conv<T>::ld(c + i));
+    if (i < nphi) phi[i] += a * phi_c[i];
   }
 }
 template <typename C>
@@ -488,20 +584,40 @@ __global__ void k_refine_update(double* __restrict__ psi64, const T* __restrict_
 }  // namespace
 
 template <typename C>
-cudaError_t launch_learn_features(const C* rho_part, int nchunk, const C* sigt, const C* sigs_gg, double dx, int nx,
-                                  int ny, int W8, int H8, double* d_sum, double* d_part, int nblk, float* feat,
-                                  float* scale_out, cudaStream_t s) {
+cudaError_t launch_learn_features(const C* rho_part, int nchunk, const C* phi_part, const C* phi_prev, const C* sigt,
+                                  const C* sigs_gg, double dx, int nx, int ny, int W8, int H8, double* d_sum,
+                                  double* d_part, int nblk, float* feat, float* scale_out, cudaStream_t s) {
   k_rho_norm<C><<<nblk, 256, 0, s>>>(rho_part, nchunk, nx * ny, d_part);
   k_sum_fwd(d_part, nblk, d_sum, s);
-  k_learn_features<C><<<grid_for((size_t)W8 * H8, 256), 256, 0, s>>>(rho_part, nchunk, sigt, sigs_gg, dx, nx, ny,
-                                                                       W8, H8, d_sum, feat, scale_out);
+  if (phi_prev) {
+    k_dphi_norm<C><<<nblk, 256, 0, s>>>(phi_part, nchunk, phi_prev, nx * ny, d_part);
+    k_sum_fwd(d_part, nblk, d_sum + 1, s);
+  }
+  k_learn_features<C><<<grid_for((size_t)W8 * H8, 256), 256, 0, s>>>(rho_part, nchunk, phi_part, phi_prev, sigt,
+                                                                       sigs_gg, dx, nx, ny, W8, H8, d_sum, feat,
+                                                                       scale_out);
   return cudaGetLastError();
 }
 template <typename T, typename C>
-cudaError_t launch_learn_apply(T* psi, int nd, int nx, int ny, int W8, const float* delta, const float* scale,
-                               float omega, C* phi0, cudaStream_t s) {
-  k_learn_apply<T, C><<<grid_for((size_t)nd * nx * ny, 256), 256, 0, s>>>(psi, nd, nx, ny, W8, delta, scale, omega,
-                                                                         phi0);
+cudaError_t launch_learn_build(T* c_out, C* b_out, const float* delta, const float* scale, const C* sigt,
+                               const C* sigs_gg, const Dir<C>* dir, int nd, int nx, int ny, int W8, double dx,
+                               double dy, double inv_len, cudaStream_t s) {
+  k_learn_build<T, C><<<grid_for((size_t)nd * nx * ny, 256), 256, 0, s>>>(c_out, b_out, delta, scale, sigt, sigs_gg,
+                                                                         dir, nd, nx, ny, W8, 1.0 / dx, 1.0 / dy,
+                                                                         inv_len);
+  return cudaGetLastError();
+}
+template <typename C>
+cudaError_t launch_learn_dot(const C* r1, const C* rc, const Dir<C>* dir, int nx, int ny, int nd, double dxdy,
+                             double* part, int nblk, double* out, cudaStream_t s) {
+  k_learn_dot<C><<<nblk, 256, 0, s>>>(r1, rc, dir, (size_t)nx * ny, nd, dxdy, part);
+  k_sum_fwd(part, nblk, out, s);
+  return cudaGetLastError();
+}
+template <typename T, typename C>
+cudaError_t launch_learn_update(T* psi, const T* c, size_t n, C* phi, const C* phi_c, size_t nphi, const double* ldot,
+                                const double* rn2, double* stat, cudaStream_t s) {
+  k_learn_update<T, C><<<grid_for(n, 256), 256, 0, s>>>(psi, c, n, phi, phi_c, nphi, ldot, rn2, stat);
   return cudaGetLastError();
 }
 template <typename C>

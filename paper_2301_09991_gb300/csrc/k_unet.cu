@@ -455,6 +455,14 @@ void free_ws(btmg_unet* U) {
 // 12 c3 (P2,112) 13 d3 (P2,48) 14 c2 (P1,80)  15 d2 (P1,32) 16 c1 (P0,48) 17 d1 (P0,16)
 // 18 dout (P0,16) (gradient of the output only)
 int ensure_ws(btmg_unet* U, int N, int H, int W) {
+  // kernel attributes once per process, outside any graph capture (the
+  // first forward call of a size runs eagerly)
+  static bool attrs = false;
+  if (!attrs) {
+    UCK(cudaFuncSetAttribute(k_conv_fwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    UCK(cudaFuncSetAttribute(k_conv_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attrs = true;
+  }
   if (U->N == N && U->H == H && U->W == W) return BTMG_OK;
   free_ws(U);
   const long P0 = (long)N * H * W, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
@@ -494,10 +502,8 @@ cudaError_t conv(btmg_unet* U, int li, const bf16* X, long N, int H, int W, bf16
   const int blocks = (int)((P + 63) / 64);
   const int relu = (Y == nullptr) ? 0 : (c.relu ? 1 : 0);
   if (c.ks == 3) {
-    cudaFuncSetAttribute(k_conv_fwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     k_conv_fwd<3><<<blocks, 128, smem, s>>>(X, (int)N, H, W, cin, wt, U->w + c.boff, cout, Y, Yf, relu);
   } else {
-    cudaFuncSetAttribute(k_conv_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     k_conv_fwd<1><<<blocks, 128, smem, s>>>(X, (int)N, H, W, cin, wt, U->w + c.boff, cout, Y, Yf, relu);
   }
   return cudaGetLastError();
@@ -563,18 +569,14 @@ int conv_bwd(btmg_unet* U, int li, const bf16* X, const bf16* Y, bf16* dY, long 
   if (dX) {
     // dX = conv(dY, flipped transposed weights), no bias, no activation
     k_flip<<<gsz(nw), 256, 0, s>>>(U->wb + c.woff, c.cout, KK, c.cin, U->wflip);
-    const long zb = 0;
-    (void)zb;
     const size_t smem = sizeof(bf16) * (size_t)c.cin * KK * c.cout;
     const int blocks = (int)((P + 63) / 64);
     // the forward kernel adds bias[co]: give it the zero tail of yf as bias
     UCK(cudaMemsetAsync(U->xin, 0, sizeof(float) * 128, s));
     if (c.ks == 3) {
-      cudaFuncSetAttribute(k_conv_fwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      k_conv_fwd<3><<<blocks, 128, smem, s>>>(dY, (int)N, H, W, c.cout, U->wflip, U->xin, c.cin, dX, nullptr, 0);
+        k_conv_fwd<3><<<blocks, 128, smem, s>>>(dY, (int)N, H, W, c.cout, U->wflip, U->xin, c.cin, dX, nullptr, 0);
     } else {
-      cudaFuncSetAttribute(k_conv_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      k_conv_fwd<1><<<blocks, 128, smem, s>>>(dY, (int)N, H, W, c.cout, U->wflip, U->xin, c.cin, dX, nullptr, 0);
+        k_conv_fwd<1><<<blocks, 128, smem, s>>>(dY, (int)N, H, W, c.cout, U->wflip, U->xin, c.cin, dX, nullptr, 0);
     }
   }
   UCK(cudaGetLastError());
@@ -747,3 +749,6 @@ int btmg_unet_train_step(btmg_unet* U, const float* x, const float* target, int3
 const char* btmg_unet_last_error(void) { return u_err.c_str(); }
 
 }  // extern "C"
+
+// input channels of a U-net (library-internal, used by btmg_set_learned)
+int unet_in_channels(const btmg_unet* U) { return U ? U->in_ch : 0; }

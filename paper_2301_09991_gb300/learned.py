@@ -4,11 +4,13 @@ evaluation against plain multigrid.
 
 A training pair is taken at cycle k of plain multigrid on a seeded
 checkerboard problem (upwind fine scheme, FP32):
-  input  = the features of the learned step computed from the residual of
-           psi_k (btmg_learn_features: rho / rms(rho), log optical
-           thickness, scattering ratio);
-  target = (phi* - phi_{k+1}) / rms(rho): the scalar-flux error left after
-           cycle k, phi* from an FP64-refined solve of the same problem.
+  input  = the features of the learned step for psi_k after psi_{k-1}
+           (btmg_learn_features: rho / rms(rho), log optical thickness,
+           scattering ratio, (phi_k - phi_{k-1}) / rms);
+  target = e / rms(e), e = phi* - phi_k the scalar-flux error of psi_k
+           (phi* from an FP64-refined solve of the same problem): the shape
+           of the error, since the step length of the learned step sets its
+           size.
 The pairs are augmented by the eight symmetries of the square (the features
 and the target are isotropic quantities and the cycle is D4-symmetric).
 
@@ -27,7 +29,7 @@ import numpy as np
 from . import btmg
 from . import inputs as I
 
-CYCLES = (0, 2, 5, 10, 20, 40, 70, 100, 140, 180)
+CYCLES = (1, 3, 6, 10, 20, 40, 70, 100, 140, 180)
 
 
 def training_problem(seed, n=64, n_polar=8, n_azim=16, c=None, length=None):
@@ -56,24 +58,26 @@ def reference_flux(prob, rtol=1e-9):
 
 
 def pairs_for_problem(prob, cycles=CYCLES):
-    """Features and targets [m][H8][W8][3], [m][H8][W8] (torch, CUDA)."""
+    """Features and targets [m][H8][W8][4], [m][H8][W8] (torch, CUDA)."""
     import torch
     phi_star, _ = reference_flux(prob)
     gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
     psi = gp.zeros()
     X, Y = [], []
     ny, nx = gp.shape[2], gp.shape[3]
+    prev = None
     for k in range(max(cycles) + 1):
         if k in cycles:
-            feat, scale = gp.learn_features(psi)
-        gp.mg_cycle(psi, want_residual=False)
-        if k in cycles:
-            phi = gp.scalar_flux(psi).double()
-            err = (phi_star - phi)[0] / max(float(scale[0]), 1e-30)
+            feat, _ = gp.learn_features(psi, prev)
+            err = (phi_star - gp.scalar_flux(psi).double())[0]
+            err = err / max(float(torch.sqrt(torch.mean(err * err))), 1e-300)
             tgt = torch.zeros(feat.shape[1:3], dtype=torch.float32, device="cuda")
             tgt[:ny, :nx] = err.float()
             X.append(feat[0].clone())
             Y.append(tgt)
+        if k + 1 in cycles:
+            prev = psi.clone()
+        gp.mg_cycle(psi, want_residual=False)
     return torch.stack(X), torch.stack(Y)
 
 
@@ -136,7 +140,7 @@ def solve_cycles(prob, net=None, rtol=1e-5, max_cycles=2000, dtype=btmg.F32, eve
     out = gp.solve(psi, rtol=rtol, max_cycles=max_cycles)
     torch.cuda.synchronize()
     out["seconds"] = time.perf_counter() - t0
-    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0)
+    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0.0, 0.0)
     return out, psi
 
 
@@ -152,12 +156,12 @@ def refined_cycles(prob, net=None, rtol=1e-6, inner=4, dtype=btmg.F32, max_outer
     out = gp.solve_refined(psi64, rtol=rtol, max_outer=max_outer, inner_cycles=inner)
     torch.cuda.synchronize()
     out["seconds"] = time.perf_counter() - t0
-    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0)
+    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0.0, 0.0)
     return out, psi64
 
 
 def load_net(path):
-    net = btmg.UNet(in_channels=3, seed=1)
+    net = btmg.UNet(in_channels=btmg.LEARN_FEATURES, seed=1)
     net.set_params(np.load(path))
     return net
 
@@ -176,7 +180,7 @@ def main():
         t0 = time.time()
         X, Y = make_dataset(range(1000, 1000 + args.problems), n=args.n, log=log)
         log("dataset: %d pairs of %s (%.0f s)" % (X.shape[0], tuple(X.shape[1:]), time.time() - t0))
-        net = btmg.UNet(in_channels=3, seed=1)
+        net = btmg.UNet(in_channels=btmg.LEARN_FEATURES, seed=1)
         t1 = time.time()
         hist = train(net, X, Y, steps=args.steps, log=log)
         log("training: %d steps in %.0f s" % (args.steps, time.time() - t1))
@@ -189,20 +193,15 @@ def main():
                            (5003, 0.99, 30.0, 128)):
             prob = training_problem(s, n=n, c=c, length=L)
             plain, p0 = solve_cycles(prob, None)
-            for every, omega in ((1, 1.0), (2, 1.0)):
-                gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
-                gp.set_learned(net, every=every, omega=omega)
-                psi = gp.zeros()
-                t0 = time.perf_counter()
-                learn = gp.solve(psi, rtol=1e-5, max_cycles=2000)
-                torch.cuda.synchronize()
-                dt = time.perf_counter() - t0
-                diff = float(torch.linalg.norm(psi - p0) / torch.linalg.norm(p0))
-                log("seed %d n %d L %g c %.2f every %d omega %.1f: plain %d cycles %.3f s, learned %d cycles "
-                    "%.3f s (accepted %d, rejected %d), solution diff %.1e"
-                    % (s, n, L, c, every, omega, plain["cycles"], plain["seconds"], learn["cycles"], dt,
-                       *gp.learn_stats(), diff))
-
+            solve_cycles(prob, net)  # warm-up: graphs and U-net workspaces
+            for every in (1, 2, 4):
+                learn, p1 = solve_cycles(prob, net, every=every)
+                diff = float(torch.linalg.norm(p1 - p0) / torch.linalg.norm(p0))
+                st = learn["learn_stats"]
+                log("seed %d n %d L %g c %.3f every %d: plain %d cycles %.3f s, learned %d cycles %.3f s "
+                    "(%d steps, mean factor %.3f), solution diff %.1e"
+                    % (s, n, L, c, every, plain["cycles"], plain["seconds"], learn["cycles"], learn["seconds"],
+                       st[0], st[1], diff))
 
 if __name__ == "__main__":
     main()
