@@ -208,16 +208,18 @@ const char* btmg_unet_last_error(void);
  * cycles of btmg_solve_refined.  Such a cycle of group g:
  *   1. phi0 = scalar flux of psi; psi' = the plain cycle of psi;
  *   2. r' = residual of psi', rho' = sum_n p_n r'_n;
- *   3. the U-net (4 input channels, see btmg_learn_features) predicts the
- *      shape e of the scalar-flux error of psi' from rho', the materials
- *      and phi(psi') - phi0;
+ *   3. the U-net (4 input channels, see btmg_learn_features) predicts, on
+ *      the coarse canvas (btmg_learn_canvas), the shape e of the scalar-flux
+ *      error of psi' from rho', the materials and phi(psi') - phi0; e is
+ *      interpolated bilinearly to the nodes and
  *      c_n = (e - (mu_n de/dx + nu_n de/dy) / max(sigma_t, 1/L)) / (4 pi),
  *      the P1 angular flux of e (L = max(lx, ly));
  *   4. c' = M c, the plain cycle applied to c with zero external source;
  *   5. rc = residual of c' (= -L c');
- *   6. psi' += alpha c' with alpha = -<r', rc>_W / <rc, rc>_W (W = p_n dx dy,
- *      |alpha| <= 1e6, 0 when undefined), the minimiser of the residual norm
- *      of psi' + alpha c'.
+ *   6. psi' += alpha c' with alpha = -<r', rc>_W / <rc, rc>_W (W = p_n dx dy),
+ *      the minimiser of the residual norm of psi' + alpha c'; alpha = 0 when
+ *      undefined or when the predicted reduction of ||r'||^2 is below 1e-4;
+ *      |alpha| rms(phi(c')) <= 1e3 rms(phi(psi') - phi0).
  * The step cannot raise the residual norm of the linear (pg = 0) operator;
  * alpha = 0 is the plain cycle (plain multigrid is the fallback and the
  * judge).  Everything runs on the device and solves capture cycles with and
@@ -225,17 +227,26 @@ const char* btmg_unet_last_error(void);
  * Errors: INVALID_ARG (null problem, every < 1), OOM.                      */
 int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every);
 /* Learned steps since btmg_set_learned, their mean residual reduction
- * factor ||r1 + alpha rc|| / ||r1|| and the last alpha (synchronises the
- * device).                                                                  */
-int btmg_learn_stats(btmg_problem* p, int64_t* steps, double* mean_factor, double* last_alpha);
-/* Canvas size of the learned features (ny, nx rounded up to multiples of 8). */
-int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8);
+ * factor ||r' + alpha rc|| / ||r'||, the last alpha, and the number of solves
+ * that fell back to plain cycles (synchronises the device).  A solve falls
+ * back, for the rest of that call, when its residual exceeds twice its best
+ * so far (btmg_solve) or its outer FP64 residual exceeds 1.5 times its best
+ * (btmg_solve_refined).
+ * Any output may be NULL.                                                   */
+int btmg_learn_stats(btmg_problem* p, int64_t* steps, double* mean_factor, double* last_alpha,
+                     int32_t* fallbacks);
+/* Coarse canvas of the learned correction: factor f = ceil(max(nx, ny) / 64)
+ * and the canvas ceil(ny / f) x ceil(nx / f), each rounded up to a multiple
+ * of 8; canvas pixel (X, Y) covers the nodes [X f, X f + f) x [Y f, Y f + f). */
+int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8, int32_t* factor);
 /* Features of the learned step for psi (training pairs): feat device FP32
- * [G][H8][W8][4] = (rho / rms(rho), log(sigma_t dx + 1e-3) / 4,
- * sigma_s / sigma_t, (phi - phi_prev) / rms(phi - phi_prev)) with rho =
- * sum_n p_n r_n of the residual of psi and phi, phi_prev the scalar fluxes of
- * psi and psi_prev (nullable: channel 3 = 0); zero outside the grid.
- * scale device FP32 [G] = rms(rho) of each group.                          */
+ * [G][H8][W8][4] on the coarse canvas, each pixel the mean over its nodes:
+ * (rho / rms(rho), log(sigma_t f dx + 1e-3) / 4 with the mean sigma_t,
+ * mean sigma_s / mean sigma_t, dphi / rms(dphi)) with rho = sum_n p_n r_n of
+ * the residual of psi and dphi = phi - phi_prev, the change of scalar flux
+ * from psi_prev to psi (psi_prev nullable: channel 3 = 0); the rms are over
+ * the covered canvas pixels; zero outside them.  scale device FP32 [G] =
+ * rms of the mean rho of each group.                                       */
 int btmg_learn_features(btmg_problem* p, const void* psi, const void* psi_prev, float* feat, float* scale,
                         void* stream);
 

@@ -115,8 +115,8 @@ def load(build_if_missing: bool = True):
     L.btmg_apply_operator_noalloc.argtypes = [i32, i32, C.c_double, C.c_double, i32, i32,
                                               C.POINTER(i32), i32, i32, vp, vp, vp, vp, vp, vp]
     L.btmg_set_learned.argtypes = [vp, vp, i32]
-    L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
-    L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i32)]
+    L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.btmg_learn_features.argtypes = [vp, vp, vp, vp, vp, vp]
     L.btmg_unet_create.argtypes = [i32, C.c_uint64, C.POINTER(vp)]
     L.btmg_unet_destroy.argtypes = [vp]
@@ -278,18 +278,24 @@ class Problem:
         _check(load().btmg_set_learned(self.h, unet.h if unet is not None else None, int(every)))
 
     def learn_stats(self):
-        """(learned steps, mean residual reduction factor, last alpha)."""
-        n, f, a = C.c_int64(), C.c_double(), C.c_double()
-        _check(load().btmg_learn_stats(self.h, C.byref(n), C.byref(f), C.byref(a)))
-        return n.value, f.value, a.value
+        """(learned steps, mean residual reduction factor, last alpha,
+        solves that fell back to plain cycles)."""
+        n, f, a, b = C.c_int64(), C.c_double(), C.c_double(), C.c_int32()
+        _check(load().btmg_learn_stats(self.h, C.byref(n), C.byref(f), C.byref(a), C.byref(b)))
+        return n.value, f.value, a.value, b.value
+
+    def learn_canvas(self):
+        """(H8, W8, f): coarse canvas of the learned correction and its factor."""
+        h8, w8, f = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().btmg_learn_canvas(self.h, C.byref(h8), C.byref(w8), C.byref(f)))
+        return h8.value, w8.value, f.value
 
     def learn_features(self, psi, psi_prev=None, stream=None):
         """(features [G][H8][W8][4], scale [G]) of the learned step for psi
         (psi_prev: the iterate one cycle earlier, or None)."""
         torch = _torch()
-        h8, w8 = C.c_int32(), C.c_int32()
-        _check(load().btmg_learn_canvas(self.h, C.byref(h8), C.byref(w8)))
-        feat = torch.empty((self.G, h8.value, w8.value, LEARN_FEATURES), dtype=torch.float32, device="cuda")
+        h8, w8, _ = self.learn_canvas()
+        feat = torch.empty((self.G, h8, w8, LEARN_FEATURES), dtype=torch.float32, device="cuda")
         scale = torch.empty((self.G,), dtype=torch.float32, device="cuda")
         prev = _ptr(psi_prev) if psi_prev is not None else None
         _check(load().btmg_learn_features(self.h, _ptr(psi), prev, _ptr(feat), _ptr(scale), _stream_ptr(stream)))

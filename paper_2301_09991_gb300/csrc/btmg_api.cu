@@ -162,13 +162,13 @@ struct btmg_problem {
   // learned correction (btmg_set_learned)
   btmg_unet* learned = nullptr;
   int learn_every = 1;
-  int H8 = 8, W8 = 8;
+  int H8 = 8, W8 = 8, lf = 1;  // coarse canvas of the learned correction and its factor
   void* d_rho_part = nullptr;   // [G][nchunk][npix] compute type
   float* d_feat = nullptr;      // [H8][W8][3]
   float* d_dimg = nullptr;      // [H8][W8]
   float* d_lscale = nullptr;    // [1]
   double* d_lsum = nullptr;
-  double* d_lpart = nullptr;    // [n_q_blocks]
+  double* d_lpart = nullptr;    // [max(2 kLearnBlocks, n_q_blocks)]
   void* d_lc = nullptr;         // [nd][ny][nx] P1 correction c (storage type)
   void* d_lr = nullptr;         // [nd][ny][nx] residual of c, -L c (compute type)
   void* d_lb = nullptr;         // [ny][nx] scattering source of c (compute type)
@@ -180,6 +180,8 @@ struct btmg_problem {
   void* d_lphi0 = nullptr;      // [ny][nx] scalar flux before the cycle (compute type)
   void* d_lprev_all = nullptr;  // [G][ny][nx] scalar flux of psi_prev (btmg_learn_features)
   int64_t learn_count = 0;      // mg_cycle calls since the net was attached
+  bool learn_off = false;       // solve-time fallback to plain cycles (reset by each solve)
+  int32_t learn_fallbacks = 0;  // solves that fell back since the net was attached
   // per-kernel-class CUDA-event timing (btmg_profile) and launch counting
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_pool;
@@ -433,15 +435,20 @@ template <typename T, typename C> struct Impl {
   //  1. phi0 = scalar flux of psi; psi' = the plain cycle of psi;
   //  2. r' = residual of psi', rho' = sum_n p_n r'_n;
   //  3. the U-net predicts the shape of the scalar-flux error e of psi' from
-  //     rho', the materials and the cycle's update phi(psi') - phi0; c = the
-  //     P1 angular flux of e, b_c its scattering source;
+  //     rho', the materials and the cycle's update phi(psi') - phi0, all
+  //     averaged over lf x lf nodes (a canvas of at most 64 x 64 pixels, so
+  //     the net sees the whole domain and its cost does not grow with the
+  //     grid); c = the P1 angular flux of e interpolated to the fine nodes,
+  //     b_c its scattering source;
   //  4. c' = M c, the plain cycle applied to c with zero source (M = the
   //     cycle's error propagation, which damps the small-scale part of the
   //     prediction as it damps the error of psi);
   //  5. rc = residual of c' (= -L c');
   //  6. psi' += alpha c' with alpha = -<r', rc>_W / <rc, rc>_W, which
-  //     minimises the weighted residual norm of psi' + alpha c' (alpha = 0:
-  //     the plain cycle).
+  //     minimises the weighted residual norm of psi' + alpha c' (alpha = 0,
+  //     the plain cycle, when the predicted gain is rounding noise; |alpha|
+  //     capped so that the step's scalar flux stays within 1e3 times the
+  //     cycle's own update).
   // Everything runs on the device, so the cycle can be graph-captured.  With
   // the nonlinear PG operator, step 6 uses the linearisation; the next cycle
   // evaluates the true residual.
@@ -458,15 +465,19 @@ template <typename T, typename C> struct Impl {
     CK(cycle_part_a(P, psi_g, g, s));
     CK(timed(P, PC_MISC, s, [&] {
       return launch_learn_features<C>(dptr<C>(P->d_rho_part) + (size_t)g * P->nchunk * npix, P->nchunk, phi_g,
-                                      dptr<C>(P->d_lphi0), sigt, sigs, L0.dx, L0.nx, L0.ny, P->W8, P->H8, P->d_lsum,
-                                      P->d_lpart, P->n_q_blocks, P->d_feat, P->d_lscale, s);
+                                      dptr<C>(P->d_lphi0), sigt, sigs, L0.dx, L0.nx, L0.ny, P->lf, P->W8, P->H8,
+                                      P->d_lsum, P->d_lpart, P->d_feat, P->d_lscale, s);
+    }));
+    CK(timed(P, PC_MISC, s, [&] {
+      return launch_dphi_norm<C>(phi_g, P->nchunk, dptr<C>(P->d_lphi0), (int)npix, P->d_ldpart, kDotBlocks,
+                                 P->d_ldot + 3, s);
     }));
     if (int rc = btmg_unet_forward(P->learned, P->d_feat, P->d_dimg, 1, P->H8, P->W8, s))
       return fail(rc, std::string("learned correction: ") + btmg_unet_last_error());
     const double len = std::max(P->d.lx, P->d.ly);
     CK(timed(P, PC_MISC, s, [&] {
-      return launch_learn_build<T, C>(dptr<T>(P->d_lc), dptr<C>(P->d_lb), P->d_dimg, nullptr, sigt, sigs, dir,
-                                      L0.nd, L0.nx, L0.ny, P->W8, L0.dx, L0.dy, len > 0 ? 1.0 / len : 0.0, s);
+      return launch_learn_build<T, C>(dptr<T>(P->d_lc), dptr<C>(P->d_lb), P->d_dimg, sigt, sigs, dir, L0.nd, L0.nx,
+                                      L0.ny, P->lf, P->W8, L0.dx, L0.dy, len > 0 ? 1.0 / len : 0.0, s);
     }));
     // r' stays in d_lr while the cycle of c uses the level-0 residual buffer
     CK(cudaMemcpyAsync(P->d_lr, P->d_s[0], L0.n() * sizeof(C), cudaMemcpyDeviceToDevice, s));
@@ -474,6 +485,10 @@ template <typename T, typename C> struct Impl {
     CK(cycle_part_b(P, dptr<T>(P->d_lc), g, s, true));
     CK(homog_source(P, g, s));
     if (int rc = homog_residual(P, g, dptr<C>(P->d_s[0]), P->d_ldot + 1, s)) return rc;
+    CK(timed(P, PC_MISC, s, [&] {
+      return launch_dphi_norm<C>(dptr<C>(P->d_lphi), P->nchunk, dptr<C>(P->d_lzero), (int)npix, P->d_ldpart,
+                                 kDotBlocks, P->d_ldot + 2, s);
+    }));
     CK(timed(P, PC_MISC, s, [&] {
       return launch_learn_dot<C>(dptr<C>(P->d_lr), dptr<C>(P->d_s[0]), dir, L0.nx, L0.ny, L0.nd, L0.dx * L0.dy,
                                  P->d_ldpart, kDotBlocks, P->d_ldot, s);
@@ -488,7 +503,7 @@ template <typename T, typename C> struct Impl {
   static int mg_cycle(btmg_problem* P, void* psi, double* rel, cudaStream_t s) {
     T* ps = reinterpret_cast<T*>(psi);
     CK(phi_partials(P, ps, s));
-    const bool learn = P->learned && (P->learn_count++ % P->learn_every) == 0;
+    const bool learn = P->learned && !P->learn_off && (P->learn_count++ % P->learn_every) == 0;
     for (int g = 0; g < P->G; ++g) {
       if (int rc = cycle_group(P, ps + (size_t)g * P->lev[0].n(), g, s, learn)) return rc;
     }
@@ -556,6 +571,7 @@ template <typename T, typename C> struct Impl {
     T* ps = reinterpret_cast<T*>(psi);
     const int check = (info && info->check_every > 0) ? info->check_every : 1;
     if (P->graph_psi != psi || P->graph_stream != s) free_graphs(P);
+    P->learn_off = false;
     int cycles = 0, status = BTMG_OK;
     CK(phi_partials(P, ps, s));
     int max_outer = (info && info->max_outer > 0) ? info->max_outer : (P->upscatter ? 8 : 1);
@@ -568,7 +584,7 @@ template <typename T, typename C> struct Impl {
         bool warm[2] = {false, false};
         for (int c = 0; c < max_cycles; ++c) {
           // the learned step runs in every learn_every-th cycle (from the first)
-          const bool learn = P->learned && (c % P->learn_every) == 0;
+          const bool learn = P->learned && !P->learn_off && (c % P->learn_every) == 0;
           cudaGraphExec_t& ge = learn ? P->lgraphs[g] : P->graphs[g];
           if (!ge) {
             if (!warm[learn]) {
@@ -605,6 +621,12 @@ template <typename T, typename C> struct Impl {
             if (rel > 1e3 * best && best < 1e299) {
               status = BTMG_ERR_DIVERGED;
               break;
+            }
+            // plain multigrid judges the learned step: a residual above
+            // twice the best so far ends it for the rest of this solve
+            if (P->learned && !P->learn_off && best < 1e299 && rel > 2.0 * best) {
+              P->learn_off = true;
+              ++P->learn_fallbacks;
             }
             if (rel < best) best = rel;
             if (rel <= rtol) break;
@@ -661,7 +683,8 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
   btmg_problem* Q = P->twin;
   const double w = 4.0 * kPi * L0.dx * L0.dy;
   int cycles = 0, status = BTMG_ERR_NOT_CONVERGED;
-  double rel = 0.0;
+  double rel = 0.0, best = 1e300;
+  P->learn_off = false;
   for (int outer = 0; outer <= max_outer; ++outer) {
     CK(Impl<double, double>::residual_all(Q, psi64, P->d_r64, s));
     int rc = Impl<double, double>::read_rel(Q, s, 0, nullptr, &rel);
@@ -676,6 +699,13 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
       break;
     }
     if (outer == max_outer) break;
+    // plain multigrid judges the learned step: an outer residual above 1.5
+    // times the best so far ends it for the rest of this solve
+    if (P->learned && !P->learn_off && rel > 1.5 * best) {
+      P->learn_off = true;
+      ++P->learn_fallbacks;
+    }
+    if (rel < best) best = rel;
     double rn2 = 0.0;
     for (int g = 0; g < P->G; ++g) rn2 += Q->h_pinned[g];
     const double rms = std::sqrt(rn2 / (w * (double)npix * P->G));
@@ -725,8 +755,8 @@ template <typename T, typename C> struct RunFeatures {
       CK(launch_learn_features<C>(a.rho_part, P->nchunk, dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * npix,
                                   psi_prev ? dptr<C>(P->d_lprev_all) + (size_t)g * npix : nullptr,
                                   dptr<C>(P->d_sig[0]) + (size_t)g * npix,
-                                  dptr<C>(P->d_sigs) + ((size_t)g * P->G + g) * npix, L0.dx, L0.nx, L0.ny, P->W8,
-                                  P->H8, P->d_lsum, P->d_lpart, P->n_q_blocks, feat + (size_t)g * nf, scale + g, s));
+                                  dptr<C>(P->d_sigs) + ((size_t)g * P->G + g) * npix, L0.dx, L0.nx, L0.ny, P->lf,
+                                  P->W8, P->H8, P->d_lsum, P->d_lpart, feat + (size_t)g * nf, scale + g, s));
     }
     return BTMG_OK;
   }
@@ -1213,24 +1243,31 @@ int btmg_solve(btmg_problem* p, void* psi, double rtol, int32_t max_cycles, btmg
 }
 
 namespace {
+// Coarse canvas of the learned correction: factor f = ceil(max(nx, ny) / 64),
+// canvas ceil(n / f) rounded up to a multiple of 8 (the U-net pools 3 times).
+void learn_canvas(int nx, int ny, int* f, int* h8, int* w8) {
+  const int m = std::max(nx, ny);
+  *f = std::max(1, (m + 63) / 64);
+  *w8 = std::max(8, ((nx + *f - 1) / *f + 7) / 8 * 8);
+  *h8 = std::max(8, ((ny + *f - 1) / *f + 7) / 8 * 8);
+}
+
 int ensure_learn_ws(btmg_problem* P) {
   if (P->d_rho_part) return BTMG_OK;
   const LevelH& L0 = P->lev[0];
-  P->W8 = (L0.nx + 7) / 8 * 8;
-  P->H8 = (L0.ny + 7) / 8 * 8;
-  if (P->W8 < 8) P->W8 = 8;
-  if (P->H8 < 8) P->H8 = 8;
+  learn_canvas(L0.nx, L0.ny, &P->lf, &P->H8, &P->W8);
   const size_t es = dtype_size(P->dtype);
   CK(cudaMalloc(&P->d_rho_part, (size_t)P->G * P->nchunk * L0.npix() * P->csize));
   CK(cudaMalloc(&P->d_feat, sizeof(float) * kLearnFeatures * P->H8 * P->W8));
   CK(cudaMalloc(&P->d_dimg, sizeof(float) * P->H8 * P->W8));
   CK(cudaMalloc(&P->d_lscale, sizeof(float)));
   CK(cudaMalloc(&P->d_lsum, sizeof(double) * 2));
-  CK(cudaMalloc(&P->d_lpart, sizeof(double) * P->n_q_blocks));
+  // partial sums of the canvas features and of the correction's source norm
+  CK(cudaMalloc(&P->d_lpart, sizeof(double) * std::max(2 * kLearnBlocks, P->n_q_blocks)));
   CK(cudaMalloc(&P->d_lc, L0.n() * es));
   CK(cudaMalloc(&P->d_lr, L0.n() * P->csize));
   CK(cudaMalloc(&P->d_lb, L0.npix() * P->csize));
-  CK(cudaMalloc(&P->d_ldot, sizeof(double) * 2));
+  CK(cudaMalloc(&P->d_ldot, sizeof(double) * 4));
   CK(cudaMalloc(&P->d_ldpart, sizeof(double) * kDotBlocks));
   CK(cudaMalloc(&P->d_lstat, sizeof(double) * 3));
   CK(cudaMalloc(&P->d_lphi, (size_t)P->nchunk * L0.npix() * P->csize));
@@ -1254,11 +1291,13 @@ int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every) {
   p->learned = unet;
   p->learn_every = every;
   p->learn_count = 0;
+  p->learn_fallbacks = 0;
   if (p->d_lstat) CK(cudaMemset(p->d_lstat, 0, sizeof(double) * 3));
   return BTMG_OK;
 }
 
-int btmg_learn_stats(btmg_problem* p, int64_t* steps, double* mean_factor, double* last_alpha) {
+int btmg_learn_stats(btmg_problem* p, int64_t* steps, double* mean_factor, double* last_alpha,
+                     int32_t* fallbacks) {
   if (!p) return fail(BTMG_ERR_INVALID_ARG, "null problem");
   double st[3] = {0.0, 0.0, 0.0};
   if (p->d_lstat) {
@@ -1268,13 +1307,17 @@ int btmg_learn_stats(btmg_problem* p, int64_t* steps, double* mean_factor, doubl
   if (steps) *steps = (int64_t)st[1];
   if (mean_factor) *mean_factor = st[1] > 0 ? st[0] / st[1] : 0.0;
   if (last_alpha) *last_alpha = st[2];
+  if (fallbacks) *fallbacks = p->learn_fallbacks;
   return BTMG_OK;
 }
 
-int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8) {
+int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8, int32_t* factor) {
   if (!p) return fail(BTMG_ERR_INVALID_ARG, "null problem");
-  if (h8) *h8 = (p->lev[0].ny + 7) / 8 * 8;
-  if (w8) *w8 = (p->lev[0].nx + 7) / 8 * 8;
+  int f, h, w;
+  learn_canvas(p->lev[0].nx, p->lev[0].ny, &f, &h, &w);
+  if (h8) *h8 = h;
+  if (w8) *w8 = w;
+  if (factor) *factor = f;
   return BTMG_OK;
 }
 

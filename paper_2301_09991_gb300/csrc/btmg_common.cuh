@@ -135,14 +135,18 @@ cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s);
 // thickness, scattering ratio) from the residual-moment partials; apply
 // psi_n += omega * scale * delta / (4 pi) and the flux partial of chunk 0
 constexpr int kLearnFeatures = 4;  // input channels of the learned correction
+constexpr int kLearnBlocks = 32;   // blocks of the coarse-canvas feature kernels
 template <typename C>
 cudaError_t launch_learn_features(const C* rho_part, int nchunk, const C* phi_part, const C* phi_prev, const C* sigt,
-                                  const C* sigs_gg, double dx, int nx, int ny, int W8, int H8, double* d_sum,
-                                  double* d_part, int nblk, float* feat, float* scale_out, cudaStream_t s);
+                                  const C* sigs_gg, double dx, int nx, int ny, int f, int W8, int H8, double* d_sum,
+                                  double* d_part, float* feat, float* scale_out, cudaStream_t s);
+template <typename C>
+cudaError_t launch_dphi_norm(const C* phi_part, int nchunk, const C* phi_prev, int npix, double* d_part, int nblk,
+                             double* out, cudaStream_t s);
 template <typename T, typename C>
-cudaError_t launch_learn_build(T* c_out, C* b_out, const float* delta, const float* scale, const C* sigt,
-                               const C* sigs_gg, const Dir<C>* dir, int nd, int nx, int ny, int W8, double dx,
-                               double dy, double inv_len, cudaStream_t s);
+cudaError_t launch_learn_build(T* c_out, C* b_out, const float* delta, const C* sigt, const C* sigs_gg,
+                               const Dir<C>* dir, int nd, int nx, int ny, int f, int W8, double dx, double dy,
+                               double inv_len, cudaStream_t s);
 template <typename C>
 cudaError_t launch_learn_dot(const C* r1, const C* rc, const Dir<C>* dir, int nx, int ny, int nd, double dxdy,
                              double* part, int nblk, double* out, cudaStream_t s);

@@ -19,8 +19,9 @@ INST_TC(float, float)
 INST_C(float)
 template cudaError_t launch_scale_to<float>(const double*, float*, double, size_t, cudaStream_t);
 template cudaError_t launch_refine_update<float>(double*, const float*, double, size_t, cudaStream_t);
-template cudaError_t launch_learn_features<float>(const float*, int, const float*, const float*, const float*, const float*, double, int, int, int, int, double*, double*, int, float*, float*, cudaStream_t);
-template cudaError_t launch_learn_build<float, float>(float*, float*, const float*, const float*, const float*, const float*, const Dir<float>*, int, int, int, int, double, double, double, cudaStream_t);
 template cudaError_t launch_learn_update<float, float>(float*, const float*, size_t, float*, const float*, size_t, const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_learn_dot<float>(const float*, const float*, const Dir<float>*, int, int, int, double, double*, int, double*, cudaStream_t);
+template cudaError_t launch_learn_build<float, float>(float*, float*, const float*, const float*, const float*, const Dir<float>*, int, int, int, int, int, double, double, double, cudaStream_t);
+template cudaError_t launch_learn_features<float>(const float*, int, const float*, const float*, const float*, const float*, double, int, int, int, int, int, double*, double*, float*, float*, cudaStream_t);
+template cudaError_t launch_dphi_norm<float>(const float*, int, const float*, int, double*, int, double*, cudaStream_t);
 }  // namespace btmg

@@ -17,8 +17,9 @@ INST_TC(double, double)
 INST_C(double)
 template cudaError_t launch_scale_to<double>(const double*, double*, double, size_t, cudaStream_t);
 template cudaError_t launch_refine_update<double>(double*, const double*, double, size_t, cudaStream_t);
-template cudaError_t launch_learn_features<double>(const double*, int, const double*, const double*, const double*, const double*, double, int, int, int, int, double*, double*, int, float*, float*, cudaStream_t);
-template cudaError_t launch_learn_build<double, double>(double*, double*, const float*, const float*, const double*, const double*, const Dir<double>*, int, int, int, int, double, double, double, cudaStream_t);
 template cudaError_t launch_learn_update<double, double>(double*, const double*, size_t, double*, const double*, size_t, const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_learn_dot<double>(const double*, const double*, const Dir<double>*, int, int, int, double, double*, int, double*, cudaStream_t);
+template cudaError_t launch_learn_build<double, double>(double*, double*, const float*, const double*, const double*, const Dir<double>*, int, int, int, int, int, double, double, double, cudaStream_t);
+template cudaError_t launch_learn_features<double>(const double*, int, const double*, const double*, const double*, const double*, double, int, int, int, int, int, double*, double*, float*, float*, cudaStream_t);
+template cudaError_t launch_dphi_norm<double>(const double*, int, const double*, int, double*, int, double*, cudaStream_t);
 }  // namespace btmg

@@ -414,25 +414,6 @@ cudaError_t launch_phi_sum(const C* part, int nchunk, int npix, C* phi, cudaStre
 }
 
 namespace {
-// sum over the padded canvas of rho^2 (per-block partials), rho = sum of chunks
-template <typename C>
-__global__ void k_rho_norm(const C* __restrict__ rho_part, int nchunk, int npix, double* __restrict__ part) {
-  __shared__ double red[8];
-  double acc = 0.0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-    C v = C(0);
-    for (int c = 0; c < nchunk; ++c) v += rho_part[(size_t)c * npix + p];
-    acc += (double)v * (double)v;
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    part[blockIdx.x] = s;
-  }
-}
 // sum over the grid of (phi - phi_prev)^2 (per-block partials), phi = sum of chunks
 template <typename C>
 __global__ void k_dphi_norm(const C* __restrict__ phi_part, int nchunk, const C* __restrict__ phi_prev, int npix,
@@ -454,73 +435,128 @@ __global__ void k_dphi_norm(const C* __restrict__ phi_part, int nchunk, const C*
     part[blockIdx.x] = s;
   }
 }
-// features of the learned correction on a W8 x H8 canvas (zeros outside):
-// rho / rms(rho), log(sigma_t dx + 1e-3) / 4, sigma_s / sigma_t and
-// (phi - phi_prev) / rms(phi - phi_prev) (0 without phi_prev)
+// Features of the learned correction on the coarse canvas W8 x H8: canvas
+// pixel (X, Y) averages the fine nodes [X f, X f + f) x [Y f, Y f + f) of
+// the grid (cut at its edge; zeros outside the ncx x ncy covered pixels):
+//   0 mean rho (normalised afterwards),  1 log(mean sigma_t * f dx + 1e-3) / 4,
+//   2 mean sigma_s / mean sigma_t,       3 mean (phi - phi_prev) (normalised
+//   afterwards; 0 without phi_prev).
+// part[blk], part[nblk + blk]: partial sums of channel 0 and 3 squared.
 template <typename C>
-__global__ void k_learn_features(const C* __restrict__ rho_part, int nchunk, const C* __restrict__ phi_part,
-                                 const C* __restrict__ phi_prev, const C* __restrict__ sigt,
-                                 const C* __restrict__ sigs_gg, double dx, int nx, int ny, int W8, int H8,
-                                 const double* __restrict__ d_sum, float* __restrict__ feat,
-                                 float* __restrict__ scale_out) {
-  const int npix = nx * ny;
-  const double rms = sqrt(d_sum[0] / (double)npix);
-  const double inv = rms > 0 ? 1.0 / rms : 0.0;
-  const double rms_d = phi_prev ? sqrt(d_sum[1] / (double)npix) : 0.0;
-  const double inv_d = rms_d > 0 ? 1.0 / rms_d : 0.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) scale_out[0] = (float)rms;
+__global__ void k_learn_coarse(const C* __restrict__ rho_part, const C* __restrict__ phi_part,
+                               const C* __restrict__ phi_prev, int nchunk, const C* __restrict__ sigt,
+                               const C* __restrict__ sigs_gg, int nx, int ny, int f, int ncx, int ncy, int W8, int H8,
+                               double dXc, float* __restrict__ feat, double* __restrict__ part) {
+  __shared__ double red0[8], red3[8];
+  const size_t npix = (size_t)nx * ny;
+  double a0 = 0.0, a3 = 0.0;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < W8 * H8; q += gridDim.x * blockDim.x) {
-    const int x = q % W8, y = q / W8;
+    const int X = q % W8, Y = q / W8;
     float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
-    if (x < nx && y < ny) {
-      const int p = y * nx + x;
-      C v = C(0), ph = C(0);
-      for (int c = 0; c < nchunk; ++c) v += rho_part[(size_t)c * npix + p];
-      const double st = (double)sigt[p];
-      f0 = (float)((double)v * inv);
-      f1 = (float)(0.25 * log(st * dx + 1e-3));
-      f2 = st > 0 ? (float)((double)sigs_gg[p] / st) : 0.f;
-      if (phi_prev) {
-        for (int c = 0; c < nchunk; ++c) ph += phi_part[(size_t)c * npix + p];
-        f3 = (float)(((double)ph - (double)phi_prev[p]) * inv_d);
-      }
+    if (X < ncx && Y < ncy) {
+      double r = 0.0, st = 0.0, ss = 0.0, dp = 0.0;
+      int cnt = 0;
+      for (int y = Y * f; y < min(Y * f + f, ny); ++y)
+        for (int x = X * f; x < min(X * f + f, nx); ++x) {
+          const size_t p = (size_t)y * nx + x;
+          C v = C(0);
+          for (int c = 0; c < nchunk; ++c) v += rho_part[(size_t)c * npix + p];
+          r += (double)v;
+          st += (double)sigt[p];
+          ss += (double)sigs_gg[p];
+          if (phi_prev) {
+            C ph = C(0);
+            for (int c = 0; c < nchunk; ++c) ph += phi_part[(size_t)c * npix + p];
+            dp += (double)ph - (double)phi_prev[p];
+          }
+          ++cnt;
+        }
+      const double inv = 1.0 / (double)cnt;
+      f0 = (float)(r * inv);
+      f1 = (float)(0.25 * log(st * inv * dXc + 1e-3));
+      f2 = st > 0 ? (float)(ss / st) : 0.f;
+      f3 = (float)(dp * inv);
+      a0 += (double)f0 * f0;
+      a3 += (double)f3 * f3;
     }
-    float* f = feat + (size_t)q * kLearnFeatures;
-    f[0] = f0;
-    f[1] = f1;
-    f[2] = f2;
-    f[3] = f3;
+    float* o = feat + (size_t)q * kLearnFeatures;
+    o[0] = f0;
+    o[1] = f1;
+    o[2] = f2;
+    o[3] = f3;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red0[threadIdx.x >> 5] = a0;
+    red3[threadIdx.x >> 5] = a3;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s3 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      s0 += red0[w];
+      s3 += red3[w];
+    }
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s3;
+  }
+}
+// channels 0 and 3 divided by their rms over the covered canvas pixels;
+// scale_out = rms of channel 0
+__global__ void k_learn_normalise(float* __restrict__ feat, int n, int ncov, const double* __restrict__ d_sum,
+                                  float* __restrict__ scale_out) {
+  const double r0 = sqrt(d_sum[0] / (double)ncov), r3 = sqrt(d_sum[1] / (double)ncov);
+  const float i0 = r0 > 0 ? (float)(1.0 / r0) : 0.f, i3 = r3 > 0 ? (float)(1.0 / r3) : 0.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) scale_out[0] = (float)r0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    feat[(size_t)q * kLearnFeatures + 0] *= i0;
+    feat[(size_t)q * kLearnFeatures + 3] *= i3;
   }
 }
 // Learned correction as a P1 angular flux (Sec. 2.5 scalar flux, Fick's law
-// closure): the predicted scalar-flux error e (U-net output times the input
-// scale) becomes c_n = (e - (mu_n de/dx + nu_n de/dy) / sigma) / (4 pi), with
-// sigma = max(sigma_t, 1 / domain length) and central differences (one-sided
-// at the edges).  b_out = (sigma_s,gg / 4 pi) e is the in-group scattering
-// source of c, so that a residual evaluation of c with b_out gives -L c.
+// closure): e = the U-net output on the coarse canvas, interpolated
+// bilinearly to the fine nodes (canvas pixel X is centred on fine
+// coordinate (X + 1/2) f - 1/2, clamped at the covered edge), becomes
+// c_n = (e - (mu_n de/dx + nu_n de/dy) / sigma) / (4 pi), with
+// sigma = max(sigma_t, 1 / domain length) and central differences
+// (one-sided at the edges).  b_out = (sigma_s,gg / 4 pi) e is the in-group
+// scattering source of c, so that a residual evaluation of c with b_out
+// gives -L c.
 template <typename T, typename C>
 __global__ void k_learn_build(T* __restrict__ c_out, C* __restrict__ b_out, const float* __restrict__ delta,
-                              const float* __restrict__ scale, const C* __restrict__ sigt,
-                              const C* __restrict__ sigs_gg, const Dir<C>* __restrict__ dir, int nd, int nx, int ny,
-                              int W8, double inv_dx, double inv_dy, double inv_len) {
+                              const C* __restrict__ sigt, const C* __restrict__ sigs_gg,
+                              const Dir<C>* __restrict__ dir, int nd, int nx, int ny, int W8, int f, int ncx, int ncy,
+                              float inv_dx, float inv_dy, float inv_len) {
   const size_t npix = (size_t)nx * ny, total = (size_t)nd * npix;
-  const double a = scale ? (double)scale[0] : 1.0;
-  const double inv4pi = 0.07957747154594767;
+  const float inv4pi = 0.07957747154594767f, invf = 1.f / (float)f;
+  auto E = [&](int x, int y) {
+    float u = ((float)x + 0.5f) * invf - 0.5f, v = ((float)y + 0.5f) * invf - 0.5f;
+    u = fminf(fmaxf(u, 0.f), (float)(ncx - 1));
+    v = fminf(fmaxf(v, 0.f), (float)(ncy - 1));
+    const int i0 = (int)u, j0 = (int)v;
+    const int i1 = min(i0 + 1, ncx - 1), j1 = min(j0 + 1, ncy - 1);
+    const float tu = u - (float)i0, tv = v - (float)j0;
+    const float a = delta[(size_t)j0 * W8 + i0], b = delta[(size_t)j0 * W8 + i1];
+    const float c = delta[(size_t)j1 * W8 + i0], d = delta[(size_t)j1 * W8 + i1];
+    return (1.f - tv) * ((1.f - tu) * a + tu * b) + tv * ((1.f - tu) * c + tu * d);
+  };
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t p = i % npix;
     const int n = (int)(i / npix);
     const int x = (int)(p % nx), y = (int)(p / nx);
-    auto E = [&](int xx, int yy) { return a * (double)delta[(size_t)yy * W8 + xx]; };
-    const double e = E(x, y);
+    const float e = E(x, y);
     const int xl = x > 0 ? x - 1 : x, xr = x + 1 < nx ? x + 1 : x;
     const int yl = y > 0 ? y - 1 : y, yr = y + 1 < ny ? y + 1 : y;
-    const double ex = xr > xl ? (E(xr, y) - E(xl, y)) * inv_dx / (double)(xr - xl) : 0.0;
-    const double ey = yr > yl ? (E(x, yr) - E(x, yl)) * inv_dy / (double)(yr - yl) : 0.0;
-    const double st = (double)sigt[p];
-    const double sg = st > inv_len ? st : inv_len;
-    const double v = (e - ((double)dir[n].mu * ex + (double)dir[n].nu * ey) / sg) * inv4pi;
+    const float ex = xr > xl ? (E(xr, y) - E(xl, y)) * inv_dx / (float)(xr - xl) : 0.f;
+    const float ey = yr > yl ? (E(x, yr) - E(x, yl)) * inv_dy / (float)(yr - yl) : 0.f;
+    const float st = (float)sigt[p];
+    const float sg = st > inv_len ? st : inv_len;
+    const float v = (e - ((float)dir[n].mu * ex + (float)dir[n].nu * ey) / sg) * inv4pi;
     Conv<T>::st(c_out + i, (C)v);
-    if (n == 0) b_out[p] = (C)((double)sigs_gg[p] * e * inv4pi);
+    if (n == 0) b_out[p] = (C)((float)sigs_gg[p] * e * inv4pi);
   }
 }
 // partial sums of sum_n p_n dx dy r1 rc over one group (the residual weight)
@@ -542,23 +578,30 @@ __global__ void k_learn_dot(const C* __restrict__ r1, const C* __restrict__ rc, 
   }
 }
 // Step length minimising the weighted residual norm along c:
-// r(psi + alpha c) = r + alpha rc, alpha = -<r, rc> / <rc, rc>, |alpha| <= 1e6
-// (0 if <rc, rc> is 0 or not finite); psi += alpha c and the scalar-flux
-// partials phi += alpha phi_c.  ldot = {<r, rc>, <rc, rc>}; rn2 = <r, r>;
-// stat accumulates the residual reduction factor of the step, the step
-// count and the last alpha.
-__device__ __forceinline__ double learn_alpha(const double* ldot) {
-  const double d = ldot[0], nn = ldot[1];
-  double al = (nn > 0.0 && isfinite(nn) && isfinite(d)) ? -d / nn : 0.0;
-  return al > 1e6 ? 1e6 : (al < -1e6 ? -1e6 : al);
+// r(psi + alpha c) = r + alpha rc, alpha = -<r, rc> / <rc, rc>, then psi +=
+// alpha c and the scalar-flux partials phi += alpha phi_c.
+// ldot = {<r, rc>, <rc, rc>, sum phi_c^2, sum dphi^2} (dphi = the plain
+// cycle's scalar-flux update); rn2 = <r, r>.  Guards: alpha = 0 when a sum is
+// not finite, <rc, rc> = 0 or the predicted reduction of ||r||^2 is below
+// 1e-4 (a step of rounding noise); |alpha| rms(phi_c) <= 1e3 rms(dphi) (any
+// alpha between 0 and the minimiser still lowers the residual).  stat
+// accumulates the residual reduction factor, the step count and the last
+// alpha.
+__device__ __forceinline__ double learn_alpha(const double* ldot, double rr) {
+  const double d = ldot[0], nn = ldot[1], pc = ldot[2], dp = ldot[3];
+  if (!(nn > 0.0) || !isfinite(nn) || !isfinite(d) || !isfinite(pc) || !isfinite(dp) || !(rr > 0.0)) return 0.0;
+  if (d * d < 1e-4 * nn * rr) return 0.0;
+  double al = -d / nn;
+  const double cap = pc > 0.0 ? 1e3 * sqrt(dp / pc) : 0.0;
+  return al > cap ? cap : (al < -cap ? -cap : al);
 }
 template <typename T, typename C>
 __global__ void k_learn_update(T* __restrict__ psi, const T* __restrict__ c, size_t n, C* __restrict__ phi,
                                const C* __restrict__ phi_c, size_t nphi, const double* __restrict__ ldot,
                                const double* __restrict__ rn2, double* __restrict__ stat) {
-  const double al = learn_alpha(ldot);
+  const double rr = rn2[0];
+  const double al = learn_alpha(ldot, rr);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const double rr = rn2[0];
     const double after = rr + 2.0 * al * ldot[0] + al * al * ldot[1];
     stat[0] += (rr > 0.0 && after > 0.0) ? sqrt(after / rr) : 0.0;
     stat[1] += 1.0;
@@ -585,26 +628,31 @@ __global__ void k_refine_update(double* __restrict__ psi64, const T* __restrict_
 
 template <typename C>
 cudaError_t launch_learn_features(const C* rho_part, int nchunk, const C* phi_part, const C* phi_prev, const C* sigt,
-                                  const C* sigs_gg, double dx, int nx, int ny, int W8, int H8, double* d_sum,
-                                  double* d_part, int nblk, float* feat, float* scale_out, cudaStream_t s) {
-  k_rho_norm<C><<<nblk, 256, 0, s>>>(rho_part, nchunk, nx * ny, d_part);
-  k_sum_fwd(d_part, nblk, d_sum, s);
-  if (phi_prev) {
-    k_dphi_norm<C><<<nblk, 256, 0, s>>>(phi_part, nchunk, phi_prev, nx * ny, d_part);
-    k_sum_fwd(d_part, nblk, d_sum + 1, s);
-  }
-  k_learn_features<C><<<grid_for((size_t)W8 * H8, 256), 256, 0, s>>>(rho_part, nchunk, phi_part, phi_prev, sigt,
-                                                                       sigs_gg, dx, nx, ny, W8, H8, d_sum, feat,
-                                                                       scale_out);
+                                  const C* sigs_gg, double dx, int nx, int ny, int f, int W8, int H8, double* d_sum,
+                                  double* d_part, float* feat, float* scale_out, cudaStream_t s) {
+  const int ncx = (nx + f - 1) / f, ncy = (ny + f - 1) / f;
+  k_learn_coarse<C><<<kLearnBlocks, 256, 0, s>>>(rho_part, phi_part, phi_prev, nchunk, sigt, sigs_gg, nx, ny, f, ncx,
+                                                 ncy, W8, H8, dx * f, feat, d_part);
+  k_sum_fwd(d_part, kLearnBlocks, d_sum, s);
+  k_sum_fwd(d_part + kLearnBlocks, kLearnBlocks, d_sum + 1, s);
+  k_learn_normalise<<<kLearnBlocks, 256, 0, s>>>(feat, W8 * H8, ncx * ncy, d_sum, scale_out);
   return cudaGetLastError();
 }
 template <typename T, typename C>
-cudaError_t launch_learn_build(T* c_out, C* b_out, const float* delta, const float* scale, const C* sigt,
-                               const C* sigs_gg, const Dir<C>* dir, int nd, int nx, int ny, int W8, double dx,
-                               double dy, double inv_len, cudaStream_t s) {
-  k_learn_build<T, C><<<grid_for((size_t)nd * nx * ny, 256), 256, 0, s>>>(c_out, b_out, delta, scale, sigt, sigs_gg,
-                                                                         dir, nd, nx, ny, W8, 1.0 / dx, 1.0 / dy,
-                                                                         inv_len);
+cudaError_t launch_learn_build(T* c_out, C* b_out, const float* delta, const C* sigt, const C* sigs_gg,
+                               const Dir<C>* dir, int nd, int nx, int ny, int f, int W8, double dx, double dy,
+                               double inv_len, cudaStream_t s) {
+  const int ncx = (nx + f - 1) / f, ncy = (ny + f - 1) / f;
+  k_learn_build<T, C><<<grid_for((size_t)nd * nx * ny, 256), 256, 0, s>>>(
+      c_out, b_out, delta, sigt, sigs_gg, dir, nd, nx, ny, W8, f, ncx, ncy, (float)(1.0 / dx), (float)(1.0 / dy),
+      (float)inv_len);
+  return cudaGetLastError();
+}
+template <typename C>
+cudaError_t launch_dphi_norm(const C* phi_part, int nchunk, const C* phi_prev, int npix, double* d_part, int nblk,
+                             double* out, cudaStream_t s) {
+  k_dphi_norm<C><<<nblk, 256, 0, s>>>(phi_part, nchunk, phi_prev, npix, d_part);
+  k_sum_fwd(d_part, nblk, out, s);
   return cudaGetLastError();
 }
 template <typename C>

@@ -17,8 +17,8 @@ INST_TC(__nv_bfloat16, float)
 INST_TC(__half, float)
 template cudaError_t launch_refine_update<__nv_bfloat16>(double*, const __nv_bfloat16*, double, size_t, cudaStream_t);
 template cudaError_t launch_refine_update<__half>(double*, const __half*, double, size_t, cudaStream_t);
-template cudaError_t launch_learn_build<__nv_bfloat16, float>(__nv_bfloat16*, float*, const float*, const float*, const float*, const float*, const Dir<float>*, int, int, int, int, double, double, double, cudaStream_t);
 template cudaError_t launch_learn_update<__nv_bfloat16, float>(__nv_bfloat16*, const __nv_bfloat16*, size_t, float*, const float*, size_t, const double*, const double*, double*, cudaStream_t);
-template cudaError_t launch_learn_build<__half, float>(__half*, float*, const float*, const float*, const float*, const float*, const Dir<float>*, int, int, int, int, double, double, double, cudaStream_t);
 template cudaError_t launch_learn_update<__half, float>(__half*, const __half*, size_t, float*, const float*, size_t, const double*, const double*, double*, cudaStream_t);
+template cudaError_t launch_learn_build<__nv_bfloat16, float>(__nv_bfloat16*, float*, const float*, const float*, const float*, const Dir<float>*, int, int, int, int, int, double, double, double, cudaStream_t);
+template cudaError_t launch_learn_build<__half, float>(__half*, float*, const float*, const float*, const float*, const Dir<float>*, int, int, int, int, int, double, double, double, cudaStream_t);
 }  // namespace btmg

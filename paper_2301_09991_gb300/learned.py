@@ -33,14 +33,14 @@ CYCLES = (1, 3, 6, 10, 20, 40, 70, 100, 140, 180)
 
 
 def training_problem(seed, n=64, n_polar=8, n_azim=16, c=None, length=None):
-    """Config-2-class problem in the scattering-dominated regime: checkerboard
-    of sigma_t ~ logU[0.1, 10] with a seeded block count (4 or 8 per side),
-    scattering ratio c ~ U[0.95, 0.995] and domain side ~ logU[3, 30] (or the
-    given c and side)."""
+    """Config-2-class problem reaching into the scattering-dominated regime:
+    checkerboard of sigma_t ~ logU[0.1, 10] with a seeded block count (4 or 8
+    per side), scattering ratio c ~ U[0.9, 0.995] and domain side
+    ~ logU[1, 30] (or the given c and side)."""
     rng = np.random.default_rng(10_000 + seed)
     blocks = int(rng.choice([4, 8]))
-    cc = float(rng.uniform(0.95, 0.995))
-    ll = float(np.exp(rng.uniform(np.log(3.0), np.log(30.0))))
+    cc = float(rng.uniform(0.9, 0.995))
+    ll = float(np.exp(rng.uniform(np.log(1.0), np.log(30.0))))
     c = cc if c is None else c
     length = ll if length is None else length
     return I.checkerboard(n=n, n_polar=n_polar, n_azim=n_azim, blocks=blocks, seed=seed, c=c, length=length)
@@ -57,28 +57,50 @@ def reference_flux(prob, rtol=1e-9):
     return phi, out["rel_resid"]
 
 
-def pairs_for_problem(prob, cycles=CYCLES):
-    """Features and targets [m][H8][W8][4], [m][H8][W8] (torch, CUDA)."""
+def pairs_for_problem(prob, cycles=CYCLES, min_rel=1e-4):
+    """Features and targets [m][H8][W8][4], [m][H8][W8] (torch, CUDA); an
+    iterate whose relative residual is below min_rel gives no pair (its
+    error is mostly FP32 rounding)."""
     import torch
     phi_star, _ = reference_flux(prob)
     gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
     psi = gp.zeros()
     X, Y = [], []
-    ny, nx = gp.shape[2], gp.shape[3]
+    _, _, f = gp.learn_canvas()
     prev = None
     for k in range(max(cycles) + 1):
         if k in cycles:
             feat, _ = gp.learn_features(psi, prev)
-            err = (phi_star - gp.scalar_flux(psi).double())[0]
+            err = coarse_mean((phi_star - gp.scalar_flux(psi).double())[0], f)
             err = err / max(float(torch.sqrt(torch.mean(err * err))), 1e-300)
             tgt = torch.zeros(feat.shape[1:3], dtype=torch.float32, device="cuda")
-            tgt[:ny, :nx] = err.float()
+            tgt[:err.shape[0], :err.shape[1]] = err.float()
             X.append(feat[0].clone())
             Y.append(tgt)
         if k + 1 in cycles:
             prev = psi.clone()
-        gp.mg_cycle(psi, want_residual=False)
-    return torch.stack(X), torch.stack(Y)
+        rel = gp.mg_cycle(psi)
+        if k in cycles and rel < min_rel:
+            X.pop()
+            Y.pop()
+            break
+    return torch.stack(X) if X else None, torch.stack(Y) if Y else None
+
+
+def coarse_mean(img, f):
+    """Means of img [ny][nx] over f x f blocks (cut at the edge), the
+    averaging of the learned correction's coarse canvas."""
+    import torch
+    if f == 1:
+        return img
+    ny, nx = img.shape
+    cy, cx = -(-ny // f), -(-nx // f)
+    pad = torch.zeros((cy * f, cx * f), dtype=img.dtype, device=img.device)
+    cnt = torch.zeros_like(pad)
+    pad[:ny, :nx] = img
+    cnt[:ny, :nx] = 1.0
+    s = pad.reshape(cy, f, cx, f).sum(dim=(1, 3))
+    return s / cnt.reshape(cy, f, cx, f).sum(dim=(1, 3))
 
 
 def d4(X, Y):
@@ -94,12 +116,15 @@ def d4(X, Y):
     return torch.cat(xs), torch.cat(ys)
 
 
-def make_dataset(seeds, n=64, n_polar=8, n_azim=16, augment=True, log=None):
+def make_dataset(plan, n_polar=8, n_azim=16, augment=True, log=None):
+    """plan: [(seed, n)]; all canvases are 64 x 64 for n in {64, 128, 256}."""
     import torch
     Xs, Ys = [], []
     t0 = time.time()
-    for i, s in enumerate(seeds):
+    for i, (s, n) in enumerate(plan):
         X, Y = pairs_for_problem(training_problem(s, n, n_polar, n_azim))
+        if X is None:
+            continue
         Xs.append(X)
         Ys.append(Y)
         if log and (i + 1) % 50 == 0:
@@ -140,7 +165,7 @@ def solve_cycles(prob, net=None, rtol=1e-5, max_cycles=2000, dtype=btmg.F32, eve
     out = gp.solve(psi, rtol=rtol, max_cycles=max_cycles)
     torch.cuda.synchronize()
     out["seconds"] = time.perf_counter() - t0
-    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0.0, 0.0)
+    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0.0, 0.0, 0)
     return out, psi
 
 
@@ -156,7 +181,7 @@ def refined_cycles(prob, net=None, rtol=1e-6, inner=4, dtype=btmg.F32, max_outer
     out = gp.solve_refined(psi64, rtol=rtol, max_outer=max_outer, inner_cycles=inner)
     torch.cuda.synchronize()
     out["seconds"] = time.perf_counter() - t0
-    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0.0, 0.0)
+    out["learn_stats"] = gp.learn_stats() if net is not None else (0, 0.0, 0.0, 0)
     return out, psi64
 
 
@@ -171,14 +196,19 @@ def main():
     ap.add_argument("cmd", choices=["train", "eval"])
     ap.add_argument("--out", default="learned_unet.npy")
     ap.add_argument("--weights", default=None)
-    ap.add_argument("--problems", type=int, default=250)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--mix", default="64:200,128:60,256:30",
+                    help="grid size:problem count, comma separated (seeds from 1000 on)")
+    ap.add_argument("--steps", type=int, default=4000)
     args = ap.parse_args()
     log = lambda m: print(m, flush=True)
     if args.cmd == "train":
         t0 = time.time()
-        X, Y = make_dataset(range(1000, 1000 + args.problems), n=args.n, log=log)
+        plan, seed = [], 1000
+        for item in args.mix.split(","):
+            n, count = (int(v) for v in item.split(":"))
+            plan += [(seed + i, n) for i in range(count)]
+            seed += count
+        X, Y = make_dataset(plan, log=log)
         log("dataset: %d pairs of %s (%.0f s)" % (X.shape[0], tuple(X.shape[1:]), time.time() - t0))
         net = btmg.UNet(in_channels=btmg.LEARN_FEATURES, seed=1)
         t1 = time.time()
@@ -189,19 +219,28 @@ def main():
     else:
         import torch
         net = load_net(args.weights)
-        for s, c, L, n in ((5000, 0.99, 10.0, 64), (5001, 0.99, 30.0, 64), (5002, 0.98, 20.0, 128),
-                           (5003, 0.99, 30.0, 128)):
-            prob = training_problem(s, n=n, c=c, length=L)
-            plain, p0 = solve_cycles(prob, None)
-            solve_cycles(prob, net)  # warm-up: graphs and U-net workspaces
-            for every in (1, 2, 4):
-                learn, p1 = solve_cycles(prob, net, every=every)
-                diff = float(torch.linalg.norm(p1 - p0) / torch.linalg.norm(p0))
-                st = learn["learn_stats"]
-                log("seed %d n %d L %g c %.3f every %d: plain %d cycles %.3f s, learned %d cycles %.3f s "
-                    "(%d steps, mean factor %.3f), solution diff %.1e"
-                    % (s, n, L, c, every, plain["cycles"], plain["seconds"], learn["cycles"], learn["seconds"],
-                       st[0], st[1], diff))
+        cases = (("solve", 5001, 64, 8, 16, 0.99, 30.0), ("solve", 5003, 128, 8, 16, 0.99, 30.0),
+                 ("solve", 5002, 128, 8, 16, 0.98, 20.0), ("refined", 5010, 256, 16, 32, 0.99, 30.0),
+                 ("refined", 5011, 256, 16, 32, 0.95, 3.0), ("refined", 5012, 512, 32, 32, 0.99, 30.0),
+                 ("refined", 5000, 512, 32, 32, 0.9, 1.0))
+        for mode, s, n, npol, naz, c, L in cases:
+            prob = training_problem(s, n=n, n_polar=npol, n_azim=naz, c=c, length=L)
+            if mode == "solve":
+                f = lambda nt, ev: solve_cycles(prob, nt, rtol=1e-5, max_cycles=3000, every=ev)
+            else:
+                f = lambda nt, ev: refined_cycles(prob, nt, rtol=1e-6, inner=8, every=ev, max_outer=400)
+            f(None, 1)  # warm-up
+            plain, p0 = f(None, 1)
+            row = dict(case="%s n%d %dx%d c%.3f L%g" % (mode, n, npol, naz, c, L),
+                       plain=dict(cycles=plain["cycles"], s=round(plain["seconds"], 4), rel=plain["rel_resid"]))
+            for every in (2, 4):
+                f(net, every)
+                lr, p1 = f(net, every)
+                st = lr["learn_stats"]
+                row["every%d" % every] = dict(cycles=lr["cycles"], s=round(lr["seconds"], 4), rel=lr["rel_resid"],
+                                              steps=st[0], factor=round(st[1], 4), fallbacks=st[3],
+                                              diff=float(torch.linalg.norm(p1 - p0) / torch.linalg.norm(p0)))
+            print(json.dumps(row), flush=True)
 
 if __name__ == "__main__":
     main()
