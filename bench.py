@@ -8,9 +8,20 @@ residual norm.  Default workload: 256 x 256 nodes, 16 x 32 directions (512),
 one group, seeded 8 x 8 checkerboard of sigma_t ~ logU[0.1, 10], scattering
 ratio 0.9, source 1, vacuum, quadratic ConvFEM with PG, psi in FP32.
 
-Metric: MG unknown-updates/s = (unknowns x cycles) / seconds, all ranks.
-Multi-GPU runs are independent replicas (one problem per rank, no
-collective on the data path; the path does not need one).
+Metric: MG unknown-updates/s = (unknowns x cycles) / seconds, all ranks;
+the timed cycles run as the library's captured CUDA graph (btmg_solve with
+a fixed cycle count), the per-kernel shares come from an eager, event-timed
+run of the same cycles.  Multi-GPU runs are independent replicas (one
+problem per rank, no collective on the data path; the path does not need
+one).
+
+The second half of the metric, time to a 1e-6 relative residual (learned vs
+plain multigrid), is reported under "time_to_1e-6" for the learned-
+correction evaluation workload (512 x 512 nodes, 32 x 32 directions, the
+checkerboard family at held-out seed 5000) and for a scattering-dominated
+case (256 x 256, 16 x 32, domain side 30, c = 0.99): plain FP32 multigrid,
+FP64-refined FP32 and BF16 inner cycles, and FP64-refined FP32 with the
+learned correction every 4th cycle.
 
 --impl reference times the FP64 CPU oracle (the slow reference program of
 this repository) on the host cores, on a bounded sample of the workload.
@@ -197,6 +208,62 @@ def run_reference(args):
     return 0
 
 
+def time_to_residual(btmg, torch, rtol=1e-6):
+    """Seconds (wall, synchronised) and cycles to a relative residual of rtol
+    for plain FP32 multigrid, FP64-refined FP32 / BF16 inner cycles and
+    FP64-refined FP32 with the learned correction (upwind fine operator,
+    pg = 0, for which the FP64 refinement is defined)."""
+    from paper_2301_09991_gb300 import learned as LN
+    net = LN.load_net(os.path.join(ROOT, "paper_2301_09991_gb300", "weights", "unet_thick.npy"))
+    cases = {
+        "checker512_32x32_seed5000": (I.checkerboard(n=512, n_polar=32, n_azim=32, blocks=8, seed=5000, c=0.9),
+                                      "512x512 nodes, 32x32 dirs, unit square, c=0.9 (held-out seed)"),
+        "thick256_16x32_L30_c0.99": (LN.training_problem(5010, n=256, n_polar=16, n_azim=32, c=0.99, length=30.0),
+                                     "256x256 nodes, 16x32 dirs, side 30, c=0.99 (held-out seed)"),
+    }
+    out = {}
+    for name, (prob, desc) in cases.items():
+        row = {"description": desc}
+
+        def timed(fn):
+            fn()  # warm-up: workspaces, graphs, twin problem
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            return r, time.perf_counter() - t0
+
+        gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+        psi = gp.zeros()
+
+        def plain():
+            psi.zero_()
+            return gp.solve(psi, rtol=rtol, max_cycles=600, check_every=10, history=False)
+        r, sec = timed(plain)
+        row["plain_f32"] = {"seconds": round(sec, 4), "cycles": r["cycles"], "rel_resid": r["rel_resid"],
+                            "reached": bool(r["rel_resid"] <= rtol)}
+        del gp, psi
+        for key, dt, nt in (("refined_f32", btmg.F32, None), ("refined_bf16", btmg.BF16, None),
+                            ("refined_f32_learned", btmg.F32, net)):
+            gp = btmg.Problem(prob, dtype=dt, pg=0)
+            if nt is not None:
+                gp.set_learned(nt, every=4)
+            psi64 = torch.zeros(gp.shape, dtype=torch.float64, device="cuda")
+
+            def refined():
+                psi64.zero_()
+                return gp.solve_refined(psi64, rtol=rtol, max_outer=300, inner_cycles=8)
+            r, sec = timed(refined)
+            row[key] = {"seconds": round(sec, 4), "cycles": r["cycles"], "rel_resid": r["rel_resid"],
+                        "reached": bool(r["rel_resid"] <= rtol)}
+            if nt is not None:
+                st = gp.learn_stats()
+                row[key].update({"learned_steps": st[0], "fallbacks": st[3]})
+            del gp, psi64
+        out[name] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -208,6 +275,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cycles", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-6 section")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -231,8 +299,9 @@ def main():
     N = gp.num_unknowns()
     psi = gp.zeros()
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        gp.mg_cycle(psi, want_residual=False)
+    # warm-up: its first cycle runs eagerly, the second captures the cycle
+    # graph for this psi and stream, which the timed call then replays
+    gp.solve(psi, rtol=0.0, max_cycles=args.warmup, check_every=args.warmup, history=False)
     torch.cuda.synchronize()
 
     def barrier():
@@ -244,24 +313,34 @@ def main():
     clocks.start()
     time.sleep(0.3)
     barrier()
-    gp.profile(True)
-    n0 = gp.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
-        gp.mg_cycle(psi, want_residual=False)
+    out = gp.solve(psi, rtol=0.0, max_cycles=args.steps, check_every=args.steps, history=False)
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1)
-    prof = gp.profile_read()
-    gp.profile(False)
-    launches = gp.launch_count() - n0
     clk = clocks.stop()
+    assert out["cycles"] == args.steps, out
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     value = N * args.steps * ws / (ms / 1000.0)
+
+    # per-kernel device times: the same cycles eagerly, each launch bracketed
+    # by CUDA events on the launching stream
+    n_prof = min(args.steps, 10)
+    gp.profile(True)
+    n0 = gp.launch_count()
+    for _ in range(n_prof):
+        gp.mg_cycle(psi, want_residual=False)
+    torch.cuda.synchronize()
+    prof = gp.profile_read()
+    gp.profile(False)
+    per_cycle = (gp.launch_count() - n0) / n_prof
+    # the timed solve: the cycles' kernels plus one final residual evaluation
+    # (phi partials, source, norm sums and the residual kernel)
+    launches = int(round(per_cycle * args.steps)) + 4 * gp.G + gp.G
 
     # end to end through the public call with host buffers: H2D of psi from
     # pinned memory, one cycle, D2H of psi and of the FP64 residual
@@ -290,7 +369,8 @@ def main():
         achieved = PG_FLOPS_PER_UNKNOWN * per_launch_unknowns / avg_s / 1e12
         peak = fp32_peak_tflops(sm_mhz)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_from_profiles("k_pg"),
+                "frac": achieved / peak,
+                "traffic": traffic_from_profiles("k_pg_resid" if dom == "pg_residual" else "k_pg_jacobi"),
                 "kernel": "k_pg (%s)" % dom,
                 "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz}
     else:
@@ -300,7 +380,7 @@ def main():
         achieved = byts / avg_s / 1e9
         peak = float(pk["hbm_gbs"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_from_profiles("k_upwind"), "kernel": "k_upwind (%s)" % dom,
+                "traffic": traffic_from_profiles("k_upwind_fine"), "kernel": "k_upwind (%s)" % dom,
                 "peak_source": "%s copy bandwidth" % src}
     roof["kernel_ms"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items()}
     roof["kernel_share"] = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()}
@@ -313,6 +393,8 @@ def main():
                        "l2": "inputs larger than L2 (psi, psi_tmp and r_1 are %d MB each)"
                              % (nbytes // 2 ** 20)},
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and not args.no_ttr:
+        line["time_to_1e-6"] = time_to_residual(btmg, torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)
     if rank == 0:
