@@ -81,6 +81,12 @@ typedef struct {
   int32_t psi_dtype;       /* BTMG_F64 / BTMG_F32 / BTMG_BF16 / BTMG_F16     */
   int32_t max_levels;      /* 0: coarsen until every dimension is 1          */
   int32_t pg_half;         /* 1: scale f^{k-Diff} by 1/2 (analytic form)     */
+  int32_t chunks;          /* direction chunks per group (CTAs along the
+                              direction axis of the fine kernels): 0 picks the
+                              count whose grid best fills whole waves of
+                              resident CTAs; otherwise a divisor of the number
+                              of directions, at most 64 (set by the batch
+                              autotuner)                                     */
 } btmg_problem_desc;
 
 typedef struct {
@@ -249,6 +255,45 @@ int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8, int32_t* 
  * rms of the mean rho of each group.                                       */
 int btmg_learn_features(btmg_problem* p, const void* psi, const void* psi_prev, float* feat, float* scale,
                         void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched solves of independent problems (no counterpart in the paper: its
+ * solver treats one problem at a time).
+ *
+ * btmg_create_batch creates n problems from descs[0..n-1] (each as
+ * btmg_create_problem).  With autotune = 1, the direction-chunk count of
+ * every distinct problem shape (nx, ny, directions, groups, psi_dtype, pg,
+ * nu_jacobi) is chosen by timing: each candidate divisor of the direction
+ * count (at most 64, within a factor 4 of the automatic choice) runs 2
+ * warm-up and 3 timed eager cycles on a scratch copy of the problem (CUDA
+ * events on `stream`); the fastest is kept.  Choices are cached per shape
+ * for the life of the process.  descs[i].chunks != 0 is kept as given.
+ *
+ * btmg_solve_batch solves every problem i from its caller-owned device
+ * psi[i] (layout of btmg_get_layout; initial guess in, solution out): one
+ * eager cycle per problem, then each problem's whole cycle (all groups) is
+ * captured once as a CUDA graph and one parent graph holds the cycles of all
+ * unconverged problems as independent branches (plus the copies of their
+ * residual norms to the host), so one graph launch advances every problem by
+ * a cycle and small problems run side by side.  Every check_every launches
+ * the residuals are read; converged, failed or exhausted problems leave the
+ * parent graph, which is then rebuilt.  infos[i] (nullable array, history
+ * ignored) receives cycles, status and the FP64 relative residual of the
+ * returned psi as btmg_solve.  Returns BTMG_OK when every problem
+ * converged, else BTMG_ERR_NOT_CONVERGED (or the first hard error).  Learned
+ * corrections are not applied in batched solves.
+ * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT (a bounded device wait gave up).  */
+typedef struct btmg_batch btmg_batch;
+int btmg_create_batch(const btmg_problem_desc* descs, int32_t n, int32_t autotune, void* stream,
+                      btmg_batch** out);
+int btmg_destroy_batch(btmg_batch* b);
+/* Problem i of the batch (owned by the batch; do not destroy it).         */
+int btmg_batch_problem(btmg_batch* b, int32_t i, btmg_problem** p);
+/* Chunk count of problem i, the automatic choice for its shape, and the
+ * tuned time of one eager cycle in ms (0 when not tuned).                  */
+int btmg_batch_chunks(const btmg_batch* b, int32_t i, int32_t* chunks, int32_t* auto_chunks, double* ms);
+int btmg_solve_batch(btmg_batch* b, void* const* psi, double rtol, int32_t max_cycles, int32_t check_every,
+                     btmg_solve_info* infos, void* stream);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * btmg_profile(p, 1) brackets every subsequent kernel launch of the cycle

@@ -32,7 +32,8 @@ EXPORTS = (
     "btmg_unet_create", "btmg_unet_destroy", "btmg_unet_num_params", "btmg_unet_get_params",
     "btmg_unet_set_params", "btmg_unet_get_grads", "btmg_unet_forward", "btmg_unet_train_step",
     "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_learn_canvas",
-    "btmg_learn_features",
+    "btmg_learn_features", "btmg_create_batch", "btmg_destroy_batch", "btmg_batch_problem",
+    "btmg_batch_chunks", "btmg_solve_batch",
 )
 LEARN_FEATURES = 4  # input channels of the learned correction
 PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
@@ -57,6 +58,7 @@ class Desc(C.Structure):
         ("psi_dtype", C.c_int32),
         ("max_levels", C.c_int32),
         ("pg_half", C.c_int32),
+        ("chunks", C.c_int32),
     ]
 
 
@@ -118,6 +120,11 @@ def load(build_if_missing: bool = True):
     L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i32)]
     L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.btmg_learn_features.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.btmg_create_batch.argtypes = [C.POINTER(Desc), i32, i32, vp, C.POINTER(vp)]
+    L.btmg_destroy_batch.argtypes = [vp]
+    L.btmg_batch_problem.argtypes = [vp, i32, C.POINTER(vp)]
+    L.btmg_batch_chunks.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), dp]
+    L.btmg_solve_batch.argtypes = [vp, C.POINTER(vp), C.c_double, i32, i32, C.POINTER(SolveInfo), vp]
     L.btmg_unet_create.argtypes = [i32, C.c_uint64, C.POINTER(vp)]
     L.btmg_unet_destroy.argtypes = [vp]
     L.btmg_unet_num_params.argtypes = [vp, i64p]
@@ -167,6 +174,34 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def make_desc(prob, dtype=F32, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0, order=None, chunks=0):
+    """btmg_problem_desc of a problem dict (see inputs.py) and the host arrays
+    it points to (keep them alive until the problem is created)."""
+    keep = (np.ascontiguousarray(prob["region"], dtype=np.int32),
+            np.ascontiguousarray(prob["sigma_t"], dtype=np.float64),
+            np.ascontiguousarray(prob["sigma_s"], dtype=np.float64),
+            np.ascontiguousarray(prob["source"], dtype=np.float64))
+    region, st, ss, src = keep
+    d = Desc()
+    d.nx, d.ny = int(prob["nx"]), int(prob["ny"])
+    d.lx, d.ly = float(prob["lx"]), float(prob["ly"])
+    d.order = int(order if order is not None else prob.get("order", 2))
+    d.n_polar, d.n_azim = int(prob["n_polar"]), int(prob["n_azim"])
+    d.n_groups = int(st.shape[1])
+    d.region = region.ctypes.data_as(C.POINTER(C.c_int32))
+    d.n_regions = int(st.shape[0])
+    dp = C.POINTER(C.c_double)
+    d.sigma_t = st.ctypes.data_as(dp)
+    d.sigma_s = ss.ctypes.data_as(dp)
+    d.source = src.ctypes.data_as(dp)
+    for i, b in enumerate(prob.get("bc", (0, 0, 0, 0))):
+        d.bc[i] = int(b)
+    d.pg, d.nu_jacobi, d.beta_pg = int(pg), int(nu), float(beta_pg)
+    d.psi_dtype, d.max_levels, d.pg_half = int(dtype), int(max_levels), int(pg_half)
+    d.chunks = int(chunks)
+    return d, keep
+
+
 class Problem:
     """A fixed-source problem resident on the GPU.
 
@@ -176,38 +211,34 @@ class Problem:
     """
 
     def __init__(self, prob, dtype=F32, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0,
-                 order=None, stream=None):
+                 order=None, stream=None, chunks=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("btmg needs a CUDA device (sm_103a); there is no CPU path")
         L = load()
-        self._region = np.ascontiguousarray(prob["region"], dtype=np.int32)
-        self._st = np.ascontiguousarray(prob["sigma_t"], dtype=np.float64)
-        self._ss = np.ascontiguousarray(prob["sigma_s"], dtype=np.float64)
-        self._src = np.ascontiguousarray(prob["source"], dtype=np.float64)
-        d = Desc()
-        d.nx, d.ny = int(prob["nx"]), int(prob["ny"])
-        d.lx, d.ly = float(prob["lx"]), float(prob["ly"])
-        d.order = int(order if order is not None else prob.get("order", 2))
-        d.n_polar, d.n_azim = int(prob["n_polar"]), int(prob["n_azim"])
-        d.n_groups = int(self._st.shape[1])
-        d.region = self._region.ctypes.data_as(C.POINTER(C.c_int32))
-        d.n_regions = int(self._st.shape[0])
-        dp = C.POINTER(C.c_double)
-        d.sigma_t = self._st.ctypes.data_as(dp)
-        d.sigma_s = self._ss.ctypes.data_as(dp)
-        d.source = self._src.ctypes.data_as(dp)
-        for i, b in enumerate(prob.get("bc", (0, 0, 0, 0))):
-            d.bc[i] = int(b)
-        d.pg, d.nu_jacobi, d.beta_pg = int(pg), int(nu), float(beta_pg)
-        d.psi_dtype, d.max_levels, d.pg_half = int(dtype), int(max_levels), int(pg_half)
-        self.desc = d
+        d, self._keep = make_desc(prob, dtype, pg, nu, beta_pg, max_levels, pg_half, order, chunks)
         h = C.c_void_p()
         _check(L.btmg_create_problem(C.byref(d), _stream_ptr(stream), C.byref(h)))
+        self._owned = True
+        self._attach(h, d)
+
+    @classmethod
+    def _view(cls, h, d, owner):
+        """A problem owned by a Batch (not destroyed by this object)."""
+        self = cls.__new__(cls)
+        self._owned = False
+        self._owner = owner
+        self._attach(h, d)
+        return self
+
+    def _attach(self, h, d):
+        torch = _torch()
+        L = load()
+        self.desc = d
         self.h = h
-        self.dtype_code = int(dtype)
-        self.torch_dtype = _dtype_of(dtype)
-        self.compute_dtype = torch.float64 if dtype == F64 else torch.float32
+        self.dtype_code = int(d.psi_dtype)
+        self.torch_dtype = _dtype_of(self.dtype_code)
+        self.compute_dtype = torch.float64 if self.dtype_code == F64 else torch.float32
         self.G = d.n_groups
         n = C.c_int32()
         _check(L.btmg_num_levels(self.h, C.byref(n)))
@@ -217,9 +248,9 @@ class Problem:
         self.shape = (self.G, self.nd, d.ny, d.nx)
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             load().btmg_destroy_problem(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -389,6 +420,72 @@ class Problem:
         if hist is not None:
             out["history"] = hist[:min(info.cycles, hist.size)].copy()
         return out
+
+
+class Batch:
+    """Independent problems solved together (btmg_create_batch /
+    btmg_solve_batch): one graph launch advances every unconverged problem
+    by one cycle.  `problems[i]` are non-owning Problem views."""
+
+    def __init__(self, probs, dtype=F32, pg=0, nu=3, autotune=False, chunks=None, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("btmg needs a CUDA device (sm_103a); there is no CPU path")
+        L = load()
+        n = len(probs)
+        descs = (Desc * n)()
+        self._keep = []
+        for i, prob in enumerate(probs):
+            d, keep = make_desc(prob, dtype, pg, nu, chunks=(chunks[i] if chunks else 0))
+            descs[i] = d
+            self._keep.append(keep)
+        h = C.c_void_p()
+        _check(L.btmg_create_batch(descs, n, int(bool(autotune)), _stream_ptr(stream), C.byref(h)))
+        self.h = h
+        self.problems = []
+        for i in range(n):
+            ph = C.c_void_p()
+            _check(L.btmg_batch_problem(self.h, i, C.byref(ph)))
+            self.problems.append(Problem._view(ph, descs[i], self))
+
+    def chunks(self, i):
+        """(chunks, automatic chunks, tuned ms per eager cycle) of problem i."""
+        c, a, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _check(load().btmg_batch_chunks(self.h, i, C.byref(c), C.byref(a), C.byref(ms)))
+        return c.value, a.value, ms.value
+
+    def zeros(self):
+        return [p.zeros() for p in self.problems]
+
+    def solve(self, psis, rtol=1e-6, max_cycles=1000, check_every=1, stream=None):
+        """Solve every problem from psis[i] (device tensors, in place); returns
+        (status, [dict(status, cycles, rel_resid)])."""
+        n = len(self.problems)
+        if len(psis) != n:
+            raise ValueError("need one psi per problem")
+        for p, x in zip(self.problems, psis):
+            p._check_psi(x)
+        ptrs = (C.c_void_p * n)(*[x.data_ptr() for x in psis])
+        infos = (SolveInfo * n)()
+        rc = load().btmg_solve_batch(self.h, ptrs, float(rtol), int(max_cycles), int(check_every), infos,
+                                     _stream_ptr(stream))
+        if rc not in (OK, ERR_NOT_CONVERGED):
+            _check(rc)
+        return rc, [dict(status=infos[i].status, cycles=infos[i].cycles, rel_resid=infos[i].rel_resid)
+                    for i in range(n)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            for p in self.problems:
+                p.h = None
+            load().btmg_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _ucheck(rc):

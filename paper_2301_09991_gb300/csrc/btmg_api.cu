@@ -7,6 +7,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/btmg.h"
@@ -888,6 +891,35 @@ int upload(void** dst, const std::vector<char>& buf) {
   return BTMG_OK;
 }
 
+// Direction chunks: the PG grid is tiles x chunks CTAs; pick the divisor of nd
+// (at most 64 chunks) whose grid comes closest to whole waves of resident
+// CTAs, preferring fewer chunks on ties (fewer flux partials).
+int auto_chunks(int dtype, bool pg, int tiles, int nd) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int occ = 1;
+  switch (dtype) {
+    case BTMG_F64: occ = pg_blocks_per_sm<double, double>(pg); break;
+    case BTMG_F32: occ = pg_blocks_per_sm<float, float>(pg); break;
+    case BTMG_BF16: occ = pg_blocks_per_sm<__nv_bfloat16, float>(pg); break;
+    default: occ = pg_blocks_per_sm<__half, float>(pg); break;
+  }
+  const double slots = (double)sms * occ;
+  int best = 1;
+  double best_eff = -1.0;
+  for (int c = 1; c <= nd && c <= 64; ++c) {
+    if (nd % c) continue;
+    const double items = (double)tiles * c;
+    const double waves = std::ceil(items / slots);
+    const double eff = items / (waves * slots);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = c;
+    }
+  }
+  return best;
+}
+
 int create(const btmg_problem_desc* d, btmg_problem** out) {
   if (!d || !out) return fail(BTMG_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
@@ -899,6 +931,11 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
     return fail(BTMG_ERR_INVALID_ARG, "bad material description");
   if (d->psi_dtype < BTMG_F64 || d->psi_dtype > BTMG_F16) return fail(BTMG_ERR_INVALID_ARG, "bad psi_dtype");
   if (d->nu_jacobi < 1 || d->nu_jacobi > 8) return fail(BTMG_ERR_INVALID_ARG, "nu_jacobi must be in 1..8");
+  {
+    const int nd = d->n_polar * d->n_azim;  // 8 faces of (n_polar / 2) x (n_azim / 4)
+    if (d->chunks < 0 || d->chunks > 64 || (d->chunks > 0 && nd % d->chunks))
+      return fail(BTMG_ERR_INVALID_ARG, "chunks must be 0 or a divisor of the direction count, at most 64");
+  }
   if (d->pg && d->order != 2) return fail(BTMG_ERR_UNSUPPORTED, "the GPU PG operator implements order 2");
   for (int i = 0; i < 4; ++i)
     if (d->bc[i] != BTMG_VACUUM && d->bc[i] != BTMG_REFLECTIVE) return fail(BTMG_ERR_INVALID_ARG, "bad bc");
@@ -1004,33 +1041,9 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
   P->tiles_y = (F.ny + kTile - 1) / kTile;
   const int tiles = P->tiles_x * P->tiles_y;
   {
-    // Direction chunks: the PG grid is tiles x chunks CTAs; pick the divisor
-    // of nd (at most 64 chunks) whose grid comes closest to whole waves of
-    // resident CTAs, preferring fewer chunks on ties (fewer flux partials).
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int occ = 1;
-    switch (P->dtype) {
-      case BTMG_F64: occ = pg_blocks_per_sm<double, double>(d->pg != 0); break;
-      case BTMG_F32: occ = pg_blocks_per_sm<float, float>(d->pg != 0); break;
-      case BTMG_BF16: occ = pg_blocks_per_sm<__nv_bfloat16, float>(d->pg != 0); break;
-      default: occ = pg_blocks_per_sm<__half, float>(d->pg != 0); break;
-    }
-    const double slots = (double)sms * occ;
-    int best = 1;
-    double best_eff = -1.0;
-    for (int c = 1; c <= F.nd && c <= 64; ++c) {
-      if (F.nd % c) continue;
-      const double items = (double)tiles * c;
-      const double waves = std::ceil(items / slots);
-      const double eff = items / (waves * slots);
-      if (eff > best_eff + 0.02) {
-        best_eff = eff;
-        best = c;
-      }
-    }
-    P->nchunk = best;
-    P->dpc = F.nd / best;
+    const int best = auto_chunks(P->dtype, d->pg != 0, tiles, F.nd);
+    P->nchunk = d->chunks > 0 ? d->chunks : best;
+    P->dpc = F.nd / P->nchunk;
   }
   P->graphs.assign(G, nullptr);
 
@@ -1113,6 +1126,264 @@ int check_level(const btmg_problem* p, int level) {
   return BTMG_OK;
 }
 
+// ------------------------------------------------------------ batches ----
+// Whole cycle of one problem (scalar-flux partials and every group) captured
+// as a graph on a non-default stream.
+template <typename T, typename C> struct RunCapture {
+  static int run(btmg_problem* P, void* psi, cudaStream_t s, cudaGraph_t* g) {
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int rc = Impl<T, C>::mg_cycle(P, psi, nullptr, s);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    CK(ee);
+    *g = graph;
+    return BTMG_OK;
+  }
+};
+// relative residual of psi (all groups), FP64 norms
+template <typename T, typename C> struct RunResidual {
+  static int run(btmg_problem* P, const void* psi, double* rel, cudaStream_t s) {
+    CK(Impl<T, C>::residual_all(P, reinterpret_cast<const T*>(psi), nullptr, s));
+    return Impl<T, C>::read_rel(P, s, 0, nullptr, rel);
+  }
+};
+
+// Autotuner cache: problem shape -> (chunks, ms per eager cycle).
+struct TuneKey {
+  int nx, ny, nd, G, dtype, pg, nu;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nx, ny, nd, G, dtype, pg, nu) < std::tie(o.nx, o.ny, o.nd, o.G, o.dtype, o.pg, o.nu);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, double>> g_tune;
+
+// Time `cycles` eager cycles (after `warm` untimed ones) of the problem d on s.
+int time_cycles(const btmg_problem_desc& d, int warm, int cycles, cudaStream_t s, double* ms) {
+  btmg_problem* P = nullptr;
+  if (int rc = create(&d, &P)) return rc;
+  void* psi = nullptr;
+  const size_t bytes = (size_t)P->G * P->lev[0].n() * dtype_size(P->dtype);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = BTMG_OK;
+  auto done = [&](int code) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (psi) cudaFree(psi);
+    destroy(P);
+    return code;
+  };
+  if (cudaMalloc(&psi, bytes) != cudaSuccess) return done(fail(BTMG_ERR_OOM, "autotune: psi"));
+  if (cudaMemsetAsync(psi, 0, bytes, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    return done(fail(BTMG_ERR_CUDA, "autotune: setup"));
+  for (int k = 0; k < warm && rc == BTMG_OK; ++k) rc = dispatch<RunCycle>(P->dtype, P, psi, nullptr, s);
+  if (rc) return done(rc);
+  cudaEventRecord(e0, s);
+  for (int k = 0; k < cycles && rc == BTMG_OK; ++k) rc = dispatch<RunCycle>(P->dtype, P, psi, nullptr, s);
+  if (rc) return done(rc);
+  cudaEventRecord(e1, s);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return done(fail(BTMG_ERR_CUDA, "autotune: timing"));
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / cycles;
+  return done(BTMG_OK);
+}
+
+// Chunk count for the shape of d: candidates are the divisors of the
+// direction count (at most 64) within a factor 4 of the automatic choice,
+// each timed over 3 eager cycles after 2 warm-up cycles.
+int tune_chunks(const btmg_problem_desc& d, cudaStream_t s, int* chunks, double* ms) {
+  const int nd = d.n_polar * d.n_azim;
+  const int tiles = ((d.nx + kTile - 1) / kTile) * ((d.ny + kTile - 1) / kTile);
+  const TuneKey key{d.nx, d.ny, nd, d.n_groups, d.psi_dtype, d.pg, d.nu_jacobi};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *chunks = it->second.first;
+      *ms = it->second.second;
+      return BTMG_OK;
+    }
+  }
+  const int a = auto_chunks(d.psi_dtype, d.pg != 0, tiles, nd);
+  int best = a;
+  double best_ms = 1e300;
+  for (int c = 1; c <= nd && c <= 64; ++c) {
+    if (nd % c || 4 * c < a || c > 4 * a) continue;
+    btmg_problem_desc d2 = d;
+    d2.chunks = c;
+    double t = 0.0;
+    if (int rc = time_cycles(d2, 2, 3, s, &t)) return rc;
+    if (t < best_ms) {
+      best_ms = t;
+      best = c;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {best, best_ms};
+  *chunks = best;
+  *ms = best_ms;
+  return BTMG_OK;
+}
+
+}  // namespace
+
+struct btmg_batch {
+  std::vector<btmg_problem*> probs;
+  std::vector<int> auto_ch;
+  std::vector<double> tuned_ms;
+  cudaStream_t bs = nullptr;    // capture and launch stream
+  cudaEvent_t order = nullptr;  // orders bs after the caller's stream and back
+  std::vector<cudaGraph_t> cyc;  // per problem: one whole cycle
+  std::vector<const void*> cyc_psi;
+  cudaGraphExec_t exec = nullptr;  // parent graph of the active problems
+  std::vector<int> exec_set;
+  double* h_res = nullptr;  // pinned: per problem rn2[G], qn2[G]
+  int* h_err = nullptr;     // pinned: per problem bounded-wait flag
+  std::vector<size_t> res_off;
+};
+
+namespace {
+void batch_free(btmg_batch* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  for (cudaGraph_t g : B->cyc)
+    if (g) cudaGraphDestroy(g);
+  for (btmg_problem* P : B->probs) destroy(P);
+  if (B->h_res) cudaFreeHost(B->h_res);
+  if (B->h_err) cudaFreeHost(B->h_err);
+  if (B->order) cudaEventDestroy(B->order);
+  if (B->bs) cudaStreamDestroy(B->bs);
+  delete B;
+}
+
+// parent graph: one child-graph branch per active problem, each followed by
+// the copies of its residual norms and its error flag to pinned host memory
+int batch_build(btmg_batch* B, const std::vector<int>& active) {
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  cudaGraph_t parent = nullptr;
+  CK(cudaGraphCreate(&parent, 0));
+  for (int i : active) {
+    btmg_problem* P = B->probs[i];
+    cudaGraphNode_t child, m0, m1, m2;
+    cudaError_t e = cudaGraphAddChildGraphNode(&child, parent, nullptr, 0, B->cyc[i]);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&m0, parent, &child, 1, B->h_res + B->res_off[i], P->d_rn2,
+                                   sizeof(double) * P->G, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&m1, parent, &child, 1, B->h_res + B->res_off[i] + P->G, P->d_qn2,
+                                   sizeof(double) * P->G, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&m2, parent, &child, 1, B->h_err + i, P->d_err, sizeof(int),
+                                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(parent);
+      CK(e);
+    }
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&B->exec, parent, 0);
+  cudaGraphDestroy(parent);
+  CK(ei);
+  B->exec_set = active;
+  return BTMG_OK;
+}
+
+int solve_batch(btmg_batch* B, void* const* psi, double rtol, int max_cycles, int check, btmg_solve_info* infos,
+                cudaStream_t s) {
+  const int n = (int)B->probs.size();
+  CK(cudaEventRecord(B->order, s));
+  CK(cudaStreamWaitEvent(B->bs, B->order, 0));
+  std::vector<int> cycles(n, 0), status(n, BTMG_ERR_NOT_CONVERGED);
+  std::vector<double> best(n, 1e300), rel(n, 0.0);
+  std::vector<char> done(n, 0);
+  // first cycle eagerly (kernel attributes, workspaces), then capture
+  bool recaptured = false;
+  for (int i = 0; i < n; ++i) {
+    btmg_problem* P = B->probs[i];
+    if (int rc = dispatch<RunCycle>(P->dtype, P, psi[i], nullptr, B->bs)) return rc;
+    cycles[i] = 1;
+    if (!B->cyc[i] || B->cyc_psi[i] != psi[i]) {
+      if (B->cyc[i]) cudaGraphDestroy(B->cyc[i]);
+      B->cyc[i] = nullptr;
+      if (int rc = dispatch<RunCapture>(P->dtype, P, psi[i], B->bs, &B->cyc[i])) return rc;
+      B->cyc_psi[i] = psi[i];
+      recaptured = true;
+    }
+    if (cycles[i] >= max_cycles) done[i] = 1;
+  }
+  if (recaptured && B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  const double pi4 = 4.0 * kPi;
+  for (;;) {
+    std::vector<int> active;
+    int k = check;
+    for (int i = 0; i < n; ++i)
+      if (!done[i]) {
+        active.push_back(i);
+        k = std::min(k, max_cycles - cycles[i]);
+      }
+    if (active.empty()) break;
+    if (!B->exec || active != B->exec_set) {
+      if (int rc = batch_build(B, active)) return rc;
+    }
+    for (int j = 0; j < k; ++j) CK(cudaGraphLaunch(B->exec, B->bs));
+    CK(cudaStreamSynchronize(B->bs));
+    for (int i : active) {
+      btmg_problem* P = B->probs[i];
+      cycles[i] += k;
+      if (B->h_err[i]) return fail(BTMG_ERR_TIMEOUT, "a bounded device wait gave up (batch problem)");
+      double sr = 0.0, sq = 0.0;
+      for (int g = 0; g < P->G; ++g) {
+        sr += B->h_res[B->res_off[i] + g];
+        sq += B->h_res[B->res_off[i] + P->G + g];
+      }
+      const double w = pi4 * P->lev[0].dx * P->lev[0].dy;
+      const double r = sq > 0 ? std::sqrt(sr / (w * sq)) : std::sqrt(sr);
+      if (std::isnan(r)) {
+        status[i] = BTMG_ERR_NAN;
+        done[i] = 1;
+      } else if (r > 1e3 * best[i] && best[i] < 1e299) {
+        status[i] = BTMG_ERR_DIVERGED;
+        done[i] = 1;
+      } else {
+        best[i] = std::min(best[i], r);
+        if (r <= rtol) {
+          status[i] = BTMG_OK;
+          done[i] = 1;
+        } else if (cycles[i] >= max_cycles) {
+          done[i] = 1;
+        }
+      }
+    }
+  }
+  // residual of every returned psi (FP64 norms)
+  int result = BTMG_OK;
+  for (int i = 0; i < n; ++i) {
+    btmg_problem* P = B->probs[i];
+    if (int rc = dispatch<RunResidual>(P->dtype, P, (const void*)psi[i], &rel[i], B->bs)) return rc;
+    if (status[i] == BTMG_OK && !(rel[i] <= rtol))
+      status[i] = std::isnan(rel[i]) ? BTMG_ERR_NAN : BTMG_ERR_NOT_CONVERGED;
+    if (infos) {
+      infos[i].cycles = cycles[i];
+      infos[i].status = status[i];
+      infos[i].rel_resid = rel[i];
+    }
+    if (status[i] != BTMG_OK && result == BTMG_OK) result = BTMG_ERR_NOT_CONVERGED;
+  }
+  CK(cudaEventRecord(B->order, B->bs));
+  CK(cudaStreamWaitEvent(s, B->order, 0));
+  return result;
+}
 }  // namespace
 
 extern "C" {
@@ -1386,5 +1657,92 @@ const char* btmg_error_string(int status) {
 }
 
 const char* btmg_last_error(void) { return g_last_error.c_str(); }
+
+int btmg_create_batch(const btmg_problem_desc* descs, int32_t n, int32_t autotune, void* stream,
+                      btmg_batch** out) {
+  if (!descs || n < 1 || !out) return fail(BTMG_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  btmg_batch* B = nullptr;
+  try {
+    B = new btmg_batch();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&B->bs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->order, cudaEventDisableTiming) != cudaSuccess) {
+      batch_free(B);
+      return fail(BTMG_ERR_CUDA, "batch stream");
+    }
+    if (!s) s = B->bs;
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+      btmg_problem_desc d = descs[i];
+      const int nd = d.n_polar * d.n_azim;
+      const int tiles = ((d.nx + kTile - 1) / kTile) * ((d.ny + kTile - 1) / kTile);
+      double ms = 0.0;
+      if (autotune && d.chunks == 0 && d.nx > 0 && d.ny > 0 && d.n_polar > 0 && d.n_azim > 0) {
+        int c = 0;
+        if (int rc = tune_chunks(d, s, &c, &ms)) {
+          batch_free(B);
+          return rc;
+        }
+        d.chunks = c;
+      }
+      btmg_problem* P = nullptr;
+      if (int rc = create(&d, &P)) {
+        batch_free(B);
+        return rc;
+      }
+      B->probs.push_back(P);
+      B->auto_ch.push_back(auto_chunks(d.psi_dtype, d.pg != 0, tiles, nd));
+      B->tuned_ms.push_back(ms);
+      B->res_off.push_back(off);
+      off += 2 * (size_t)P->G;
+    }
+    B->cyc.assign(n, nullptr);
+    B->cyc_psi.assign(n, nullptr);
+    if (cudaMallocHost(&B->h_res, sizeof(double) * off) != cudaSuccess ||
+        cudaMallocHost(&B->h_err, sizeof(int) * n) != cudaSuccess) {
+      batch_free(B);
+      return fail(BTMG_ERR_OOM, "batch pinned buffers");
+    }
+    std::memset(B->h_err, 0, sizeof(int) * n);
+  } catch (...) {
+    batch_free(B);
+    return fail(BTMG_ERR_OOM, "host allocation failed");
+  }
+  *out = B;
+  return BTMG_OK;
+}
+
+int btmg_destroy_batch(btmg_batch* b) {
+  if (b) cudaDeviceSynchronize();
+  batch_free(b);
+  return BTMG_OK;
+}
+
+int btmg_batch_problem(btmg_batch* b, int32_t i, btmg_problem** p) {
+  if (!b || !p || i < 0 || i >= (int)b->probs.size()) return fail(BTMG_ERR_INVALID_ARG, "bad batch index");
+  *p = b->probs[i];
+  return BTMG_OK;
+}
+
+int btmg_batch_chunks(const btmg_batch* b, int32_t i, int32_t* chunks, int32_t* auto_chunks_out, double* ms) {
+  if (!b || i < 0 || i >= (int)b->probs.size()) return fail(BTMG_ERR_INVALID_ARG, "bad batch index");
+  if (chunks) *chunks = b->probs[i]->nchunk;
+  if (auto_chunks_out) *auto_chunks_out = b->auto_ch[i];
+  if (ms) *ms = b->tuned_ms[i];
+  return BTMG_OK;
+}
+
+int btmg_solve_batch(btmg_batch* b, void* const* psi, double rtol, int32_t max_cycles, int32_t check_every,
+                     btmg_solve_info* infos, void* stream) {
+  if (!b || !psi || max_cycles < 1) return fail(BTMG_ERR_INVALID_ARG, "bad batch solve arguments");
+  for (size_t i = 0; i < b->probs.size(); ++i)
+    if (!psi[i]) return fail(BTMG_ERR_INVALID_ARG, "null psi in batch");
+  try {
+    return solve_batch(b, psi, rtol, max_cycles, check_every > 0 ? check_every : 1, infos, (cudaStream_t)stream);
+  } catch (...) {
+    return fail(BTMG_ERR_OOM, "host allocation failed");
+  }
+}
 
 }  // extern "C"
