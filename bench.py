@@ -264,6 +264,50 @@ def time_to_residual(btmg, torch, rtol=1e-6):
     return out
 
 
+def batched(btmg, torch, cycles=4):
+    """Batched workload: 64 independent one-group Voronoi problems (seed 4),
+    N uniform over the multiples of 16 in [64, 512], direction grids uniform
+    over {8x16, 16x16, 16x32, 32x32}, PG on, FP32.  Throughput of `cycles`
+    cycles of btmg_solve_batch (autotuned chunks; one eager cycle, graph
+    cycles, final residuals) against the same cycles run problem by problem
+    (btmg_solve, graph path)."""
+    probs = I.batch()
+    N = sum(p["nx"] * p["ny"] * p["n_polar"] * p["n_azim"] for p in probs)
+    t0 = time.perf_counter()
+    b = btmg.Batch(probs, dtype=btmg.F32, pg=1, autotune=True)
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter() - t0
+    psis = b.zeros()
+    b.solve(psis, rtol=0.0, max_cycles=2, check_every=1)  # warm-up, graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.solve(psis, rtol=0.0, max_cycles=cycles, check_every=cycles)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    chunks = [b.chunks(i) for i in range(len(probs))]
+    b.close()
+    del psis, b
+    torch.cuda.empty_cache()
+    gps = [btmg.Problem(p, dtype=btmg.F32, pg=1) for p in probs]
+    xs = [g.zeros() for g in gps]
+    for g, x in zip(gps, xs):
+        g.solve(x, rtol=0.0, max_cycles=3, check_every=3, history=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, x in zip(gps, xs):
+        g.solve(x, rtol=0.0, max_cycles=cycles, check_every=cycles, history=False)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    del gps, xs
+    torch.cuda.empty_cache()
+    return {"workload": "64 Voronoi problems, N in 64..512 (step 16), dirs in {8x16,16x16,16x32,32x32}, "
+                        "seed 4, PG on, FP32",
+            "unknowns": N, "cycles": cycles, "value": N * cycles / t_batch, "unit": UNIT,
+            "seconds": round(t_batch, 4), "sequential_value": N * cycles / t_seq,
+            "sequential_seconds": round(t_seq, 4), "autotune_seconds": round(t_tune, 2),
+            "chunks_tuned_vs_auto": sum(1 for c in chunks if c[0] != c[1])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -276,6 +320,7 @@ def main():
     ap.add_argument("--cpu-cycles", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-6 section")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload section")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -395,6 +440,10 @@ def main():
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
     if rank == 0 and not args.no_ttr:
         line["time_to_1e-6"] = time_to_residual(btmg, torch)
+    if rank == 0 and not args.no_batch:
+        del psi, gp, hpsi
+        torch.cuda.empty_cache()
+        line["batched"] = batched(btmg, torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)
     if rank == 0:
