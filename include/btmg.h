@@ -324,8 +324,10 @@ int btmg_launch_count(const btmg_problem* p, int64_t* n);
  * the process exits.
  *   nx, ny, lx, ly, n_polar, n_azim, bc, pg, pg_half: as in btmg_problem_desc
  *     (quadratic ConvFEM; nx*ny <= BTMG_NOALLOC_MAX_NODES and
- *     8*(n_polar/2)*(n_azim/4) <= BTMG_NOALLOC_MAX_DIRS, otherwise
- *     BTMG_ERR_NOALLOC_TOO_LARGE is returned and nothing is launched);
+ *     8*(n_polar/2)*(n_azim/4) <= BTMG_NOALLOC_MAX_DIRS, and the norm
+ *     partial sums of the residual kernel must fit the scratch (very thin
+ *     grids with pg = 0 do not); otherwise BTMG_ERR_NOALLOC_TOO_LARGE is
+ *     returned and nothing is launched);
  *   sigma_t, sigma_s, source: caller-owned device float arrays [ny][nx]
  *     (total, in-group isotropic scattering, isotropic source per node);
  *   psi: caller-owned device float [nd][ny][nx]; r: same shape, output.

@@ -135,7 +135,8 @@ struct btmg_problem {
   void* d_phi_part = nullptr;  // [G][nchunk][npix]
   void* d_psi_tmp = nullptr;   // storage type, one group
   double* d_norm_part = nullptr;
-  int n_norm_part = 0;
+  int n_norm_part = 0;  // allocated norm partials
+  int n_norm_sum = 0;   // norm partials written by the fine residual kernel
   double* d_qn2_part = nullptr;
   int n_q_blocks = 0;
   double* d_rn2 = nullptr;  // [G]
@@ -352,8 +353,7 @@ template <typename T, typename C> struct Impl {
     if ((e = timed(P, PC_PG_RESID, s, [&] { return launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s); })) !=
         cudaSuccess)
       return e;
-    const int nblk = P->tiles_x * P->tiles_y * P->nchunk;
-    return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, nblk, P->d_rn2 + g, s); });
+    return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, P->n_norm_sum, P->d_rn2 + g, s); });
   }
 
   // With `homog`, the cycle of the learned correction c (in P->d_lc, its
@@ -427,8 +427,7 @@ template <typename T, typename C> struct Impl {
     a.norm_part = P->d_norm_part;
     CK(timed(P, PC_PG_RESID, s, [&] { return launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s); }));
     if (norm_to) {
-      const int nblk = P->tiles_x * P->tiles_y * P->nchunk;
-      CK(timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, nblk, norm_to, s); }));
+      CK(timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, P->n_norm_sum, norm_to, s); }));
     }
     return BTMG_OK;
   }
@@ -537,7 +536,7 @@ template <typename T, typename C> struct Impl {
       a.r_out = r_out ? r_out + (size_t)g * L0.n() : dptr<C>(P->d_s[0]);
       a.norm_part = P->d_norm_part;
       if ((e = launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s)) != cudaSuccess) return e;
-      if ((e = launch_sum(P->d_norm_part, P->tiles_x * P->tiles_y * P->nchunk, P->d_rn2 + g, s)) != cudaSuccess)
+      if ((e = launch_sum(P->d_norm_part, P->n_norm_sum, P->d_rn2 + g, s)) != cudaSuccess)
         return e;
     }
     return cudaSuccess;
@@ -1101,7 +1100,8 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
       cudaMalloc(&P->d_phi_part, (size_t)G * P->nchunk * npix * P->csize) != cudaSuccess ||
       cudaMalloc(&P->d_psi_tmp, F.n() * dtype_size(P->dtype)) != cudaSuccess)
     return bail(fail(BTMG_ERR_OOM, "workspace"));
-  P->n_norm_part = tiles * P->nchunk;
+  P->n_norm_sum = d->pg ? tiles * P->nchunk : upres_norm_blocks(F.nx, F.ny, P->nchunk);
+  P->n_norm_part = std::max(tiles * P->nchunk, upres_norm_blocks(F.nx, F.ny, P->nchunk));
   P->n_q_blocks = (int)((npix + 255) / 256 < 1024 ? (npix + 255) / 256 : 1024);
   if (cudaMalloc(&P->d_norm_part, sizeof(double) * P->n_norm_part) != cudaSuccess ||
       cudaMalloc(&P->d_qn2_part, sizeof(double) * P->n_q_blocks) != cudaSuccess ||

@@ -104,6 +104,10 @@ template <typename T, typename C> struct UpArgs {
 // ----------------------------------------------------------- launchers -----
 // All return cudaError_t of the launch.
 template <typename T, typename C>
+cudaError_t launch_upres(const PgArgs<T, C>& a, int mode, int nchunk, cudaStream_t s);
+template <typename T, typename C> int upres_blocks_per_sm();
+int upres_norm_blocks(int nx, int ny, int nchunk);  // norm partials of the upwind-mode kernel
+template <typename T, typename C>
 cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cudaStream_t s);
 // resident CTAs per SM of the PG kernel (for choosing whole-wave grids)
 template <typename T, typename C> int pg_blocks_per_sm(bool pg);

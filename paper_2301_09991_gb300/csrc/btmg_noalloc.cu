@@ -129,9 +129,12 @@ extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, do
   if ((int64_t)nx * ny > kMaxPix || nd > kMaxDirs) return BTMG_ERR_NOALLOC_TOO_LARGE;
   const int tiles_x = (nx + kTile - 1) / kTile;
   const int64_t tiles = (int64_t)tiles_x * ((ny + kTile - 1) / kTile);
+  // norm partials written by the residual kernel: one per 32x32 tile and
+  // chunk (PG), one per 128x8 tile and chunk (upwind scheme)
+  auto parts = [&](int c) -> int64_t { return pg ? tiles * c : (int64_t)upres_norm_blocks(nx, ny, c); };
   int nchunk = kChunks;  // direction chunks of the residual kernel
-  while (nchunk > 1 && (nd % nchunk || tiles * nchunk > kMaxNormParts)) nchunk >>= 1;
-  if (tiles * nchunk > kMaxNormParts) return BTMG_ERR_NOALLOC_TOO_LARGE;
+  while (nchunk > 1 && (nd % nchunk || parts(nchunk) > kMaxNormParts)) nchunk >>= 1;
+  if (parts(nchunk) > kMaxNormParts) return BTMG_ERR_NOALLOC_TOO_LARGE;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BTMG_ERR_CUDA;
   if (!g_scratch_dev[dev]) {  // first call on this device: resolve the symbol
@@ -188,6 +191,6 @@ extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, do
   a.norm_part = norm_part;
   a.err = err;
   if (launch_pg<float, float>(a, PG_RESID, pg != 0, nchunk, s) != cudaSuccess) return BTMG_ERR_CUDA;
-  if (launch_sum(norm_part, (int)(tiles * nchunk), sums, s) != cudaSuccess) return BTMG_ERR_CUDA;
+  if (launch_sum(norm_part, (int)parts(nchunk), sums, s) != cudaSuccess) return BTMG_ERR_CUDA;
   return BTMG_OK;
 }

@@ -27,47 +27,10 @@
 #include <cstring>
 
 #include "btmg_common.cuh"
+#include "tma.cuh"
 
 namespace btmg {
 namespace {
-
-// ---- TMA / mbarrier helpers (inline PTX, sm_90+ async copy engine) -------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after a few million polls (about a second).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
 constexpr int TX = 32, TY = 32, NT = 256;
 constexpr int W6 = TX + 12, H6 = TY + 12;  // 44
@@ -611,37 +574,11 @@ template <typename C, bool PGON> constexpr size_t smem_bytes() {
 // starts at x0 - 8, a multiple of 8 elements (the innermost coordinate of a
 // TMA copy must be 16-byte aligned).  Used when psi is stored in the compute
 // type, its base is 16-byte aligned and a row is a multiple of 16 bytes.
-// The encoder is a driver entry point; it is looked up through the runtime
-// so that the library does not link against the driver library.
-PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 template <typename T, typename C> bool make_tmap(CUtensorMap* m, const PgArgs<T, C>& a) {
   if (sizeof(T) != sizeof(C)) return false;
-  PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
-  if (!encode) return false;
   const size_t es = sizeof(T);
-  if ((reinterpret_cast<uintptr_t>(a.psi) % 16) != 0 || ((size_t)a.nx * es) % 16 != 0) return false;
-  const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nd};
-  const cuuint64_t strides[2] = {(cuuint64_t)a.nx * es, (cuuint64_t)a.nx * a.ny * es};
-  const cuuint32_t box[3] = {(cuuint32_t)PS, (cuuint32_t)H6, 1u};
-  const cuuint32_t estr[3] = {1u, 1u, 1u};
-  return encode(m, dt, 3, const_cast<T*>(a.psi), dims, strides, box, estr,
-                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode_tmap_3d(m, a.psi, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, es,
+                        a.nx, a.ny, a.nd, PS, H6);
 }
 
 template <typename T, typename C, int MODE, bool PGON, bool TMA>
@@ -684,17 +621,18 @@ template <typename T, typename C, int MODE, bool PGON> int occupancy_mode() {
 
 }  // namespace
 
+// The upwind scheme (pg = 0) reaches one node upstream and needs no staged
+// tile: it runs in the streaming kernel of k_upres.cu.
 template <typename T, typename C>
 cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cudaStream_t s) {
   if (pg)
     return mode == PG_RESID ? launch_mode<T, C, PG_RESID, true>(a, nchunk, s)
                             : launch_mode<T, C, PG_JACOBI, true>(a, nchunk, s);
-  return mode == PG_RESID ? launch_mode<T, C, PG_RESID, false>(a, nchunk, s)
-                          : launch_mode<T, C, PG_JACOBI, false>(a, nchunk, s);
+  return launch_upres<T, C>(a, mode, nchunk, s);
 }
 
 template <typename T, typename C> int pg_blocks_per_sm(bool pg) {
-  return pg ? occupancy_mode<T, C, PG_JACOBI, true>() : occupancy_mode<T, C, PG_JACOBI, false>();
+  return pg ? occupancy_mode<T, C, PG_JACOBI, true>() : upres_blocks_per_sm<T, C>();
 }
 
 template cudaError_t launch_pg<double, double>(const PgArgs<double, double>&, int, bool, int, cudaStream_t);
