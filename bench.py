@@ -74,6 +74,19 @@ def fp32_peak_tflops(sm_mhz):
     return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+def job_throughput(ms_local, units_per_rank, steps, ws, device="cpu"):
+    """Whole-job (max-over-ranks ms, unknown-updates/s): every rank processes
+    units_per_rank unknowns per step; the job takes as long as its slowest
+    rank.  Replicas only: the one collective is this MAX of the elapsed time."""
+    ms = float(ms_local)
+    if ws > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * steps * ws / (ms / 1000.0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -366,11 +379,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     assert out["cycles"] == args.steps, out
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * args.steps * ws / (ms / 1000.0)
+    ms, value = job_throughput(ms, N, args.steps, ws, "cuda")
 
     # per-kernel device times: the same cycles eagerly, each launch bracketed
     # by CUDA events on the launching stream

@@ -256,6 +256,15 @@ int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8, int32_t* 
 int btmg_learn_features(btmg_problem* p, const void* psi, const void* psi_prev, float* feat, float* scale,
                         void* stream);
 
+/* Failure-path self-test (no counterpart in the paper).  Every wait of the
+ * staged kernels on a copy (mbarrier) is bounded: when it gives up the kernel
+ * sets the problem's error flag, drains its copies and returns, and the next
+ * call that reads the flag returns BTMG_ERR_TIMEOUT with the context still
+ * usable.  This call runs that path on purpose: a kernel waits, with `polls`
+ * polls (>= 1), on an mbarrier that nothing arrives on.  Returns
+ * BTMG_ERR_TIMEOUT (the expected outcome), INVALID_ARG or CUDA.            */
+int btmg_wait_selftest(int32_t polls, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched solves of independent problems (no counterpart in the paper: its
  * solver treats one problem at a time).

@@ -33,7 +33,7 @@ EXPORTS = (
     "btmg_unet_set_params", "btmg_unet_get_grads", "btmg_unet_forward", "btmg_unet_train_step",
     "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_learn_canvas",
     "btmg_learn_features", "btmg_create_batch", "btmg_destroy_batch", "btmg_batch_problem",
-    "btmg_batch_chunks", "btmg_solve_batch",
+    "btmg_batch_chunks", "btmg_solve_batch", "btmg_wait_selftest",
 )
 LEARN_FEATURES = 4  # input channels of the learned correction
 PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = True):
     L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i32)]
     L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.btmg_learn_features.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.btmg_wait_selftest.argtypes = [i32, vp]
     L.btmg_create_batch.argtypes = [C.POINTER(Desc), i32, i32, vp, C.POINTER(vp)]
     L.btmg_destroy_batch.argtypes = [vp]
     L.btmg_batch_problem.argtypes = [vp, i32, C.POINTER(vp)]
@@ -141,6 +142,12 @@ def load(build_if_missing: bool = True):
     L.btmg_last_error.argtypes = []
     _lib = L
     return L
+
+
+def wait_selftest(polls=1000, stream=None):
+    """Run the bounded-wait failure path once; returns the status code
+    (ERR_TIMEOUT expected)."""
+    return load().btmg_wait_selftest(int(polls), _stream_ptr(stream))
 
 
 def error_string(code):

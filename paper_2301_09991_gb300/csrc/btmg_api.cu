@@ -1658,6 +1658,21 @@ const char* btmg_error_string(int status) {
 
 const char* btmg_last_error(void) { return g_last_error.c_str(); }
 
+int btmg_wait_selftest(int32_t polls, void* stream) {
+  if (polls < 1) return fail(BTMG_ERR_INVALID_ARG, "polls must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d = nullptr;
+  int h = 0;
+  CK(cudaMalloc(&d, sizeof(int)));
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_wait_selftest(d, polls, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  CK(e);
+  return h ? fail(BTMG_ERR_TIMEOUT, "bounded wait gave up (self-test)") : BTMG_OK;
+}
+
 int btmg_create_batch(const btmg_problem_desc* descs, int32_t n, int32_t autotune, void* stream,
                       btmg_batch** out) {
   if (!descs || n < 1 || !out) return fail(BTMG_ERR_INVALID_ARG, "bad batch arguments");

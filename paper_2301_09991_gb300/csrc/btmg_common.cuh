@@ -107,6 +107,7 @@ template <typename T, typename C>
 cudaError_t launch_upres(const PgArgs<T, C>& a, int mode, int nchunk, cudaStream_t s);
 template <typename T, typename C> int upres_blocks_per_sm();
 int upres_norm_blocks(int nx, int ny, int nchunk);  // norm partials of the upwind-mode kernel
+cudaError_t launch_wait_selftest(int* err, int polls, cudaStream_t s);
 template <typename T, typename C>
 cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cudaStream_t s);
 // resident CTAs per SM of the PG kernel (for choosing whole-wave grids)

@@ -426,6 +426,26 @@ template <typename T, typename C> int upres_blocks_per_sm() {
   return blocks > 0 ? blocks : 1;
 }
 
+// Bounded-wait self-test: one CTA waits, with `polls` polls, on an mbarrier
+// that nothing arrives on -- the situation of a stalled copy in the staged
+// kernels -- and, on giving up, sets *err like they do and returns.
+__global__ void k_wait_selftest(int* err, int polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  bool ok = false;
+  for (int it = 0; it < polls && !ok; ++it) ok = mbar_try_wait(&bar, 0u);
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+cudaError_t launch_wait_selftest(int* err, int polls, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(err, polls);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_upres<double, double>(const PgArgs<double, double>&, int, int, cudaStream_t);
 template cudaError_t launch_upres<float, float>(const PgArgs<float, float>&, int, int, cudaStream_t);
 template cudaError_t launch_upres<__nv_bfloat16, float>(const PgArgs<__nv_bfloat16, float>&, int, int,
