@@ -66,7 +66,7 @@ typedef struct btmg_problem btmg_problem;
 typedef struct {
   int32_t nx, ny;          /* nodes in x and y (>= 1)                        */
   double lx, ly;           /* domain size (> 0)                              */
-  int32_t order;           /* ConvFEM order: 2 (quadratic 5x5 filters)       */
+  int32_t order;           /* ConvFEM order: 2 (quadratic 5x5 filters) or 1 (linear 3x3; PG in FP64/FP32 only) */
   int32_t n_polar, n_azim; /* direction grid: 8 faces of (n_polar/2)x(n_azim/4) */
   int32_t n_groups;        /* energy groups G (>= 1)                         */
   const int32_t* region;   /* host [ny][nx] region id per node               */
@@ -101,8 +101,9 @@ typedef struct {
 
 /* Builds the quadrature (Sec. 2.2), the space-angle hierarchy with harmonic
  * averaged cross sections (Sec. 2.5) and the device workspaces.  Copies every
- * host array.  Errors: INVALID_ARG (bad sizes, region ids, dtype, order != 2
- * with pg = 1), OOM, CUDA.  *out is NULL on failure.                        */
+ * host array.  Errors: INVALID_ARG (bad sizes, region ids, dtype, chunks),
+ * UNSUPPORTED (pg = 1 with an order other than 2, except order 1 with FP64 or
+ * FP32 storage), OOM, CUDA.  *out is NULL on failure.                       */
 int btmg_create_problem(const btmg_problem_desc* desc, void* stream, btmg_problem** out);
 
 /* Frees every library-owned device buffer.  NULL is accepted.              */

@@ -253,11 +253,12 @@ template <typename T, typename C> struct Impl {
     a.inv_dx2 = (C)(1.0 / (L0.dx * L0.dx));
     a.inv_dy2 = (C)(1.0 / (L0.dy * L0.dy));
     a.dxdy = (C)(L0.dx * L0.dy);
-    // Sec. 2.6 constants for order p = 2: eps_k = 1e-3, alpha_kabs = 2^p/16,
+    // Sec. 2.6 constants for order p: eps_k = 1e-3, alpha_kabs = 2^p/16,
     // alpha_ksquare = 2^p/2; alpha_r = beta_r = 3.
     a.eps_k = (C)1e-3;
-    a.a_kabs = (C)0.25;
-    a.a_ksq = (C)2.0;
+    a.a_kabs = (C)(P->d.order == 1 ? 0.125 : 0.25);  // 2^p / 16
+    a.a_ksq = (C)(P->d.order == 1 ? 1.0 : 2.0);      // 2^p / 2
+    a.order = P->d.order;
     a.a_r = (C)3.0;
     a.half = (C)(P->d.pg_half ? 0.5 : 1.0);
     a.beta = (C)(P->d.pg ? P->d.beta_pg : 1.0);
@@ -935,7 +936,8 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
     if (d->chunks < 0 || d->chunks > 64 || (d->chunks > 0 && nd % d->chunks))
       return fail(BTMG_ERR_INVALID_ARG, "chunks must be 0 or a divisor of the direction count, at most 64");
   }
-  if (d->pg && d->order != 2) return fail(BTMG_ERR_UNSUPPORTED, "the GPU PG operator implements order 2");
+  if (d->pg && d->order != 2 && !(d->order == 1 && d->psi_dtype <= BTMG_F32))
+    return fail(BTMG_ERR_UNSUPPORTED, "the GPU PG operator implements order 2, and order 1 in FP64/FP32");
   for (int i = 0; i < 4; ++i)
     if (d->bc[i] != BTMG_VACUUM && d->bc[i] != BTMG_REFLECTIVE) return fail(BTMG_ERR_INVALID_ARG, "bad bc");
   const int G = d->n_groups, nx = d->nx, ny = d->ny;

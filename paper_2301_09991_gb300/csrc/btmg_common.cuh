@@ -77,6 +77,7 @@ template <typename T, typename C> struct PgArgs {
   C eps_k, a_kabs, a_ksq, a_r, half, beta;
   Bc bc;
   int* err;  // set to nonzero when a bounded wait gave up (device word)
+  int order;  // ConvFEM order of the PG kernel: 2 (quadratic) or 1 (linear)
 };
 
 // ------------------------------------------------------- upwind Jacobi ----

@@ -184,6 +184,7 @@ extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, do
   a.eps_k = 1e-3f;
   a.a_kabs = 0.25f;
   a.a_ksq = 2.0f;
+  a.order = 2;
   a.a_r = 3.0f;
   a.half = pg_half ? 0.5f : 1.0f;
   a.beta = 1.0f;

@@ -37,15 +37,22 @@ constexpr int W6 = TX + 12, H6 = TY + 12;  // 44
 constexpr int W4 = TX + 8, H4 = TY + 8;    // 40
 constexpr int W2 = TX + 4, H2 = TY + 4;    // 36
 
-// quadratic ConvFEM 1D stencils (offsets -2..2), h = 1
-template <typename C> __device__ __forceinline__ C M1(int k) {
+// ConvFEM 1D stencils (offsets -2..2), h = 1, of order ORD (Sec. 2.7 and the
+// Appendix): quadratic m1 = (-1,4,24,4,-1)/30, d1 = (1,-8,0,8,-1)/12,
+// s1 = (1,-16,30,-16,1)/12; linear m1 = (1,4,1)/6, d1 = (-1,0,1)/2,
+// s1 = (-1,2,-1), written with zero outer taps (the 3x3 filters are
+// tensor products of them).
+template <typename C, int ORD> __device__ __forceinline__ C M1(int k) {
+  if (ORD == 1) return k == 2 ? C(4.0 / 6.0) : ((k == 1 || k == 3) ? C(1.0 / 6.0) : C(0));
   return k == 2 ? C(24.0 / 30.0) : ((k == 1 || k == 3) ? C(4.0 / 30.0) : C(-1.0 / 30.0));
 }
-template <typename C> __device__ __forceinline__ C S1(int k) {
+template <typename C, int ORD> __device__ __forceinline__ C S1(int k) {
+  if (ORD == 1) return k == 2 ? C(2.0) : ((k == 1 || k == 3) ? C(-1.0) : C(0));
   return k == 2 ? C(30.0 / 12.0) : ((k == 1 || k == 3) ? C(-16.0 / 12.0) : C(1.0 / 12.0));
 }
 // d1 in difference form on the values at offsets -2, -1, +1, +2
-template <typename C> __device__ __forceinline__ C D1(C p0, C p1, C p3, C p4) {
+template <typename C, int ORD> __device__ __forceinline__ C D1(C p0, C p1, C p3, C p4) {
+  if (ORD == 1) return C(0.5) * (p3 - p1);
   return C(8.0 / 12.0) * (p3 - p1) - C(1.0 / 12.0) * (p4 - p0);
 }
 
@@ -140,7 +147,7 @@ __device__ __forceinline__ void ldp8(const double* p, double (&o)[8]) {
   }
 }
 
-template <typename T, typename C, int MODE, bool PGON, bool TMA>
+template <typename T, typename C, int MODE, bool PGON, bool TMA, int ORD>
 __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
     k_pg(const PgArgs<T, C> a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
             ld4(P - 2 + r * PS + c + 8, q2);
             const C p[8] = {q0[2], q0[3], q1[0], q1[1], q1[2], q1[3], q2[0], q2[1]};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) o[k] = D1<C>(p[k], p[k + 1], p[k + 3], p[k + 4]);
+            for (int k = 0; k < 4; ++k) o[k] = D1<C, ORD>(p[k], p[k + 1], p[k + 3], p[k + 4]);
             st4(A + r * W4 + c, o);
           } else {
             const int j = it - NA;
@@ -279,8 +286,8 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
             C o0[4], o1[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              o0[k] = D1<C>(p[0][k], p[1][k], p[3][k], p[4][k]);
-              o1[k] = D1<C>(p[1][k], p[2][k], p[4][k], p[5][k]);
+              o0[k] = D1<C, ORD>(p[0][k], p[1][k], p[3][k], p[4][k]);
+              o1[k] = D1<C, ORD>(p[1][k], p[2][k], p[4][k], p[5][k]);
             }
             st4(B + r * W6 + c, o0);
             st4(B + (r + 1) * W6 + c, o1);
@@ -304,8 +311,8 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
               C s0 = C(0), s1 = C(0);
 #pragma unroll
               for (int v = 0; v < 5; ++v) {
-                s0 += M1<C>(v) * p[v][k];
-                s1 += M1<C>(v) * p[v + 1][k];
+                s0 += M1<C, ORD>(v) * p[v][k];
+                s1 += M1<C, ORD>(v) * p[v + 1][k];
               }
               o0[k] = s0 * a.inv_dx;
               o1[k] = s1 * a.inv_dx;
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
             for (int k = 0; k < 4; ++k) {
               C s = C(0);
 #pragma unroll
-              for (int u = 0; u < 5; ++u) s += M1<C>(u) * p[k + u];
+              for (int u = 0; u < 5; ++u) s += M1<C, ORD>(u) * p[k + u];
               o[k] = s * a.inv_dy;
             }
             st4(Py + r * W4 + c, o);
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
             for (int k = 0; k < 4; ++k) {
               C s = C(0);
 #pragma unroll
-              for (int v = 0; v < 5; ++v) s += M1<C>(v) * p[q + v][k];
+              for (int v = 0; v < 5; ++v) s += M1<C, ORD>(v) * p[q + v][k];
               o[k] = s;
             }
             st4(dst + (r + q) * W4 + c, o);
@@ -387,8 +394,8 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
             C mx = C(0), my = C(0);
 #pragma unroll
             for (int u = 0; u < 5; ++u) {
-              mx += M1<C>(u) * tx[k + u];
-              my += M1<C>(u) * ty[k + u];
+              mx += M1<C, ORD>(u) * tx[k + u];
+              my += M1<C, ORD>(u) * ty[k + u];
             }
             const C pxc = pxv[k], pyc = pyv[k];
             const C Rx = cx * (mx - pxc), Ry = cy * (my - pyc);
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
               C s0 = C(0), s1 = C(0), s2 = C(0);
 #pragma unroll
               for (int v = 0; v < 5; ++v) {
-                const C w = xg ? M1<C>(v) : S1<C>(v);
+                const C w = xg ? M1<C, ORD>(v) : S1<C, ORD>(v);
                 s0 += w * kk[q + v][k] * pp[q + v][k];
                 s1 += w * kk[q + v][k];
                 s2 += w * pp[q + v][k];
@@ -480,12 +487,12 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
           fkp[k] = fp[k] = fk[k] = gkp[k] = gp[k] = gk[k] = C(0);
 #pragma unroll
           for (int u = 0; u < 5; ++u) {
-            fkp[k] += S1<C>(u) * u1[k + u];
-            fk[k] += S1<C>(u) * u2[k + u];
-            fp[k] += S1<C>(u) * w1[k + u];
-            gkp[k] += M1<C>(u) * v1[k + u];
-            gk[k] += M1<C>(u) * v2[k + u];
-            gp[k] += M1<C>(u) * v3[k + u];
+            fkp[k] += S1<C, ORD>(u) * u1[k + u];
+            fk[k] += S1<C, ORD>(u) * u2[k + u];
+            fp[k] += S1<C, ORD>(u) * w1[k + u];
+            gkp[k] += M1<C, ORD>(u) * v1[k + u];
+            gk[k] += M1<C, ORD>(u) * v2[k + u];
+            gp[k] += M1<C, ORD>(u) * v3[k + u];
           }
         }
       }
@@ -581,39 +588,49 @@ template <typename T, typename C> bool make_tmap(CUtensorMap* m, const PgArgs<T,
                         a.nx, a.ny, a.nd, PS, H6);
 }
 
-template <typename T, typename C, int MODE, bool PGON, bool TMA>
+template <typename T, typename C, int MODE, bool PGON, bool TMA, int ORD>
 cudaError_t launch_variant(const PgArgs<T, C>& a, const CUtensorMap& tm, int nchunk, cudaStream_t s) {
   constexpr size_t smem = smem_bytes<C, PGON>();
   static bool attr_set = false;  // per instantiation, once per process
   if (!attr_set) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_pg<T, C, MODE, PGON, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_pg<T, C, MODE, PGON, TMA, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int tiles_y = (a.ny + TY - 1) / TY;
   dim3 grid(a.tiles_x * tiles_y, nchunk);
-  k_pg<T, C, MODE, PGON, TMA><<<grid, NT, smem, s>>>(a, tm);
+  k_pg<T, C, MODE, PGON, TMA, ORD><<<grid, NT, smem, s>>>(a, tm);
   return cudaGetLastError();
 }
 
-template <typename T, typename C, int MODE, bool PGON>
-cudaError_t launch_mode(const PgArgs<T, C>& a, int nchunk, cudaStream_t s) {
+template <typename T, typename C, int MODE, bool PGON, int ORD>
+cudaError_t launch_order(const PgArgs<T, C>& a, int nchunk, cudaStream_t s) {
   CUtensorMap tm;
   memset(&tm, 0, sizeof(tm));
   if constexpr (sizeof(T) == sizeof(C)) {
-    if (make_tmap(&tm, a)) return launch_variant<T, C, MODE, PGON, true>(a, tm, nchunk, s);
+    if (make_tmap(&tm, a)) return launch_variant<T, C, MODE, PGON, true, ORD>(a, tm, nchunk, s);
   }
-  return launch_variant<T, C, MODE, PGON, false>(a, tm, nchunk, s);
+  return launch_variant<T, C, MODE, PGON, false, ORD>(a, tm, nchunk, s);
+}
+
+// the linear order is built for FP64 and FP32 storage
+template <typename T, typename C, int MODE, bool PGON>
+cudaError_t launch_mode(const PgArgs<T, C>& a, int nchunk, cudaStream_t s) {
+  if constexpr (sizeof(T) == sizeof(C)) {
+    if (a.order == 1) return launch_order<T, C, MODE, PGON, 1>(a, nchunk, s);
+  }
+  if (a.order != 2) return cudaErrorNotSupported;
+  return launch_order<T, C, MODE, PGON, 2>(a, nchunk, s);
 }
 
 template <typename T, typename C, int MODE, bool PGON> int occupancy_mode() {
   constexpr size_t smem = smem_bytes<C, PGON>();
-  if (cudaFuncSetAttribute(k_pg<T, C, MODE, PGON, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(k_pg<T, C, MODE, PGON, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 1;
   int blocks = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_pg<T, C, MODE, PGON, false>, NT, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_pg<T, C, MODE, PGON, false, 2>, NT, smem) !=
       cudaSuccess)
     return 1;
   return blocks < 1 ? 1 : blocks;

@@ -1,0 +1,61 @@
+"""Variant of the hot path: the linear ConvFEM order (3x3 filters derived
+from linear elements, Sec. 2.7; alpha_kabs = 2^p/16 and alpha_ksq = 2^p/2
+with p = 1) with the anisotropic PG dissipation, against the oracle's order-1
+operator and cycle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2301_09991_gb300 import btmg, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("checker_72x40", lambda: I.checkerboard(n=72, ny=40, n_polar=8, n_azim=16, blocks=4, seed=11)),
+    ("reflective_33x17", lambda: I.checkerboard(n=33, ny=17, n_polar=4, n_azim=8, blocks=3, seed=13,
+                                                bc=(1, 0, 1, 1))),
+    ("tiny_5x3", lambda: I.checkerboard(n=5, ny=3, n_polar=4, n_azim=8, blocks=2, seed=12)),
+]
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def _linear(prob):
+    return dict(prob, order=1)
+
+
+@pytest.mark.parametrize("name,mk", CASES)
+def test_linear_order_operator_fp64(name, mk):
+    prob = _linear(mk())
+    gp = btmg.Problem(prob, dtype=btmg.F64, pg=1)
+    op = O.OracleProblem(prob, pg=1)
+    psi = I.random_field(gp.shape, seed=31)
+    r = gp.apply_operator(torch.tensor(psi, device="cuda")).cpu().numpy()
+    assert rel(r, op.apply(psi)) < 1e-12
+
+
+def test_linear_order_operator_fp32_and_cycle_fp64():
+    prob = _linear(I.checkerboard(n=48, ny=40, n_polar=8, n_azim=8, blocks=4, seed=14))
+    op = O.OracleProblem(prob, pg=1)
+    g32 = btmg.Problem(prob, dtype=btmg.F32, pg=1)
+    psi = I.random_field(g32.shape, seed=32).astype(np.float32)
+    r32 = g32.apply_operator(torch.tensor(psi, device="cuda")).double().cpu().numpy()
+    assert rel(r32, op.apply(psi.astype(np.float64))) < 1e-6
+    g64 = btmg.Problem(prob, dtype=btmg.F64, pg=1)
+    x = g64.zeros()
+    ref = op.zeros()
+    for _ in range(2):
+        g64.mg_cycle(x, want_residual=False)
+        ref, _, _ = op.mg_cycle(ref)
+    assert rel(x.cpu().numpy(), ref) < 1e-10
+
+
+def test_linear_order_lowp_and_cubic_are_rejected():
+    prob = I.checkerboard(n=24, n_polar=4, n_azim=8, blocks=2, seed=15)
+    for order, dt in ((1, btmg.BF16), (3, btmg.F32)):
+        with pytest.raises(btmg.BtmgError) as e:
+            btmg.Problem(dict(prob, order=order), dtype=dt, pg=1)
+        assert e.value.code == btmg.ERR_UNSUPPORTED
