@@ -59,3 +59,29 @@ def test_linear_order_lowp_and_cubic_are_rejected():
         with pytest.raises(btmg.BtmgError) as e:
             btmg.Problem(dict(prob, order=order), dtype=dt, pg=1)
         assert e.value.code == btmg.ERR_UNSUPPORTED
+
+
+def test_duct_streaming_qualitative():
+    """The straight-duct problem of Sec. 3.1 (28 x 36 cm, a 6 x 6 cm source,
+    absorbers beside it, void ducts above and below; no scattering), solved
+    with the upwind fine scheme: the flux is mirror symmetric about the
+    source's centre lines, and along the void duct it stays far above the
+    flux at the same distance into the absorber (streaming against
+    attenuation e^{-sigma d}).  Parity with the paper's plots is unpinned:
+    the paper prints no numbers for this problem."""
+    for dx in (0.8, 0.4):
+        prob = I.duct(dx=dx, n_polar=8, n_azim=16)
+        gp = btmg.Problem(prob, dtype=btmg.F64, pg=0)
+        psi = gp.zeros()
+        out = gp.solve(psi, rtol=1e-9, max_cycles=3000)
+        assert out["status"] == btmg.OK, out
+        phi = gp.scalar_flux(psi).cpu().numpy()[0]  # [ny][nx]
+        assert np.all(phi >= -1e-12)
+        assert rel(phi, phi[::-1, :]) < 1e-9 and rel(phi, phi[:, ::-1]) < 1e-9
+        x = (np.arange(prob["nx"]) + 0.5) * dx
+        y = (np.arange(prob["ny"]) + 0.5) * dx
+        ic, jc = np.argmin(abs(x - 14.0)), np.argmin(abs(y - 18.0))
+        for d in (4.0, 8.0):
+            duct = phi[np.argmin(abs(y - (21.0 + d))), ic]
+            absorber = phi[jc, np.argmin(abs(x - (17.0 + d)))]
+            assert duct > 3.0 * absorber, (dx, d, duct, absorber)
