@@ -36,7 +36,7 @@ constexpr int UT = 32, UNT = 256, NUMAX = 8;
 __device__ __forceinline__ float rcp_(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ double rcp_(double v) { return 1.0 / v; }
 template <typename T, typename C, int MODE, int NU>
-__global__ void __launch_bounds__(UNT, 4) k_upwind(const UpArgs<T, C> a) {
+__global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
   constexpr int W = UT + NU;        // loaded region (tile + NU upwind nodes)
   constexpr int WP = W + 2;         // stride with the zero ring
   constexpr int WS = UT + 2 * NU;   // sigma region covering both upwind sides
@@ -58,14 +58,37 @@ __global__ void __launch_bounds__(UNT, 4) k_upwind(const UpArgs<T, C> a) {
   }
   for (int i = tid; i < 2 * WP * WP; i += UNT) D0[i] = C(0);  // zero rings of D0 and D1
 
-  // owned cells: (ly, lx) of slot s, or ly = -1 when the slot is unused
-  int sly[NS], slx[NS];
+  // owned cells: shared-memory index of slot s in D0/D1, or -1 when unused
+  int sidx[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const int i = tid + UNT * s;
-    sly[s] = i < W * W ? i / W : -1;
-    slx[s] = i % W;
+    sidx[s] = i < W * W ? (i / W + 1) * WP + i % W + 1 : -1;
   }
+  // The region's placement depends only on the signs of mu and nu, which a
+  // chunk of directions (inside one octant face) shares: the global offset
+  // of each owned cell (-1 outside the domain), its UpSamp parent offset and
+  // its sigma are computed once per sign combination, not per direction.
+  int gofs[NS], cofs[NS];
+  C sgv[NS];
+  int combo = -1;
+  const int shx = a.fx >> 1, shy = a.fy >> 1;
+  auto geom = [&](int cmb) {
+    const bool sxp = cmb & 1, syp = cmb & 2;
+    const int ox = x0 - (sxp ? NU : 0), oy = y0 - (syp ? NU : 0);
+    const int sgx = sxp ? 0 : NU, sgy = syp ? 0 : NU;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int i = tid + UNT * s;
+      const int ly = i / W, lx = i % W;
+      const int gx = ox + lx, gy = oy + ly;
+      const bool in = i < W * W && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+      gofs[s] = in ? gy * nx + gx : -1;
+      cofs[s] = in ? (gy >> shy) * a.nxc + (gx >> shx) : 0;
+      sgv[s] = in ? SG[(ly + sgy) * WS + lx + sgx] : C(0);
+    }
+    combo = cmb;
+  };
 
   C phi_acc[4];
 #pragma unroll
@@ -76,46 +99,46 @@ __global__ void __launch_bounds__(UNT, 4) k_upwind(const UpArgs<T, C> a) {
 
   // registers holding the next direction's inputs
   C rs[NS], rd[NS], rp[4];
-  // coarsening factors are 1 or 2: UpSamp indices are shifts
-  const int shx = a.fx >> 1, shy = a.fy >> 1;
+  // this thread's tile nodes (column tx, rows ty + 8k): offset of row 0 and
+  // the rows inside the domain
+  const int pofs = (y0 + ty) * nx + x0 + tx;
+  int pmask = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (x0 + tx < nx && y0 + ty + 8 * k < ny) pmask |= 1 << k;
   auto fetch = [&](int n) {
     const Dir<C> dr = a.dir[n];
-    const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
-    const int ox = x0 - (sxp ? NU : 0), oy = y0 - (syp ? NU : 0);
+    const int cmb = (dr.mu > C(0) ? 1 : 0) | (dr.nu > C(0) ? 2 : 0);
+    if (cmb != combo) geom(cmb);  // after the current direction's set-up
     const C* srcn = a.src + (size_t)n * a.src_stride;
     const C* initn = a.init_mode == INIT_UPSAMPLE ? a.init + (size_t)a.parent[n] * ((size_t)a.nyc * a.nxc)
                                                   : a.init + (size_t)n * npix;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const int gx = ox + slx[s], gy = oy + sly[s];
       C v = C(0), d = C(0);
-      if (sly[s] >= 0 && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-        const int gi = gy * nx + gx;
-        v = srcn[gi];
+      if (gofs[s] >= 0) {
+        v = srcn[gofs[s]];
         if (a.init_mode == INIT_UPSAMPLE)
-          d = initn[(gy >> shy) * a.nxc + (gx >> shx)];
+          d = initn[cofs[s]];
         else if (a.init_mode == INIT_SAME)
-          d = initn[gi];
+          d = initn[gofs[s]];
       }
       rs[s] = v;
       rd[s] = d;
     }
     if (MODE == UP_UPDATE) {
-      const T* pin_n = a.psi_in + (size_t)n * npix;
+      const T* pin_n = a.psi_in + (size_t)n * npix + pofs;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int gx = x0 + tx, gy = y0 + ty + 8 * k;
-        rp[k] = (gx < nx && gy < ny) ? (C)Conv<T>::ld(pin_n + gy * nx + gx) : C(0);
-      }
+      for (int k = 0; k < 4; ++k) rp[k] = (pmask >> k) & 1 ? (C)Conv<T>::ld(pin_n + 8 * k * nx) : C(0);
     }
   };
 
+  __syncthreads();  // SG is complete before the first geometry reads it
   if (n_begin < n_end) fetch(n_begin);
   for (int n = n_begin; n < n_end; ++n) {
     const Dir<C> dr = a.dir[n];
     const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
     const int ox = x0 - (sxp ? NU : 0), oy = y0 - (syp ? NU : 0);
-    const int sgx = sxp ? 0 : NU, sgy = syp ? 0 : NU;  // offset into SG
     const C ax = dr.ax, ay = dr.ay, axy = dr.ax + dr.ay;
     // reflective incoming sides touching this region: column / row to re-copy
     const bool rx_ = sxp ? (a.bc.xlo == BC_REFLECTIVE && ox < 0) : (a.bc.xhi == BC_REFLECTIVE && ox + W > nx);
@@ -127,12 +150,10 @@ __global__ void __launch_bounds__(UNT, 4) k_upwind(const UpArgs<T, C> a) {
     C sreg[NS], ireg[NS];
     __syncthreads();  // previous direction finished with D0/D1
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int gx = ox + slx[s], gy = oy + sly[s];
-      const bool in = sly[s] >= 0 && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    for (int s = 0; s < NS; ++s) {  // the geometry of this direction's signs (set by its fetch)
       sreg[s] = rs[s];
-      ireg[s] = in ? rcp_(axy + SG[(sly[s] + sgy) * WS + slx[s] + sgx]) : C(0);
-      if (sly[s] >= 0) D0[(sly[s] + 1) * WP + slx[s] + 1] = rd[s];
+      ireg[s] = gofs[s] >= 0 ? rcp_(axy + sgv[s]) : C(0);
+      if (sidx[s] >= 0) D0[sidx[s]] = rd[s];
     }
     C pin[4];
 #pragma unroll
@@ -158,8 +179,8 @@ __global__ void __launch_bounds__(UNT, 4) k_upwind(const UpArgs<T, C> a) {
     for (int k = 1; k <= NU; ++k) {
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        if (sly[s] < 0) continue;
-        const int i = (sly[s] + 1) * WP + slx[s] + 1;
+        if (sidx[s] < 0) continue;
+        const int i = sidx[s];
         Dnew[i] = (sreg[s] + ax * Dold[i + ux] + ay * Dold[i + uy]) * ireg[s];
       }
       __syncthreads();
