@@ -135,6 +135,12 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
 
   __syncthreads();  // SG is complete before the first geometry reads it
   if (n_begin < n_end) fetch(n_begin);
+  // Each direction writes its initial correction into the buffer that does
+  // not hold the previous direction's result: the last reads of that buffer
+  // were in the previous direction's final sweep, which ended at a barrier,
+  // so no barrier is needed before the write.
+  C* Dinit = D0;
+  C* Dother = D1;
   for (int n = n_begin; n < n_end; ++n) {
     const Dir<C> dr = a.dir[n];
     const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
@@ -148,20 +154,19 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
     const int hxl = sxp ? bxl - 1 : bxl + 1;  // its upwind halo cell
     const int hyl = syp ? byl - 1 : byl + 1;
     C sreg[NS], ireg[NS];
-    __syncthreads();  // previous direction finished with D0/D1
 #pragma unroll
     for (int s = 0; s < NS; ++s) {  // the geometry of this direction's signs (set by its fetch)
       sreg[s] = rs[s];
       ireg[s] = gofs[s] >= 0 ? rcp_(axy + sgv[s]) : C(0);
-      if (sidx[s] >= 0) D0[sidx[s]] = rd[s];
+      if (sidx[s] >= 0) Dinit[sidx[s]] = rd[s];
     }
     C pin[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) pin[k] = rp[k];
     if (n + 1 < n_end) fetch(n + 1);  // in flight during the sweeps
     __syncthreads();
-    C* Dold = D0;
-    C* Dnew = D1;
+    C* Dold = Dinit;
+    C* Dnew = Dother;
     const int ux = sxp ? -1 : 1, uy = syp ? -WP : WP;
     auto recopy = [&](C* D) {  // reflective halo = adjacent interior node
       if (rx_)
@@ -209,6 +214,8 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
         phi_acc[k] += dr.w * stored<T, C>(pn);
       }
     }
+    Dinit = Dnew;  // the buffer without this direction's result
+    Dother = Dold;
   }
   if (MODE == UP_UPDATE) {
     C* ph = a.phi_part + (size_t)chunk * npix;
