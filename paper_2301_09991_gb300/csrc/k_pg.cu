@@ -131,22 +131,6 @@ static_assert(OFF_A % 4 == 0 && OFF_B % 4 == 0 && OFF_PX % 4 == 0 && OFF_PY % 4 
                   OFF_KY % 4 == 0 && OFF_U % 4 == 0 && OFF_TY % 4 == 0 && S4N % 4 == 0,
               "16-byte alignment of the shared arrays");
 
-// 8 consecutive elements from the staged psi tile (8-byte aligned for FP32)
-__device__ __forceinline__ void ldp8(const float* p, float (&o)[8]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float2 v = *reinterpret_cast<const float2*>(p + 2 * k);
-    o[2 * k] = v.x, o[2 * k + 1] = v.y;
-  }
-}
-__device__ __forceinline__ void ldp8(const double* p, double (&o)[8]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double2 v = *reinterpret_cast<const double2*>(p + 2 * k);
-    o[2 * k] = v.x, o[2 * k + 1] = v.y;
-  }
-}
-
 template <typename T, typename C, int MODE, bool PGON, bool TMA, int ORD>
 __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
     k_pg(const PgArgs<T, C> a, const __grid_constant__ CUtensorMap tmap) {
