@@ -58,3 +58,24 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     psi = torch.zeros((64, 512, 1024), dtype=torch.float32, device="cuda")
     rc, _ = _noalloc(prob, psi)
     assert rc == btmg.ERR_NOALLOC_TOO_LARGE
+
+
+def test_noalloc_upwind_scheme_and_its_partial_sum_limit():
+    """pg = 0 runs the streaming upwind-scheme kernel, whose norm partial sums
+    (one per 128 x 8 tile and chunk) must also fit the fixed scratch: a thin
+    grid that fits with the PG kernel's 32 x 32 tiles is rejected for pg = 0
+    with the distinct status, nothing launched."""
+    prob = I.checkerboard(n=72, ny=40, n_polar=8, n_azim=16, blocks=4, seed=12)
+    gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+    psi = torch.tensor(I.random_field(gp.shape, seed=44), dtype=torch.float32, device="cuda")
+    ref = gp.apply_operator(psi)[0].double().cpu().numpy()
+    rc, r = _noalloc(prob, psi, pg=0)
+    assert rc == btmg.OK
+    got = r.double().cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-6
+    # 4 x 65536 nodes (the node limit), 32 directions: 2048 PG tiles fit with
+    # 2 chunks, 8192 upwind-scheme tiles do not fit even with one chunk
+    thin = I.uniform(4, 65536, 4, 8)
+    psi_thin = torch.zeros((32, 65536, 4), dtype=torch.float32, device="cuda")
+    assert _noalloc(thin, psi_thin, pg=1)[0] == btmg.OK
+    assert _noalloc(thin, psi_thin, pg=0)[0] == btmg.ERR_NOALLOC_TOO_LARGE
