@@ -55,7 +55,7 @@ def test_noalloc_matches_apply_operator_on_two_calls_in_a_row():
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     prob = I.uniform(1024, 512, 4, 8)  # 524288 nodes > 512 x 512
-    psi = torch.zeros((64, 512, 1024), dtype=torch.float32, device="cuda")
+    psi = torch.zeros((1, 32, 512, 1024), dtype=torch.float32, device="cuda")  # [G][nd][ny][nx]
     rc, _ = _noalloc(prob, psi)
     assert rc == btmg.ERR_NOALLOC_TOO_LARGE
 
@@ -76,6 +76,6 @@ def test_noalloc_upwind_scheme_and_its_partial_sum_limit():
     # 4 x 65536 nodes (the node limit), 32 directions: 2048 PG tiles fit with
     # 2 chunks, 8192 upwind-scheme tiles do not fit even with one chunk
     thin = I.uniform(4, 65536, 4, 8)
-    psi_thin = torch.zeros((32, 65536, 4), dtype=torch.float32, device="cuda")
+    psi_thin = torch.zeros((1, 32, 65536, 4), dtype=torch.float32, device="cuda")  # [G][nd][ny][nx]
     assert _noalloc(thin, psi_thin, pg=1)[0] == btmg.OK
     assert _noalloc(thin, psi_thin, pg=0)[0] == btmg.ERR_NOALLOC_TOO_LARGE
