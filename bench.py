@@ -221,6 +221,39 @@ def run_reference(args):
     return 0
 
 
+def sweep_rooflines(btmg, torch, prob, pk, peak_src, cycles=10):
+    """HBM roofline of the multigrid sweeps with the upwind fine scheme
+    (pg = 0; the operator of the converged solves and of the refinement) on
+    the same workload, FP32: the fine residual and Jacobi sweep (8 B per
+    unknown: psi in, r or psi out) and the finest nu-sweep upwind Jacobi
+    with the update (12 B per unknown: r1 and psi in, psi out), each
+    event-timed per launch in eager cycles."""
+    gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+    psi = gp.zeros()
+    for _ in range(3):
+        gp.mg_cycle(psi, want_residual=False)
+    gp.profile(True)
+    for _ in range(cycles):
+        gp.mg_cycle(psi, want_residual=False)
+    torch.cuda.synchronize()
+    prof = gp.profile_read()
+    gp.profile(False)
+    n = gp.num_unknowns() // gp.G
+    peak = float(pk["hbm_gbs"])
+    out = {"workload": "same as the metric, pg = 0 (upwind fine scheme), FP32", "peak": peak, "unit": "GB/s",
+           "peak_source": "%s copy bandwidth" % peak_src}
+    for cls, key, bpu, kernel in (("pg_residual", "k_upres_resid", 8, "fine residual (k_upres_tma)"),
+                                  ("pg_jacobi", "k_upres_jacobi", 8, "fine Jacobi (k_upres_tma)"),
+                                  ("upwind_fine", "k_upwind_fine", 12, "finest nu-sweep upwind Jacobi (k_upwind)")):
+        ms, cnt = prof[cls]
+        avg_s = ms / max(cnt, 1) / 1000.0
+        ach = n * bpu / avg_s / 1e9
+        out[cls] = {"kernel": kernel, "bytes_per_unknown": bpu, "ms": round(avg_s * 1e3, 4),
+                    "achieved": ach, "frac": ach / peak, "traffic": traffic_from_profiles(key)}
+    del gp, psi
+    return out
+
+
 def time_to_residual(btmg, torch, rtol=1e-6):
     """Seconds (wall, synchronised) and cycles to a relative residual of rtol
     for plain FP32 multigrid, FP64-refined FP32 / BF16 inner cycles and
@@ -334,6 +367,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-6 section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload section")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the upwind-scheme sweep rooflines")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -447,6 +481,8 @@ def main():
                        "l2": "inputs larger than L2 (psi, psi_tmp and r_1 are %d MB each)"
                              % (nbytes // 2 ** 20)},
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and not args.no_sweeps:
+        line["sweeps"] = sweep_rooflines(btmg, torch, prob, pk, src)
     if rank == 0 and not args.no_ttr:
         line["time_to_1e-6"] = time_to_residual(btmg, torch)
     if rank == 0 and not args.no_batch:
