@@ -11,16 +11,21 @@
 //   JACOBI: psi_out = psi + r / (beta (|mu|/dx + |nu|/dy + sigma_t)) and the
 //   scalar-flux partials of psi_out.
 //
-// The stencil reaches one node upstream, so no staging is needed: one CTA
-// owns a 128 x 8 tile and a chunk of directions (the partial sums per chunk
-// as in k_pg), a warp one 128-node row segment (whole 512-byte FP32 rows per
-// access) and a thread 4 consecutive nodes, whose sigma_t and b stay in
-// registers across the directions.  Per direction a thread loads its 4
-// values and the 4 of the upstream row (an L1/L2 hit: another warp's data),
-// takes the upstream column from the adjacent lane by a shuffle (one scalar
-// load at the segment edge), and the next direction's loads are in flight
-// while the current one is computed.  No shared memory and no barriers in
-// the loop: the kernel streams psi in and r (or psi) out.
+// The stencil reaches one node upstream.  One CTA owns a 128 x 8 tile and a
+// chunk of directions (the partial sums per chunk as in k_pg), a warp one
+// 128-node row segment (whole 512-byte FP32 rows per access) and a thread 4
+// consecutive nodes, whose sigma_t and b stay in registers across the
+// directions.  Two variants:
+//   k_upres_tma (the one that runs when psi's rows are 16-byte multiples):
+//     per direction a 144 x 10 box around the tile arrives in shared memory
+//     by one TMA copy, KS directions ahead (mbarrier pipeline, bounded
+//     waits); the upstream row and the tile-edge columns are read from the
+//     box, the neighbour columns inside the segment by lane shuffles;
+//   k_upres (any layout): the same work with plain loads, the next
+//     direction's values fetched into registers while the current one is
+//     computed.
+// Neither needs barriers inside a direction: the kernel streams psi in and
+// r (or psi) out.
 #include <cstring>
 #include <type_traits>
 
