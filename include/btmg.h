@@ -101,7 +101,8 @@ typedef struct {
 
 /* Builds the quadrature (Sec. 2.2), the space-angle hierarchy with harmonic
  * averaged cross sections (Sec. 2.5) and the device workspaces.  Copies every
- * host array.  Errors: INVALID_ARG (bad sizes, region ids, dtype, chunks),
+ * host array.  Errors: INVALID_ARG (bad sizes, region ids, dtype, chunks,
+ * a non-finite or negative cross section, a non-finite source),
  * UNSUPPORTED (pg = 1 with an order other than 2, except order 1 with FP64 or
  * FP32 storage), OOM, CUDA.  *out is NULL on failure.                       */
 int btmg_create_problem(const btmg_problem_desc* desc, void* stream, btmg_problem** out);
@@ -256,6 +257,14 @@ int btmg_learn_canvas(const btmg_problem* p, int32_t* h8, int32_t* w8, int32_t* 
  * rms of the mean rho of each group.                                       */
 int btmg_learn_features(btmg_problem* p, const void* psi, const void* psi_prev, float* feat, float* scale,
                         void* stream);
+
+/* Measurement helper (no counterpart in the paper): the FP32 FMA rate of
+ * this GPU in TFLOP/s, the best of `repeats` (>= 1) timed launches (after one
+ * warm-up) of a kernel that runs 8 independent fmaf chains per thread on
+ * every SM at full occupancy; CUDA events on `stream`.  Used beside the
+ * ALU roofline peak derived from unit counts and clock.
+ * Errors: INVALID_ARG, OOM, CUDA.                                          */
+int btmg_fp32_fma_rate(int32_t repeats, double* tflops, void* stream);
 
 /* Failure-path self-test (no counterpart in the paper).  Every wait of the
  * staged kernels on a copy (mbarrier) is bounded: when it gives up the kernel

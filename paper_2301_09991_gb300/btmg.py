@@ -33,7 +33,7 @@ EXPORTS = (
     "btmg_unet_set_params", "btmg_unet_get_grads", "btmg_unet_forward", "btmg_unet_train_step",
     "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_learn_canvas",
     "btmg_learn_features", "btmg_create_batch", "btmg_destroy_batch", "btmg_batch_problem",
-    "btmg_batch_chunks", "btmg_solve_batch", "btmg_wait_selftest",
+    "btmg_batch_chunks", "btmg_solve_batch", "btmg_wait_selftest", "btmg_fp32_fma_rate",
 )
 LEARN_FEATURES = 4  # input channels of the learned correction
 PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True):
     L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.btmg_learn_features.argtypes = [vp, vp, vp, vp, vp, vp]
     L.btmg_wait_selftest.argtypes = [i32, vp]
+    L.btmg_fp32_fma_rate.argtypes = [i32, dp, vp]
     L.btmg_create_batch.argtypes = [C.POINTER(Desc), i32, i32, vp, C.POINTER(vp)]
     L.btmg_destroy_batch.argtypes = [vp]
     L.btmg_batch_problem.argtypes = [vp, i32, C.POINTER(vp)]
@@ -142,6 +143,13 @@ def load(build_if_missing: bool = True):
     L.btmg_last_error.argtypes = []
     _lib = L
     return L
+
+
+def fp32_fma_rate(repeats=5, stream=None):
+    """Measured FP32 FMA throughput of this GPU (TFLOP/s)."""
+    t = C.c_double()
+    _check(load().btmg_fp32_fma_rate(int(repeats), C.byref(t), _stream_ptr(stream)))
+    return t.value
 
 
 def wait_selftest(polls=1000, stream=None):

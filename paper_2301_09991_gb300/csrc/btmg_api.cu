@@ -944,6 +944,14 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
   const size_t npix = (size_t)nx * ny;
   for (size_t i = 0; i < npix; ++i)
     if (d->region[i] < 0 || d->region[i] >= d->n_regions) return fail(BTMG_ERR_INVALID_ARG, "region id out of range");
+  // materials: finite, cross sections non-negative (sigma_t = 0 is a void)
+  for (size_t i = 0; i < (size_t)d->n_regions * G; ++i) {
+    if (!std::isfinite(d->sigma_t[i]) || d->sigma_t[i] < 0.0 || !std::isfinite(d->source[i]))
+      return fail(BTMG_ERR_INVALID_ARG, "sigma_t must be finite and >= 0, the source finite");
+  }
+  for (size_t i = 0; i < (size_t)d->n_regions * G * G; ++i)
+    if (!std::isfinite(d->sigma_s[i]) || d->sigma_s[i] < 0.0)
+      return fail(BTMG_ERR_INVALID_ARG, "sigma_s must be finite and >= 0");
 
   btmg_problem* P = new btmg_problem();
   P->d = *d;
@@ -1388,6 +1396,31 @@ int solve_batch(btmg_batch* B, void* const* psi, double rtol, int max_cycles, in
 }
 }  // namespace
 
+namespace {
+// FP32 FMA throughput probe: kFmaChains independent FFMA chains per thread
+// (enough to cover the pipe latency), iters rounds; the result is written
+// only under a condition the compiler cannot decide, so no chain is removed.
+constexpr int kFmaChains = 8;
+__global__ void k_fma_probe(float* out, int iters) {
+  float v[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) v[k] = 1e-3f * (float)(threadIdx.x + k);
+  const float m = 0.999999f, c = 1e-7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) v[k] = fmaf(v[k], m, c);
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) sum += v[k];
+  if (sum == -1.0f) out[0] = sum;
+}
+cudaError_t launch_fma_probe(float* out, int iters, int blocks, int block, cudaStream_t s) {
+  k_fma_probe<<<blocks, block, 0, s>>>(out, iters);
+  return cudaGetLastError();
+}
+}  // namespace
+
 extern "C" {
 
 int btmg_create_problem(const btmg_problem_desc* desc, void* stream, btmg_problem** out) {
@@ -1659,6 +1692,38 @@ const char* btmg_error_string(int status) {
 }
 
 const char* btmg_last_error(void) { return g_last_error.c_str(); }
+
+int btmg_fp32_fma_rate(int32_t repeats, double* tflops, void* stream) {
+  if (repeats < 1 || !tflops) return fail(BTMG_ERR_INVALID_ARG, "bad FMA-rate arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 152, threads = 2048;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+  const int block = 256, blocks = sms * (threads / block), iters = 1 << 15;
+  float* d = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaMalloc(&d, sizeof(float)));
+  double best = 0.0;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int r = 0; r <= repeats && e == cudaSuccess; ++r) {  // the first launch warms up
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_fma_probe(d, iters, blocks, block, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    const double flops = 2.0 * kFmaChains * (double)iters * blocks * block;
+    if (r > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d);
+  CK(e);
+  *tflops = best;
+  return BTMG_OK;
+}
 
 int btmg_wait_selftest(int32_t polls, void* stream) {
   if (polls < 1) return fail(BTMG_ERR_INVALID_ARG, "polls must be positive");
