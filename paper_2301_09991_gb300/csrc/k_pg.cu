@@ -123,7 +123,12 @@ constexpr int OFF_U = OFF_KY + H2 * W2;
 constexpr int OFF_TX = OFF_A;
 constexpr int OFF_TY = OFF_A + H2 * W4;
 constexpr int OFF_V = OFF_A;
-constexpr int PG_ELEMS = OFF_U + 3 * S4N;
+// Aligned copy of the staged tile over the k region (rows 4..39, columns
+// -2..33 of the tile: the origin of Kx/Ky), written by the x-derivative pass
+// from its aligned loads and read by the k-Diff y passes with 128-bit loads
+// (the staged tile itself is 8-byte aligned there: conflicting pair loads).
+constexpr int OFF_PK = OFF_U + 3 * S4N;
+constexpr int PG_ELEMS = OFF_PK + H2 * W2;
 static_assert(OFF_TY + H2 * W4 <= OFF_PX, "T arrays must stay inside the dead A/B region");
 static_assert(OFF_V + 3 * S4N <= OFF_PX, "V arrays must stay inside the dead A/B region");
 static_assert((PBUF * 4) % 128 == 0, "TMA destinations must be 128-byte aligned");
@@ -145,6 +150,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
   C* Ky = sm + OFF_KY;
   C* Tx = sm + OFF_TX;
   C* Ty = sm + OFF_TY;
+  C* Pk = sm + OFF_PK;
   C* U1 = sm + OFF_U;
   C* U2 = U1 + S4N;
   C* W1 = U2 + S4N;
@@ -261,6 +267,10 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
 #pragma unroll
             for (int k = 0; k < 4; ++k) o[k] = D1<C, ORD>(p[k], p[k + 1], p[k + 3], p[k + 4]);
             st4(A + r * W4 + c, o);
+            if (r >= 4 && r < 4 + H2 && c >= 4 && c <= W2) {  // tile rows -2..33, columns -2..33
+              const C pk[4] = {q0[2], q0[3], q1[0], q1[1]};
+              st4(Pk + (r - 4) * W2 + (c - 4), pk);
+            }
           } else {
             const int j = it - NA;
             const int r = (j / (W6 / 4)) * 2, c = (j % (W6 / 4)) * 4;
@@ -421,7 +431,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
 #pragma unroll
           for (int v = 0; v < 6; ++v) {
             ld4(K + (r + v) * W2 + c, kk[v]);
-            ld2x2(P + (r + 4 + v) * PS + c + 4, pp[v]);
+            ld4(Pk + (r + v) * W2 + c, pp[v]);
 #pragma unroll
             for (int k = 0; k < 4; ++k) pp[v][k] -= c0;
           }
@@ -481,7 +491,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
         }
       }
       C pcv[4], pxv[4], pyv[4], kxv[4], kyv[4];
-      ld2x2(P + (ry + 6) * PS + rx + 6, pcv);
+      ld4(P + (ry + 6) * PS + rx + 6, pcv);  // box column rx + 8: 16-byte aligned
 #pragma unroll
       for (int k = 0; k < 4; ++k) pcv[k] -= c0;  // psi - c0
       if constexpr (PGON) {
