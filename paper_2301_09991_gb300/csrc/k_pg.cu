@@ -427,37 +427,42 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
           const int j = xg ? it : it - N4;
           const int r = (j / (W2 / 4)) * 2, c = (j % (W2 / 4)) * 4;
           const C* K = xg ? Kx : Ky;
-          C kk[6][4], pp[6][4];
+          // the 6 input rows stream through: row v adds to output row 0 with
+          // tap v and to output row 1 with tap v - 1 (same sums, same order)
+          C o[2][3][4];
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+              for (int k = 0; k < 4; ++k) o[q][m][k] = C(0);
 #pragma unroll
           for (int v = 0; v < 6; ++v) {
-            ld4(K + (r + v) * W2 + c, kk[v]);
-            ld4(Pk + (r + v) * W2 + c, pp[v]);
+            C kk[4], pp[4];
+            ld4(K + (r + v) * W2 + c, kk);
+            ld4(Pk + (r + v) * W2 + c, pp);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) pp[v][k] -= c0;
+            for (int q = 0; q < 2; ++q) {
+              const int tap = v - q;
+              if (tap < 0 || tap > 4) continue;
+              const C w = xg ? M1<C, ORD>(tap) : S1<C, ORD>(tap);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const C pk = pp[k] - c0;
+                o[q][0][k] += w * kk[k] * pk;
+                o[q][1][k] += w * kk[k];
+                o[q][2][k] += w * pk;
+              }
+            }
           }
           C* d0 = xg ? U1 : V1;
           C* d1 = xg ? U2 : V2;
           C* d2 = xg ? W1 : V3;
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
-            C o0[4], o1[4], o2[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              C s0 = C(0), s1 = C(0), s2 = C(0);
-#pragma unroll
-              for (int v = 0; v < 5; ++v) {
-                const C w = xg ? M1<C, ORD>(v) : S1<C, ORD>(v);
-                s0 += w * kk[q + v][k] * pp[q + v][k];
-                s1 += w * kk[q + v][k];
-                s2 += w * pp[q + v][k];
-              }
-              o0[k] = s0;
-              o1[k] = s1;
-              o2[k] = s2;
-            }
-            st4(d0 + (r + q) * W2 + c, o0);
-            st4(d1 + (r + q) * W2 + c, o1);
-            st4(d2 + (r + q) * W2 + c, o2);
+            st4(d0 + (r + q) * W2 + c, o[q][0]);
+            st4(d1 + (r + q) * W2 + c, o[q][1]);
+            st4(d2 + (r + q) * W2 + c, o[q][2]);
           }
         }
       }
@@ -469,26 +474,24 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
       const int gy = y0 + ry;
       C fkp[4], fp[4], fk[4], gkp[4], gp[4], gk[4];
       if constexpr (PGON) {
-        C u1[8], u2[8], w1[8], v1[8], v2[8], v3[8];
-        ld8(U1 + ry * W2 + rx, u1);
-        ld8(U2 + ry * W2 + rx, u2);
-        ld8(W1 + ry * W2 + rx, w1);
-        ld8(V1 + ry * W2 + rx, v1);
-        ld8(V2 + ry * W2 + rx, v2);
-        ld8(V3 + ry * W2 + rx, v3);
+        // x group, then y group: three 8-wide rows live at a time
+        auto xpass = [&](const C* src, const bool sx, C (&o)[4]) {
+          C v[8];
+          ld8(src + ry * W2 + rx, v);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          fkp[k] = fp[k] = fk[k] = gkp[k] = gp[k] = gk[k] = C(0);
+          for (int k = 0; k < 4; ++k) {
+            C acc = C(0);
 #pragma unroll
-          for (int u = 0; u < 5; ++u) {
-            fkp[k] += S1<C, ORD>(u) * u1[k + u];
-            fk[k] += S1<C, ORD>(u) * u2[k + u];
-            fp[k] += S1<C, ORD>(u) * w1[k + u];
-            gkp[k] += M1<C, ORD>(u) * v1[k + u];
-            gk[k] += M1<C, ORD>(u) * v2[k + u];
-            gp[k] += M1<C, ORD>(u) * v3[k + u];
+            for (int u = 0; u < 5; ++u) acc += (sx ? S1<C, ORD>(u) : M1<C, ORD>(u)) * v[k + u];
+            o[k] = acc;
           }
-        }
+        };
+        xpass(U1, true, fkp);
+        xpass(U2, true, fk);
+        xpass(W1, true, fp);
+        xpass(V1, false, gkp);
+        xpass(V2, false, gk);
+        xpass(V3, false, gp);
       }
       C pcv[4], pxv[4], pyv[4], kxv[4], kyv[4];
       ld4(P + (ry + 6) * PS + rx + 6, pcv);  // box column rx + 8: 16-byte aligned
