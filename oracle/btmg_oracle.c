@@ -39,7 +39,15 @@
  *   R12 coarse equations per unit area and solid angle:
  *       s_{l+1} = sum_children p dx dy s_l / (P dX dY); beta = 1 there.
  *   R13 nu Jacobi sweeps on every level; one PG Jacobi sweep (beta = 3).
- *   R14 no scattering in the coarse / upwind correction operators.
+ *   R14 no scattering in the coarse / upwind correction operators (the
+ *       method as published).  Variant (scat_levels = 1: the levels of the
+ *       coarsest angular resolution, N_r = N_c = 1; 2: every level): the
+ *       upwind correction sweeps also carry the in-group isotropic
+ *       scattering sigma_s phi / (4 pi), each node's directions solved
+ *       together with their in-node scattering coupling (node-block
+ *       Jacobi, neighbours lagged).  Coarse sigma_s = harmonic sigma_t of
+ *       the level times the mean scattering ratio sigma_s / sigma_t of the
+ *       present children (S1).
  *   R16 each dimension (nx, ny, N_r, N_c) coarsens to ceil(n/2) until 1;
  *       a missing child counts as 0 in the restriction sum.
  *   R17 harmonic mean of the present children; 0 if any child is 0.
@@ -74,6 +82,8 @@ typedef struct {
   int32_t max_levels;      /* 0: coarsen until every dimension is 1         */
   int32_t pg_half;         /* 1: multiply f^{k-Diff} by 1/2 (analytic form) */
   int32_t ngauss;          /* Gauss points per patch dimension (16)         */
+  int32_t scat_levels;     /* R14 variant: 0 off, 1 coarsest angular levels,
+                              2 every level                                 */
 } or_desc;
 
 typedef struct {
@@ -81,6 +91,7 @@ typedef struct {
   double dx, dy;
   double *mu, *nu, *xi, *p; /* [nd] */
   double* sigt;             /* [G][ny][nx] */
+  double* cratio;           /* [G][ny][nx] in-group sigma_s / sigma_t (S1)  */
 } or_level;
 
 typedef struct or_problem {
@@ -354,6 +365,7 @@ void or_destroy(or_problem* P) {
     free(P->lev[l].xi);
     free(P->lev[l].p);
     free(P->lev[l].sigt);
+    free(P->lev[l].cratio);
   }
   free(P->sigs);
   free(P->src);
@@ -369,6 +381,7 @@ or_problem* or_create(const or_desc* d) {
   if (d->n_polar < 2 || d->n_azim < 4 || d->n_polar % 2 || d->n_azim % 4)
     return NULL;
   if (d->order < 1 || d->order > 3 || d->nu < 0) return NULL;
+  if (d->scat_levels < 0 || d->scat_levels > 2) return NULL;
   or_problem* P = (or_problem*)calloc(1, sizeof(or_problem));
   if (!P) return NULL;
   P->d = *d;
@@ -394,6 +407,7 @@ or_problem* or_create(const or_desc* d) {
   P->src = (double*)calloc((size_t)G * nx * ny, sizeof(double));
   or_level* L0 = &P->lev[0];
   L0->sigt = (double*)calloc((size_t)G * nx * ny, sizeof(double));
+  L0->cratio = (double*)calloc((size_t)G * nx * ny, sizeof(double));
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       int rg = d->region[y * nx + x];
@@ -403,6 +417,9 @@ or_problem* or_create(const or_desc* d) {
       }
       for (int g = 0; g < G; ++g) {
         L0->sigt[((size_t)g * ny + y) * nx + x] = d->sigma_t[rg * G + g];
+        if (d->sigma_t[rg * G + g] > 0.0)
+          L0->cratio[((size_t)g * ny + y) * nx + x] =
+              d->sigma_s[(rg * G + g) * G + g] / d->sigma_t[rg * G + g];
         P->src[((size_t)g * ny + y) * nx + x] = d->source[rg * G + g];
         for (int h = 0; h < G; ++h)
           P->sigs[(((size_t)g * G + h) * ny + y) * nx + x] =
@@ -442,22 +459,25 @@ or_problem* or_create(const or_desc* d) {
                   B->nu, B->xi, B->p);
     /* harmonic average of the present spatial children (R17) */
     B->sigt = (double*)calloc((size_t)G * B->nx * B->ny, sizeof(double));
+    B->cratio = (double*)calloc((size_t)G * B->nx * B->ny, sizeof(double));
     int fx = (A->nx > 1) ? 2 : 1, fy = (A->ny > 1) ? 2 : 1;
     for (int g = 0; g < G; ++g)
       for (int Y = 0; Y < B->ny; ++Y)
         for (int X = 0; X < B->nx; ++X) {
           int cnt = 0, zero = 0;
-          double inv = 0;
+          double inv = 0, cr = 0;
           for (int b = 0; b < fy; ++b)
             for (int a = 0; a < fx; ++a) {
               int x = X * fx + a, y = Y * fy + b;
               if (x >= A->nx || y >= A->ny) continue;
               double s = A->sigt[((size_t)g * A->ny + y) * A->nx + x];
               ++cnt;
+              cr += A->cratio[((size_t)g * A->ny + y) * A->nx + x];
               if (s == 0.0) zero = 1;
               else inv += 1.0 / s;
             }
           B->sigt[((size_t)g * B->ny + Y) * B->nx + X] = zero ? 0.0 : cnt / inv;
+          B->cratio[((size_t)g * B->ny + Y) * B->nx + X] = cr / cnt; /* S1 */
         }
     P->L++;
   }
@@ -497,6 +517,13 @@ int or_level_sigt(const or_problem* P, int l, double* out) {
   if (l < 0 || l >= P->L) return -1;
   const or_level* A = &P->lev[l];
   memcpy(out, A->sigt, sizeof(double) * P->G * A->nx * A->ny);
+  return 0;
+}
+/* In-group scattering ratio per node of level l (S1), [G][ny][nx]. */
+int or_level_cratio(const or_problem* P, int l, double* out) {
+  if (l < 0 || l >= P->L) return -1;
+  const or_level* A = &P->lev[l];
+  memcpy(out, A->cratio, sizeof(double) * P->G * A->nx * A->ny);
   return 0;
 }
 
@@ -879,6 +906,58 @@ static void jacobi_upwind_group(const or_problem* P, int lev, int g, const doubl
   }
 }
 
+/* Does level lev carry the in-group scattering in its upwind sweeps (R14
+ * variant)?                                                               */
+static int scat_on(const or_problem* P, int lev) {
+  if (P->d.scat_levels == 2) return 1;
+  if (P->d.scat_levels == 1) return P->lev[lev].nr == 1 && P->lev[lev].nc == 1;
+  return 0;
+}
+
+/* One node-block Jacobi sweep with the in-node scattering (R14 variant).
+ * With the neighbours taken from the old iterate, the directions of one node
+ * solve together
+ *   d_n delta_n - kappa sum_m p_m delta_m = s_n + d_n delta_n^old - (A_up delta^old)_n,
+ * kappa = sigma_s / (4 pi) (R3, S1).  Dividing by d_n, the right-hand side
+ * is the plain Jacobi update a_n; the system is the identity plus a rank-one
+ * term, so with Phi = sum_m p_m delta_m:
+ *   delta_n = a_n + kappa Phi / d_n,   Phi = (sum_n p_n a_n) / (1 - kappa sum_n p_n / d_n). */
+static void jacobi_scat_group(const or_problem* P, int lev, int g, const double* s,
+                              double* delta, int sweeps) {
+  const or_level* A = &P->lev[lev];
+  const size_t np = (size_t)A->nx * A->ny;
+  double* a = (double*)malloc(sizeof(double) * np * A->nd);
+  for (int k = 0; k < sweeps; ++k) {
+#pragma omp parallel for schedule(dynamic)
+    for (int n = 0; n < A->nd; ++n) {
+      double* an = a + (size_t)n * np;
+      const double* d = delta + (size_t)n * np;
+      const double* sn = s + (size_t)n * np;
+      upwind_apply_plane(P, lev, g, n, d, an);
+      for (int y = 0; y < A->ny; ++y)
+        for (int x = 0; x < A->nx; ++x) {
+          size_t i = (size_t)y * A->nx + x;
+          an[i] = d[i] + (sn[i] - an[i]) / upwind_diag(A, g, n, x, y);
+        }
+    }
+#pragma omp parallel for
+    for (int y = 0; y < A->ny; ++y)
+      for (int x = 0; x < A->nx; ++x) {
+        size_t i = (size_t)y * A->nx + x, gi = (size_t)g * np + i;
+        double kappa = A->cratio[gi] * A->sigt[gi] / (4.0 * OR_PI);
+        double spa = 0.0, spd = 0.0;
+        for (int n = 0; n < A->nd; ++n) {
+          spa += A->p[n] * a[(size_t)n * np + i];
+          spd += A->p[n] / upwind_diag(A, g, n, x, y);
+        }
+        double Phi = spa / (1.0 - kappa * spd);
+        for (int n = 0; n < A->nd; ++n)
+          delta[(size_t)n * np + i] = a[(size_t)n * np + i] + kappa * Phi / upwind_diag(A, g, n, x, y);
+      }
+  }
+  free(a);
+}
+
 /* Restriction level lev -> lev+1 for one group's correction source
  * (Sec. 2.5, R12, R16): s_C = sum_children p_c dx dy s_c / (P_C dX dY).
  * Children: 2 (or 1) in each of x, y, polar and azimuth; missing -> 0.     */
@@ -948,7 +1027,10 @@ int or_prolong(const or_problem* P, int lev, const double* coarse, double* fine)
 int or_jacobi_upwind(const or_problem* P, int lev, int g, const double* s,
                      double* delta, int sweeps) {
   if (lev < 0 || lev >= P->L || g < 0 || g >= P->G) return -1;
-  jacobi_upwind_group(P, lev, g, s, delta, sweeps);
+  if (scat_on(P, lev))
+    jacobi_scat_group(P, lev, g, s, delta, sweeps);
+  else
+    jacobi_upwind_group(P, lev, g, s, delta, sweeps);
   return 0;
 }
 
@@ -980,6 +1062,7 @@ static void pg_jacobi_group(const or_problem* P, int g, double* psi_g, const dou
  *   2. s_1 = r_1, s_{l+1} = R(s_l)                           (restriction)
  *   3. delta_L = nu upwind Jacobi sweeps from 0 with s_L
  *   4. l = L-1..1: delta_l = nu sweeps from UpSamp(delta_{l+1}) with s_l
+ *      (node-block sweeps with scattering on the R14 variant's levels)
  *   5. psi += delta_1
  *   6. one fine PG Jacobi sweep with diagonal beta d_1        (beta = 3)
  * Returns ||r_1||_W / ||q||_W of the input psi (R19).                      */
@@ -997,7 +1080,10 @@ static double cycle_group(const or_problem* P, int g, double* psi_g, const doubl
   for (int l = 0; l + 1 < L; ++l) restrict_group(P, l, s[l], s[l + 1]);
   for (int l = L - 1; l >= 0; --l) {
     if (l < L - 1) prolong_group(P, l, dl[l + 1], dl[l]);
-    jacobi_upwind_group(P, l, g, s[l], dl[l], P->d.nu);
+    if (scat_on(P, l))
+      jacobi_scat_group(P, l, g, s[l], dl[l], P->d.nu);
+    else
+      jacobi_upwind_group(P, l, g, s[l], dl[l], P->d.nu);
   }
   const size_t n1 = level_size(P, 0);
   for (size_t i = 0; i < n1; ++i) psi_g[i] += dl[0][i];

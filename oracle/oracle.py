@@ -56,6 +56,7 @@ class _Desc(C.Structure):
         ("max_levels", C.c_int32),
         ("pg_half", C.c_int32),
         ("ngauss", C.c_int32),
+        ("scat_levels", C.c_int32),
     ]
 
 
@@ -75,6 +76,7 @@ def lib():
         L.or_level_dims.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int32), dp]
         L.or_level_quad.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, dp]
         L.or_level_sigt.argtypes = [C.c_void_p, C.c_int, dp]
+        L.or_level_cratio.argtypes = [C.c_void_p, C.c_int, dp]
         L.or_get_filters.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
         L.or_set_extra_source.argtypes = [C.c_void_p, dp]
         L.or_set_frozen_k.argtypes = [C.c_void_p, dp, dp]
@@ -147,7 +149,7 @@ class OracleProblem:
     by ``paper_2301_09991_gb300.inputs`` (region map + per-region tables)."""
 
     def __init__(self, prob, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0,
-                 ngauss=16, order=None):
+                 ngauss=16, order=None, scat_levels=0):
         self.prob = prob
         self._region = np.ascontiguousarray(prob["region"], dtype=np.int32)
         self._st = _f64(prob["sigma_t"])
@@ -166,6 +168,7 @@ class OracleProblem:
             d.bc[i] = int(b)
         d.pg, d.nu, d.beta_pg = int(pg), int(nu), float(beta_pg)
         d.max_levels, d.pg_half, d.ngauss = int(max_levels), int(pg_half), int(ngauss)
+        d.scat_levels = int(scat_levels)
         self._d = d
         self.h = lib().or_create(C.byref(d))
         if not self.h:
@@ -193,8 +196,10 @@ class OracleProblem:
         lib().or_level_quad(self.h, l, _p(mu), _p(nu), _p(xi), _p(p))
         sig = np.zeros((self._d.n_groups, ny, nx))
         lib().or_level_sigt(self.h, l, _p(sig))
+        cr = np.zeros_like(sig)
+        lib().or_level_cratio(self.h, l, _p(cr))
         return dict(nx=nx, ny=ny, nr=nr, nc=nc, nd=nd, dx=dxdy[0], dy=dxdy[1],
-                    mu=mu, nu=nu, xi=xi, p=p, sigt=sig)
+                    mu=mu, nu=nu, xi=xi, p=p, sigt=sig, cratio=cr)
 
     def filters(self):
         w = 2 * self._d.order + 1
