@@ -87,6 +87,16 @@ typedef struct {
                               resident CTAs; otherwise a divisor of the number
                               of directions, at most 64 (set by the batch
                               autotuner)                                     */
+  int32_t scat_levels;     /* scattering smoother, a variant of the upwind
+                              correction sweeps (the method as published has
+                              none, Sec. 2.5): 0 off; 1 on the levels of the
+                              coarsest angular resolution (N_r = N_c = 1);
+                              2 on every level.  On those levels each node's
+                              directions are solved together with the in-group
+                              isotropic scattering sigma_s phi / (4 pi), upstream
+                              neighbours lagged; coarse sigma_s = harmonic
+                              sigma_t x the mean sigma_s / sigma_t of the
+                              children.  Needs sigma_s,gg <= sigma_t.          */
 } btmg_problem_desc;
 
 typedef struct {
@@ -102,7 +112,8 @@ typedef struct {
 /* Builds the quadrature (Sec. 2.2), the space-angle hierarchy with harmonic
  * averaged cross sections (Sec. 2.5) and the device workspaces.  Copies every
  * host array.  Errors: INVALID_ARG (bad sizes, region ids, dtype, chunks,
- * a non-finite or negative cross section, a non-finite source),
+ * a non-finite or negative cross section, a non-finite source, scat_levels
+ * outside 0..2 or, with scat_levels, an in-group sigma_s above sigma_t),
  * UNSUPPORTED (pg = 1 with an order other than 2, except order 1 with FP64 or
  * FP32 storage), OOM, CUDA.  *out is NULL on failure.                       */
 int btmg_create_problem(const btmg_problem_desc* desc, void* stream, btmg_problem** out);
@@ -141,9 +152,11 @@ int btmg_apply_operator(btmg_problem* p, const void* psi, void* r, void* stream)
  *    (groups in order), psi device [G][nd][ny][nx].
  *  kind = BTMG_SMOOTH_UPWIND: `sweeps` Jacobi sweeps of the upwind system
  *    A_up,l psi = src of level `level` for group `group` (beta = 1, no
- *    scattering: the correction equation of the cycle); psi and src are
- *    device buffers of one group on that level, [nd_l][ny_l][nx_l], both of
- *    the compute type.                                                     */
+ *    scattering: the correction equation of the cycle; on the levels of the
+ *    scattering smoother (desc.scat_levels) node-block sweeps of
+ *    (A_up,l - sigma_s / (4 pi) sum_n p_n) psi = src instead); psi and src
+ *    are device buffers of one group on that level, [nd_l][ny_l][nx_l], both
+ *    of the compute type.                                                  */
 int btmg_smooth(btmg_problem* p, void* psi, const void* src, int32_t level, int32_t group,
                 int32_t sweeps, int32_t kind, void* stream);
 

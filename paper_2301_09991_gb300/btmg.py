@@ -59,6 +59,7 @@ class Desc(C.Structure):
         ("max_levels", C.c_int32),
         ("pg_half", C.c_int32),
         ("chunks", C.c_int32),
+        ("scat_levels", C.c_int32),
     ]
 
 
@@ -189,7 +190,8 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def make_desc(prob, dtype=F32, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0, order=None, chunks=0):
+def make_desc(prob, dtype=F32, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0, order=None, chunks=0,
+              scat_levels=0):
     """btmg_problem_desc of a problem dict (see inputs.py) and the host arrays
     it points to (keep them alive until the problem is created)."""
     keep = (np.ascontiguousarray(prob["region"], dtype=np.int32),
@@ -214,6 +216,7 @@ def make_desc(prob, dtype=F32, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0,
     d.pg, d.nu_jacobi, d.beta_pg = int(pg), int(nu), float(beta_pg)
     d.psi_dtype, d.max_levels, d.pg_half = int(dtype), int(max_levels), int(pg_half)
     d.chunks = int(chunks)
+    d.scat_levels = int(scat_levels)
     return d, keep
 
 
@@ -226,12 +229,12 @@ class Problem:
     """
 
     def __init__(self, prob, dtype=F32, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0,
-                 order=None, stream=None, chunks=0):
+                 order=None, stream=None, chunks=0, scat_levels=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("btmg needs a CUDA device (sm_103a); there is no CPU path")
         L = load()
-        d, self._keep = make_desc(prob, dtype, pg, nu, beta_pg, max_levels, pg_half, order, chunks)
+        d, self._keep = make_desc(prob, dtype, pg, nu, beta_pg, max_levels, pg_half, order, chunks, scat_levels)
         h = C.c_void_p()
         _check(L.btmg_create_problem(C.byref(d), _stream_ptr(stream), C.byref(h)))
         self._owned = True
@@ -442,7 +445,7 @@ class Batch:
     btmg_solve_batch): one graph launch advances every unconverged problem
     by one cycle.  `problems[i]` are non-owning Problem views."""
 
-    def __init__(self, probs, dtype=F32, pg=0, nu=3, autotune=False, chunks=None, stream=None):
+    def __init__(self, probs, dtype=F32, pg=0, nu=3, autotune=False, chunks=None, stream=None, scat_levels=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("btmg needs a CUDA device (sm_103a); there is no CPU path")
@@ -451,7 +454,7 @@ class Batch:
         descs = (Desc * n)()
         self._keep = []
         for i, prob in enumerate(probs):
-            d, keep = make_desc(prob, dtype, pg, nu, chunks=(chunks[i] if chunks else 0))
+            d, keep = make_desc(prob, dtype, pg, nu, chunks=(chunks[i] if chunks else 0), scat_levels=scat_levels)
             descs[i] = d
             self._keep.append(keep)
         h = C.c_void_p()

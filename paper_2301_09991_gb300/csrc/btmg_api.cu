@@ -129,6 +129,13 @@ struct btmg_problem {
   bool upscatter = false;
   // device buffers (compute type unless noted)
   std::vector<void*> d_dir, d_rcoef, d_sig, d_s, d_delta, d_parent;
+  // scattering smoother (desc.scat_levels): per level on/off and gain w
+  // [G][npix]; shared sweep scratch (largest smoothed level)
+  std::vector<char> scat_on;
+  std::vector<void*> d_scat_w;
+  void* d_scat_j = nullptr;     // [nd][ny][nx]
+  void* d_scat_part = nullptr;  // [chunks][ny][nx]
+  void* d_scat_c = nullptr;     // [ny][nx]
   void* d_sigs = nullptr;      // [G][G][npix]
   void* d_src = nullptr;       // [G][npix]
   void* d_b = nullptr;         // [npix]
@@ -337,6 +344,79 @@ template <typename T, typename C> struct Impl {
     return u;
   }
 
+  // `sweeps` node-block sweeps of the scattering smoother on level l, group
+  // g, from the initial correction of init_mode (INIT_ZERO; INIT_UPSAMPLE of
+  // d_delta[l + 1]; INIT_SAME of `init`).  The result delta lands in
+  // d_delta[l]; with psi_out set (finest level) the final pass writes
+  // psi_out = psi_in + delta and the scalar-flux partials of psi_out instead.
+  static cudaError_t scat_level(btmg_problem* P, int l, int g, const C* src, int init_mode, const C* init,
+                                int sweeps, const T* psi_in, T* psi_out, C* phi_part, int cls, cudaStream_t s) {
+    const LevelH& A = P->lev[l];
+    const int nch = scat_chunks(A.nx, A.ny, A.nd);
+    const int dpc = (A.nd + nch - 1) / nch;
+    C* X = dptr<C>(P->d_delta[l]);  // the last sweep writes here
+    C* Y = dptr<C>(P->d_scat_j);
+    const C* w = dptr<C>(P->d_scat_w[l]) + (size_t)g * A.npix();
+    const C* sig = dptr<C>(P->d_sig[l]) + (size_t)g * A.npix();
+    const Dir<C>* dir = reinterpret_cast<const Dir<C>*>(P->d_dir[l]);
+    C* part = dptr<C>(P->d_scat_part);
+    C* cf = dptr<C>(P->d_scat_c);
+    cudaError_t e;
+    const C* prev = init;
+    for (int k = 1; k <= sweeps; ++k) {
+      ScatArgs<C> a{};
+      a.src = src;
+      a.src_stride = A.npix();
+      a.init_mode = k == 1 ? init_mode : INIT_SAME;
+      a.jin = prev;
+      a.cin = k == 1 ? nullptr : cf;
+      if (k == 1 && init_mode == INIT_UPSAMPLE) {
+        const LevelH& B = P->lev[l + 1];
+        a.coarse = dptr<C>(P->d_delta[l + 1]);
+        a.parent = reinterpret_cast<const int*>(P->d_parent[l]);
+        a.nxc = B.nx;
+        a.nyc = B.ny;
+        a.fx = A.fx;
+        a.fy = A.fy;
+      }
+      a.jout = (sweeps - k) % 2 == 0 ? X : Y;
+      a.part = part;
+      a.sig = sig;
+      a.dir = dir;
+      a.nx = A.nx;
+      a.ny = A.ny;
+      a.nd = A.nd;
+      a.dpc = dpc;
+      a.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
+      if ((e = timed(P, cls, s, [&] { return launch_scat_sweep<C>(a, nch, s); })) != cudaSuccess) return e;
+      if (k < sweeps &&
+          (e = timed(P, cls, s, [&] { return launch_scat_corr<C>(part, nch, w, (int)A.npix(), cf, s); })) !=
+              cudaSuccess)
+        return e;
+      prev = a.jout;
+    }
+    ScatFinal<T, C> f{};
+    f.j = X;
+    f.part = part;
+    f.nchunk_in = nch;
+    f.w = w;
+    f.sig = sig;
+    f.dir = dir;
+    f.nx = A.nx;
+    f.ny = A.ny;
+    f.nd = A.nd;
+    if (psi_out) {
+      f.psi_in = psi_in;
+      f.psi_out = psi_out;
+      f.phi_part = phi_part;
+      f.dpc = P->dpc;
+      return timed(P, cls, s, [&] { return launch_scat_final<T, C>(f, P->nchunk, s); });
+    }
+    f.delta_out = X;
+    f.dpc = dpc;
+    return timed(P, cls, s, [&] { return launch_scat_final<T, C>(f, nch, s); });
+  }
+
   // One sawtooth cycle of group g (Fig. multi_grid_it); the scalar-flux
   // partials of every group must describe the current psi on entry and
   // describe the updated psi on exit.  Part A evaluates the residual of the
@@ -375,6 +455,13 @@ template <typename T, typename C> struct Impl {
     }
     // 3./4. upwind Jacobi from the coarsest level up, UpSamp in between
     for (int l = L - 1; l >= 1; --l) {
+      if (P->scat_on[l]) {
+        const int im = (l == L - 1) ? INIT_ZERO : INIT_UPSAMPLE;
+        if ((e = scat_level(P, l, g, dptr<C>(P->d_s[l]), im, nullptr, P->d.nu_jacobi, nullptr, nullptr, nullptr,
+                            PC_UP_COARSE, s)) != cudaSuccess)
+          return e;
+        continue;
+      }
       UpArgs<T, C> u = up_args(P, l, g);
       u.src = dptr<C>(P->d_s[l]);
       u.init_mode = (l == L - 1) ? INIT_ZERO : INIT_UPSAMPLE;
@@ -385,7 +472,12 @@ template <typename T, typename C> struct Impl {
         return e;
     }
     // 4./5. finest level: nu sweeps from UpSamp(delta_2), psi_tmp = psi + delta
-    {
+    if (P->scat_on[0]) {
+      C* ph = homog ? dptr<C>(P->d_lphi) : dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
+      if ((e = scat_level(P, 0, g, dptr<C>(P->d_s[0]), L > 1 ? INIT_UPSAMPLE : INIT_ZERO, nullptr, P->d.nu_jacobi,
+                          psi_g, dptr<T>(P->d_psi_tmp), ph, PC_UP_FINE, s)) != cudaSuccess)
+        return e;
+    } else {
       UpArgs<T, C> u = up_args(P, 0, g);
       u.src = dptr<C>(P->d_s[0]);
       u.init_mode = (L > 1) ? INIT_UPSAMPLE : INIT_ZERO;
@@ -828,6 +920,12 @@ template <typename T, typename C> struct RunSmoothUp {
   static int run(btmg_problem* P, void* psi, const void* src, int l, int g, int sweeps, cudaStream_t s) {
     const LevelH& A = P->lev[l];
     if (!P->d_delta[l]) CK(cudaMalloc(&P->d_delta[l], A.n() * sizeof(C)));
+    if (P->scat_on[l] && sweeps > 0) {  // scattering smoother on this level
+      CK(Impl<T, C>::scat_level(P, l, g, reinterpret_cast<const C*>(src), INIT_SAME, reinterpret_cast<const C*>(psi),
+                                sweeps, nullptr, nullptr, nullptr, PC_UP_COARSE, s));
+      CK(cudaMemcpyAsync(psi, P->d_delta[l], A.n() * sizeof(C), cudaMemcpyDeviceToDevice, s));
+      return BTMG_OK;
+    }
     int left = sweeps;
     while (left > 0) {
       const int k = left > 8 ? 8 : left;
@@ -855,9 +953,11 @@ void destroy(btmg_problem* P) {
                   P->d_lprev_all})
     if (p) cudaFree(p);
   for (cudaEvent_t e : P->prof_pool) cudaEventDestroy(e);
-  for (auto v : {&P->d_dir, &P->d_rcoef, &P->d_sig, &P->d_s, &P->d_delta, &P->d_parent})
+  for (auto v : {&P->d_dir, &P->d_rcoef, &P->d_sig, &P->d_s, &P->d_delta, &P->d_parent, &P->d_scat_w})
     for (void* p : *v)
       if (p) cudaFree(p);
+  for (void* p : {P->d_scat_j, P->d_scat_part, P->d_scat_c})
+    if (p) cudaFree(p);
   for (void* p : {P->d_sigs, P->d_src, P->d_b, P->d_phi_part, P->d_psi_tmp, (void*)P->d_norm_part, (void*)P->d_err,
                   (void*)P->d_qn2_part, (void*)P->d_rn2, (void*)P->d_qn2})
     if (p) cudaFree(p);
@@ -952,6 +1052,12 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
   for (size_t i = 0; i < (size_t)d->n_regions * G * G; ++i)
     if (!std::isfinite(d->sigma_s[i]) || d->sigma_s[i] < 0.0)
       return fail(BTMG_ERR_INVALID_ARG, "sigma_s must be finite and >= 0");
+  if (d->scat_levels < 0 || d->scat_levels > 2) return fail(BTMG_ERR_INVALID_ARG, "scat_levels must be 0, 1 or 2");
+  if (d->scat_levels)
+    for (int r = 0; r < d->n_regions; ++r)
+      for (int g = 0; g < G; ++g)
+        if (d->sigma_s[((size_t)r * G + g) * G + g] > d->sigma_t[(size_t)r * G + g])
+          return fail(BTMG_ERR_INVALID_ARG, "the scattering smoother needs sigma_s,gg <= sigma_t");
 
   btmg_problem* P = new btmg_problem();
   P->d = *d;
@@ -1100,6 +1206,76 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
     if (l >= 1 && cudaMalloc(&P->d_delta[l], A.n() * P->csize) != cudaSuccess)
       return bail(fail(BTMG_ERR_OOM, "workspace delta"));
   }
+  // scattering smoother: the levels it runs on, the gain
+  // w = kappa / (1 - kappa sum_n p_n / d_n) per level and group (kappa =
+  // sigma_s / (4 pi), coarse sigma_s = harmonic sigma_t x the mean child
+  // ratio sigma_s / sigma_t), sweep scratch for the largest smoothed level
+  P->scat_on.assign(P->L, 0);
+  P->d_scat_w.assign(P->L, nullptr);
+  if (d->scat_levels) {
+    std::vector<double> crat((size_t)G * npix, 0.0);
+    for (size_t i = 0; i < npix; ++i)
+      for (int g = 0; g < G; ++g) {
+        const int rg = d->region[i];
+        const double st = d->sigma_t[(size_t)rg * G + g];
+        if (st > 0.0) crat[(size_t)g * npix + i] = d->sigma_s[((size_t)rg * G + g) * G + g] / st;
+      }
+    size_t max_n = 0, max_part = 0, max_pix = 0;
+    for (int l = 0; l < P->L; ++l) {
+      const LevelH& A = P->lev[l];
+      if (l > 0) {  // mean over the present children
+        const LevelH& F2 = P->lev[l - 1];
+        std::vector<double> cc((size_t)G * A.npix(), 0.0);
+        for (int g = 0; g < G; ++g)
+          for (int Y = 0; Y < A.ny; ++Y)
+            for (int X = 0; X < A.nx; ++X) {
+              double acc = 0.0;
+              int cnt = 0;
+              for (int yy = 0; yy < F2.fy; ++yy)
+                for (int xx = 0; xx < F2.fx; ++xx) {
+                  const int x = X * F2.fx + xx, y = Y * F2.fy + yy;
+                  if (x >= F2.nx || y >= F2.ny) continue;
+                  acc += crat[(size_t)g * F2.npix() + (size_t)y * F2.nx + x];
+                  ++cnt;
+                }
+              cc[(size_t)g * A.npix() + (size_t)Y * A.nx + X] = acc / cnt;
+            }
+        crat.swap(cc);
+      }
+      P->scat_on[l] = d->scat_levels == 2 || (A.nr == 1 && A.nc == 1);
+      if (!P->scat_on[l]) continue;
+      void* tmp = nullptr;
+      if (P->f64) put_vals<double>(buf, crat);
+      else put_vals<float>(buf, crat);
+      if ((rc = upload(&tmp, buf))) return bail(rc);
+      if (cudaMalloc(&P->d_scat_w[l], (size_t)G * A.npix() * P->csize) != cudaSuccess) {
+        cudaFree(tmp);
+        return bail(fail(BTMG_ERR_OOM, "scattering smoother gain"));
+      }
+      cudaError_t ge = cudaSuccess;
+      for (int g = 0; g < G && ge == cudaSuccess; ++g) {
+        const size_t o = (size_t)g * A.npix();
+        ge = P->f64 ? launch_scat_gain<double>(dptr<double>(P->d_sig[l]) + o, dptr<double>(tmp) + o,
+                                               reinterpret_cast<const Dir<double>*>(P->d_dir[l]), A.nd,
+                                               (int)A.npix(), dptr<double>(P->d_scat_w[l]) + o, 0)
+                     : launch_scat_gain<float>(dptr<float>(P->d_sig[l]) + o, dptr<float>(tmp) + o,
+                                               reinterpret_cast<const Dir<float>*>(P->d_dir[l]), A.nd,
+                                               (int)A.npix(), dptr<float>(P->d_scat_w[l]) + o, 0);
+      }
+      if (ge == cudaSuccess) ge = cudaStreamSynchronize(0);
+      cudaFree(tmp);
+      if (ge != cudaSuccess) return bail(fail(BTMG_ERR_CUDA, cudaGetErrorString(ge)));
+      max_n = std::max(max_n, A.n());
+      max_pix = std::max(max_pix, A.npix());
+      max_part = std::max(max_part, (size_t)scat_chunks(A.nx, A.ny, A.nd) * A.npix());
+      if (l == 0 && cudaMalloc(&P->d_delta[0], A.n() * P->csize) != cudaSuccess)
+        return bail(fail(BTMG_ERR_OOM, "workspace delta"));
+    }
+    if (max_n && (cudaMalloc(&P->d_scat_j, max_n * P->csize) != cudaSuccess ||
+                  cudaMalloc(&P->d_scat_part, max_part * P->csize) != cudaSuccess ||
+                  cudaMalloc(&P->d_scat_c, max_pix * P->csize) != cudaSuccess))
+      return bail(fail(BTMG_ERR_OOM, "scattering smoother workspace"));
+  }
   if (P->f64) put_vals<double>(buf, sigs);
   else put_vals<float>(buf, sigs);
   if ((rc = upload(&P->d_sigs, buf))) return bail(rc);
@@ -1164,9 +1340,10 @@ template <typename T, typename C> struct RunResidual {
 
 // Autotuner cache: problem shape -> (chunks, ms per eager cycle).
 struct TuneKey {
-  int nx, ny, nd, G, dtype, pg, nu;
+  int nx, ny, nd, G, dtype, pg, nu, scat;
   bool operator<(const TuneKey& o) const {
-    return std::tie(nx, ny, nd, G, dtype, pg, nu) < std::tie(o.nx, o.ny, o.nd, o.G, o.dtype, o.pg, o.nu);
+    return std::tie(nx, ny, nd, G, dtype, pg, nu, scat) <
+           std::tie(o.nx, o.ny, o.nd, o.G, o.dtype, o.pg, o.nu, o.scat);
   }
 };
 std::mutex g_tune_mu;
@@ -1210,7 +1387,7 @@ int time_cycles(const btmg_problem_desc& d, int warm, int cycles, cudaStream_t s
 int tune_chunks(const btmg_problem_desc& d, cudaStream_t s, int* chunks, double* ms) {
   const int nd = d.n_polar * d.n_azim;
   const int tiles = ((d.nx + kTile - 1) / kTile) * ((d.ny + kTile - 1) / kTile);
-  const TuneKey key{d.nx, d.ny, nd, d.n_groups, d.psi_dtype, d.pg, d.nu_jacobi};
+  const TuneKey key{d.nx, d.ny, nd, d.n_groups, d.psi_dtype, d.pg, d.nu_jacobi, d.scat_levels};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);

@@ -116,6 +116,45 @@ template <typename T, typename C> int pg_blocks_per_sm(bool pg);
 template <typename T, typename C>
 cudaError_t launch_upwind(const UpArgs<T, C>& a, int mode, int nchunk, cudaStream_t s);
 
+// Scattering smoother (node-block Jacobi with in-node isotropic scattering;
+// a variant of the upwind correction sweeps, k_scat.cu).
+template <typename C> struct ScatArgs {
+  const C* src;        // [nd][ny][nx] correction source
+  size_t src_stride;   // elements between direction planes of src
+  int init_mode;       // INIT_ZERO, INIT_UPSAMPLE (coarse, parent) or INIT_SAME (jin, cin)
+  const C* jin;        // INIT_SAME: [nd][ny][nx] plain update J of the previous sweep
+  const C* cin;        // INIT_SAME: [ny][nx] isotropic correction c of that sweep, or NULL
+  const C* coarse;     // INIT_UPSAMPLE: coarser correction [ndc][nyc][nxc]
+  const int* parent;   // INIT_UPSAMPLE: coarse direction of each direction [nd]
+  int nxc, nyc, fx, fy;
+  C* jout;             // [nd][ny][nx]
+  C* part;             // [nchunk][ny][nx] sum of p_n J_n over each chunk
+  const C* sig;        // [ny][nx]
+  const Dir<C>* dir;   // [nd]
+  int nx, ny, nd, dpc;
+  Bc bc;
+};
+template <typename T, typename C> struct ScatFinal {
+  const C* j;          // [nd][ny][nx] J of the last sweep (may alias delta_out)
+  const C* part;       // [nchunk_in][ny][nx] its partial sums
+  int nchunk_in;
+  const C* w;          // [ny][nx] gain kappa / (1 - kappa sum p / d)
+  const C* sig;
+  const Dir<C>* dir;
+  int nx, ny, nd, dpc; // output chunking (dpc directions per block row)
+  C* delta_out;        // delta = J + c / d, or NULL with psi_out set
+  const T* psi_in;     // finest level: psi_out = psi_in + delta,
+  T* psi_out;          //   scalar-flux partials of psi_out in phi_part
+  C* phi_part;         //   [nchunk][ny][nx]
+};
+template <typename C> cudaError_t launch_scat_sweep(const ScatArgs<C>& a, int nchunk, cudaStream_t s);
+template <typename C>
+cudaError_t launch_scat_corr(const C* part, int nchunk, const C* w, int npix, C* c, cudaStream_t s);
+template <typename T, typename C> cudaError_t launch_scat_final(const ScatFinal<T, C>& f, int nchunk, cudaStream_t s);
+template <typename C>
+cudaError_t launch_scat_gain(const C* sig, const C* crat, const Dir<C>* dir, int nd, int npix, C* w, cudaStream_t s);
+int scat_chunks(int nx, int ny, int nd);  // direction chunks of a sweep on a level
+
 template <typename C>
 cudaError_t launch_restrict(const C* fine, C* coarse, const C* rcoef, int nx, int ny, int nr, int nc,
                             int nxc, int nyc, int nrc, int ncc, int fx, int fy, int fr, int fc,

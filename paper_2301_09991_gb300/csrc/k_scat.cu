@@ -1,0 +1,208 @@
+// k_scat.cu -- the scattering smoother: a variant of the upwind correction
+// sweeps (Eq. matrix_full with beta = 1, upwind filters of Sec. 2.4) in
+// which the directions of a node are solved together with their in-node
+// isotropic scattering sigma_s phi / (4 pi) (Sec. 2.2), the upstream
+// neighbours taken from the previous iterate (node-block Jacobi).  The
+// method as published keeps scattering out of the correction operators; the
+// variant carries it on the levels of the coarsest angular resolution or on
+// every level, where in-group scattering dominates.
+//
+// With a_n the plain Jacobi update of direction n and d_n = |mu|/dX +
+// |nu|/dY + sigma_t its diagonal, the node's system is the identity plus a
+// rank-one term and is solved exactly:
+//   delta_n = a_n + c / d_n,   c = w sum_m p_m a_m,
+//   w = kappa / (1 - kappa sum_m p_m / d_m),   kappa = sigma_s / (4 pi).
+// w depends only on the level's directions and materials (k_scat_gain, once
+// per problem).  A sweep stores J = a and the partial sums of p_n J_n over
+// its chunk of directions; the isotropic field c is formed from the
+// partials after the sweep (k_scat_corr) and applied on the fly where the
+// next sweep reads its upstream values, and by the final pass
+// (k_scat_final), which writes delta or, on the finest level, the update
+// psi + delta with the scalar-flux partials of the result.
+//
+// Layout: one thread per node of a 32 x 8 tile, looping over the directions
+// of its chunk; consecutive threads read consecutive x (coalesced), the
+// upstream row is mostly read by the same block (L1).
+#include "btmg_common.cuh"
+
+namespace btmg {
+namespace {
+
+constexpr int SX = 32, SY = 8;
+
+__device__ __forceinline__ float srcp(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ double srcp(double v) { return 1.0 / v; }
+
+// Node of this thread, its four neighbours clamped into the domain (an
+// out-of-domain neighbour points at the node itself: the adjacent interior
+// node of the halo rule) and which of them left the domain.
+struct NodeGeo {
+  int x, y;
+  bool in;
+  size_t i0, ixm, ixp, iym, iyp;
+  bool oxm, oxp, oym, oyp;
+  __device__ NodeGeo(int nx, int ny) {
+    const int tiles_x = (nx + SX - 1) / SX;
+    x = (blockIdx.x % tiles_x) * SX + threadIdx.x;
+    y = (blockIdx.x / tiles_x) * SY + threadIdx.y;
+    in = x < nx && y < ny;
+    const int xi = min(x, nx - 1), yi = min(y, ny - 1);
+    oxm = xi == 0;
+    oxp = xi == nx - 1;
+    oym = yi == 0;
+    oyp = yi == ny - 1;
+    i0 = (size_t)yi * nx + xi;
+    ixm = oxm ? i0 : i0 - 1;
+    ixp = oxp ? i0 : i0 + 1;
+    iym = oym ? i0 : i0 - nx;
+    iyp = oyp ? i0 : i0 + nx;
+  }
+};
+
+template <typename C> __global__ void __launch_bounds__(SX * SY) k_scat_sweep(const ScatArgs<C> a) {
+  const NodeGeo g(a.nx, a.ny);
+  const size_t npix = (size_t)a.nx * a.ny;
+  const int chunk = blockIdx.y;
+  const int n_begin = chunk * a.dpc, n_end = min(n_begin + a.dpc, a.nd);
+  // materials and the isotropic correction of the previous sweep at the
+  // node and its neighbours (scalars: the upstream pair is chosen per
+  // direction by select, not by indexing)
+  const C s0 = a.sig[g.i0];
+  const C sxm = a.sig[g.ixm], sxq = a.sig[g.ixp], sym = a.sig[g.iym], syq = a.sig[g.iyp];
+  C cxm = C(0), cxq = C(0), cym = C(0), cyq = C(0);
+  if (a.cin) cxm = a.cin[g.ixm], cxq = a.cin[g.ixp], cym = a.cin[g.iym], cyq = a.cin[g.iyp];
+  size_t oxm = 0, oxq = 0, oym = 0, oyq = 0;  // UpSamp parents of the neighbours
+  if (a.init_mode == INIT_UPSAMPLE) {
+    auto parent_of = [&](size_t i) {
+      const int px = (int)(i % a.nx), py = (int)(i / a.nx);
+      return (size_t)(py / a.fy) * a.nxc + px / a.fx;
+    };
+    oxm = parent_of(g.ixm), oxq = parent_of(g.ixp), oym = parent_of(g.iym), oyq = parent_of(g.iyp);
+  }
+  const size_t npixc = (size_t)a.nxc * a.nyc;
+  C acc = C(0);
+  for (int n = n_begin; n < n_end; ++n) {
+    const Dir<C> dr = a.dir[n];
+    const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
+    const bool out_x = sxp ? g.oxm : g.oxp, out_y = syp ? g.oym : g.oyp;
+    const bool zx = out_x && (sxp ? a.bc.xlo : a.bc.xhi) == BC_VACUUM;
+    const bool zy = out_y && (syp ? a.bc.ylo : a.bc.yhi) == BC_VACUUM;
+    const size_t ix = sxp ? g.ixm : g.ixp, iy = syp ? g.iym : g.iyp;  // upstream neighbours
+    C ux = C(0), uy = C(0);
+    if (a.init_mode == INIT_SAME) {
+      const C* jn = a.jin + (size_t)n * npix;
+      if (!zx) ux = jn[ix] + (sxp ? cxm : cxq) * srcp(dr.ax + dr.ay + (sxp ? sxm : sxq));
+      if (!zy) uy = jn[iy] + (syp ? cym : cyq) * srcp(dr.ax + dr.ay + (syp ? sym : syq));
+    } else if (a.init_mode == INIT_UPSAMPLE) {
+      const C* cn = a.coarse + (size_t)a.parent[n] * npixc;
+      if (!zx) ux = cn[sxp ? oxm : oxq];
+      if (!zy) uy = cn[syp ? oym : oyq];
+    }
+    const C J = (a.src[(size_t)n * a.src_stride + g.i0] + dr.ax * ux + dr.ay * uy) * srcp(dr.ax + dr.ay + s0);
+    if (g.in) a.jout[(size_t)n * npix + g.i0] = J;
+    acc += dr.w * J;
+  }
+  if (g.in) a.part[(size_t)chunk * npix + g.i0] = acc;
+}
+
+template <typename C>
+__global__ void k_scat_corr(const C* __restrict__ part, int nchunk, const C* __restrict__ w, int npix,
+                            C* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  C s = C(0);
+  for (int k = 0; k < nchunk; ++k) s += part[(size_t)k * npix + i];
+  c[i] = w[i] * s;
+}
+
+template <typename T, typename C, bool UPDATE> __global__ void __launch_bounds__(SX * SY) k_scat_final(const ScatFinal<T, C> f) {
+  const NodeGeo g(f.nx, f.ny);
+  if (!g.in) return;
+  const size_t npix = (size_t)f.nx * f.ny;
+  const int chunk = blockIdx.y;
+  const int n_begin = chunk * f.dpc, n_end = min(n_begin + f.dpc, f.nd);
+  C s = C(0);
+  for (int k = 0; k < f.nchunk_in; ++k) s += f.part[(size_t)k * npix + g.i0];
+  const C c0 = f.w[g.i0] * s, s0 = f.sig[g.i0];
+  C acc = C(0);
+  for (int n = n_begin; n < n_end; ++n) {
+    const Dir<C> dr = f.dir[n];
+    const size_t gi = (size_t)n * npix + g.i0;
+    const C d = f.j[gi] + c0 * srcp(dr.ax + dr.ay + s0);
+    if (UPDATE) {
+      const C pn = (C)Conv<T>::ld(f.psi_in + gi) + d;
+      Conv<T>::st(f.psi_out + gi, pn);
+      acc += dr.w * stored<T, C>(pn);
+    } else {
+      f.delta_out[gi] = d;
+    }
+  }
+  if (UPDATE) f.phi_part[(size_t)chunk * npix + g.i0] = acc;
+}
+
+template <typename C>
+__global__ void k_scat_gain(const C* __restrict__ sig, const C* __restrict__ crat, const Dir<C>* __restrict__ dir,
+                            int nd, int npix, C* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  const double st = (double)sig[i];
+  double S = 0.0;
+  for (int n = 0; n < nd; ++n) S += (double)dir[n].w / ((double)dir[n].ax + (double)dir[n].ay + st);
+  const double kappa = (double)crat[i] * st / (4.0 * 3.14159265358979323846);
+  w[i] = (C)(kappa / (1.0 - kappa * S));
+}
+
+dim3 node_grid(int nx, int ny, int nchunk) {
+  return dim3(((nx + SX - 1) / SX) * ((ny + SY - 1) / SY), nchunk);
+}
+
+}  // namespace
+
+template <typename C> cudaError_t launch_scat_sweep(const ScatArgs<C>& a, int nchunk, cudaStream_t s) {
+  k_scat_sweep<C><<<node_grid(a.nx, a.ny, nchunk), dim3(SX, SY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t launch_scat_corr(const C* part, int nchunk, const C* w, int npix, C* c, cudaStream_t s) {
+  k_scat_corr<C><<<(npix + 255) / 256, 256, 0, s>>>(part, nchunk, w, npix, c);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C> cudaError_t launch_scat_final(const ScatFinal<T, C>& f, int nchunk, cudaStream_t s) {
+  if (f.psi_out)
+    k_scat_final<T, C, true><<<node_grid(f.nx, f.ny, nchunk), dim3(SX, SY), 0, s>>>(f);
+  else
+    k_scat_final<T, C, false><<<node_grid(f.nx, f.ny, nchunk), dim3(SX, SY), 0, s>>>(f);
+  return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t launch_scat_gain(const C* sig, const C* crat, const Dir<C>* dir, int nd, int npix, C* w, cudaStream_t s) {
+  k_scat_gain<C><<<(npix + 255) / 256, 256, 0, s>>>(sig, crat, dir, nd, npix, w);
+  return cudaGetLastError();
+}
+
+// node-tile chunking shared by the sweep launches and the workspace sizing
+int scat_chunks(int nx, int ny, int nd) {
+  const int tiles = ((nx + SX - 1) / SX) * ((ny + SY - 1) / SY);
+  const int want = (2432 + tiles - 1) / tiles;  // about two waves of 8 blocks on 152 SMs
+  int c = want < 1 ? 1 : (want > 64 ? 64 : want);
+  if (c > nd) c = nd;
+  const int dpc = (nd + c - 1) / c;
+  return (nd + dpc - 1) / dpc;
+}
+
+#define INST_SC(C)                                                                                       \
+  template cudaError_t launch_scat_sweep<C>(const ScatArgs<C>&, int, cudaStream_t);                      \
+  template cudaError_t launch_scat_corr<C>(const C*, int, const C*, int, C*, cudaStream_t);              \
+  template cudaError_t launch_scat_gain<C>(const C*, const C*, const Dir<C>*, int, int, C*, cudaStream_t);
+INST_SC(double)
+INST_SC(float)
+template cudaError_t launch_scat_final<double, double>(const ScatFinal<double, double>&, int, cudaStream_t);
+template cudaError_t launch_scat_final<float, float>(const ScatFinal<float, float>&, int, cudaStream_t);
+template cudaError_t launch_scat_final<__nv_bfloat16, float>(const ScatFinal<__nv_bfloat16, float>&, int,
+                                                              cudaStream_t);
+template cudaError_t launch_scat_final<__half, float>(const ScatFinal<__half, float>&, int, cudaStream_t);
+
+}  // namespace btmg
