@@ -250,6 +250,31 @@ def sweep_rooflines(btmg, torch, prob, pk, peak_src, cycles=10):
         ach = n * bpu / avg_s / 1e9
         out[cls] = {"kernel": kernel, "bytes_per_unknown": bpu, "ms": round(avg_s * 1e3, 4),
                     "achieved": ach, "frac": ach / peak, "traffic": traffic_from_profiles(key)}
+    out["cycle_ms"] = round(sum(v[0] for v in prof.values()) / cycles, 4)
+    del gp, psi
+    # the scattering smoother on every level (scat_levels = 2): the finest
+    # level's nu sweeps (J and the source in, J out: 12 B per unknown each),
+    # and the final pass (J and psi in, psi out: 12 B), per cycle
+    gp = btmg.Problem(prob, dtype=btmg.F32, pg=0, scat_levels=2)
+    psi = gp.zeros()
+    for _ in range(3):
+        gp.mg_cycle(psi, want_residual=False)
+    gp.profile(True)
+    for _ in range(cycles):
+        gp.mg_cycle(psi, want_residual=False)
+    torch.cuda.synchronize()
+    prof = gp.profile_read()
+    gp.profile(False)
+    nu = 3
+    bpu = 12 * (nu + 1)
+    fine_s = prof["upwind_fine"][0] / cycles / 1000.0
+    ach = n * bpu / fine_s / 1e9
+    out["scatter_fine"] = {"kernel": "finest-level scattering smoother (k_scat_sweep x 3, k_scat_corr x 2, "
+                                     "k_scat_final)", "bytes_per_unknown_per_cycle": bpu,
+                           "ms_per_cycle": round(fine_s * 1e3, 4), "achieved": ach, "frac": ach / peak,
+                           "launches_per_cycle": prof["upwind_fine"][1] // cycles,
+                           "coarse_ms_per_cycle": round(prof["upwind_coarse"][0] / cycles, 4),
+                           "cycle_ms": round(sum(v[0] for v in prof.values()) / cycles, 4)}
     del gp, psi
     return out
 
@@ -260,7 +285,10 @@ def time_to_residual(btmg, torch, rtol=1e-6):
     cycles per FP64 outer step: the FP64 residual is the costly part of a
     step on this GPU, whose FP64 rate is a small fraction of its FP32 rate) and
     FP64-refined FP32 with the learned correction (upwind fine operator,
-    pg = 0, for which the FP64 refinement is defined)."""
+    pg = 0, for which the FP64 refinement is defined), and FP64-refined FP32 /
+    BF16 with the scattering smoother on every level (scat_levels = 2, judged
+    by plain multigrid: an outer residual above 1.5 times the best drops it
+    for the rest of the solve)."""
     from paper_2301_09991_gb300 import learned as LN
     net = LN.load_net(os.path.join(ROOT, "paper_2301_09991_gb300", "weights", "unet_thick.npy"))
     cases = {
@@ -291,22 +319,27 @@ def time_to_residual(btmg, torch, rtol=1e-6):
         row["plain_f32"] = {"seconds": round(sec, 4), "cycles": r["cycles"], "rel_resid": r["rel_resid"],
                             "reached": bool(r["rel_resid"] <= rtol)}
         del gp, psi
-        for key, dt, nt in (("refined_f32", btmg.F32, None), ("refined_bf16", btmg.BF16, None),
-                            ("refined_f32_learned", btmg.F32, net)):
-            gp = btmg.Problem(prob, dtype=dt, pg=0)
+        for key, dt, nt, scat, inner in (("refined_f32", btmg.F32, None, 0, 32),
+                                         ("refined_bf16", btmg.BF16, None, 0, 32),
+                                         ("refined_f32_learned", btmg.F32, net, 0, 32),
+                                         ("refined_f32_scatter", btmg.F32, None, 2, 32),
+                                         ("refined_bf16_scatter", btmg.BF16, None, 2, 32)):
+            gp = btmg.Problem(prob, dtype=dt, pg=0, scat_levels=scat)
             if nt is not None:
                 gp.set_learned(nt, every=4)
             psi64 = torch.zeros(gp.shape, dtype=torch.float64, device="cuda")
 
             def refined():
                 psi64.zero_()
-                return gp.solve_refined(psi64, rtol=rtol, max_outer=300, inner_cycles=32)
+                return gp.solve_refined(psi64, rtol=rtol, max_outer=300, inner_cycles=inner)
             r, sec = timed(refined)
             row[key] = {"seconds": round(sec, 4), "cycles": r["cycles"], "rel_resid": r["rel_resid"],
                         "reached": bool(r["rel_resid"] <= rtol)}
             if nt is not None:
                 st = gp.learn_stats()
                 row[key].update({"learned_steps": st[0], "fallbacks": st[3]})
+            if scat:
+                row[key]["fallbacks"] = gp.scatter_fallbacks()
             del gp, psi64
         out[name] = row
     return out

@@ -247,6 +247,14 @@ const char* btmg_unet_last_error(void);
  * without the step as CUDA graphs.  The U-net must outlive its use.
  * Errors: INVALID_ARG (null problem, every < 1), OOM.                      */
 int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every);
+/* Number of solves on p that dropped the scattering smoother
+ * (desc.scat_levels) for the rest of the call: plain multigrid judges it as
+ * it judges the learned step, btmg_solve when a residual exceeds twice its
+ * best so far, btmg_solve_refined when an outer FP64 residual exceeds 1.5
+ * times its best; the next call starts with the smoother again.  Batched
+ * solves do not fall back.  Errors: INVALID_ARG (NULL argument).          */
+int btmg_scatter_fallbacks(const btmg_problem* p, int32_t* fallbacks);
+
 /* Learned steps since btmg_set_learned, their mean residual reduction
  * factor ||r' + alpha rc|| / ||r'||, the last alpha, and the number of solves
  * that fell back to plain cycles (synchronises the device).  A solve falls

@@ -31,7 +31,7 @@ EXPORTS = (
     "btmg_launch_count", "btmg_apply_operator_noalloc", "btmg_solve_refined",
     "btmg_unet_create", "btmg_unet_destroy", "btmg_unet_num_params", "btmg_unet_get_params",
     "btmg_unet_set_params", "btmg_unet_get_grads", "btmg_unet_forward", "btmg_unet_train_step",
-    "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_learn_canvas",
+    "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_scatter_fallbacks", "btmg_learn_canvas",
     "btmg_learn_features", "btmg_create_batch", "btmg_destroy_batch", "btmg_batch_problem",
     "btmg_batch_chunks", "btmg_solve_batch", "btmg_wait_selftest", "btmg_fp32_fma_rate",
 )
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
                                               C.POINTER(i32), i32, i32, vp, vp, vp, vp, vp, vp]
     L.btmg_set_learned.argtypes = [vp, vp, i32]
     L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i32)]
+    L.btmg_scatter_fallbacks.argtypes = [vp, C.POINTER(i32)]
     L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.btmg_learn_features.argtypes = [vp, vp, vp, vp, vp, vp]
     L.btmg_wait_selftest.argtypes = [i32, vp]
@@ -325,6 +326,13 @@ class Problem:
         """Attach (or with None detach) a learned correction, see btmg.h."""
         self._unet = unet  # keep the network alive while attached
         _check(load().btmg_set_learned(self.h, unet.h if unet is not None else None, int(every)))
+
+    def scatter_fallbacks(self):
+        """Solves on this problem that dropped the scattering smoother
+        (plain-judged fallback)."""
+        n = C.c_int32()
+        _check(load().btmg_scatter_fallbacks(self.h, C.byref(n)))
+        return n.value
 
     def learn_stats(self):
         """(learned steps, mean residual reduction factor, last alpha,

@@ -136,6 +136,9 @@ struct btmg_problem {
   void* d_scat_j = nullptr;     // [nd][ny][nx]
   void* d_scat_part = nullptr;  // [chunks][ny][nx]
   void* d_scat_c = nullptr;     // [ny][nx]
+  int scat_tail = 0;            // first level of the single-CTA tail (L: none)
+  bool scat_off = false;        // solve-time fallback to the plain sweeps
+  int32_t scat_fallbacks = 0;   // solves that fell back
   void* d_sigs = nullptr;      // [G][G][npix]
   void* d_src = nullptr;       // [G][npix]
   void* d_b = nullptr;         // [npix]
@@ -453,9 +456,35 @@ template <typename T, typename C> struct Impl {
            })) != cudaSuccess)
         return e;
     }
-    // 3./4. upwind Jacobi from the coarsest level up, UpSamp in between
-    for (int l = L - 1; l >= 1; --l) {
-      if (P->scat_on[l]) {
+    // 3./4. upwind Jacobi from the coarsest level up, UpSamp in between (the
+    // smallest levels of the scattering smoother in one launch)
+    int top = L - 1;
+    if (P->scat_tail < L && !P->scat_off) {
+      ScatTail<C> t{};
+      t.count = L - P->scat_tail;
+      t.nu = P->d.nu_jacobi;
+      t.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
+      t.out = dptr<C>(P->d_delta[P->scat_tail]);
+      for (int k = 0; k < t.count; ++k) {
+        const int l = P->scat_tail + k;
+        const LevelH& A = P->lev[l];
+        ScatTailLevel<C>& v = t.lev[k];
+        v.src = dptr<C>(P->d_s[l]);
+        v.w = dptr<C>(P->d_scat_w[l]) + (size_t)g * A.npix();
+        v.sig = dptr<C>(P->d_sig[l]) + (size_t)g * A.npix();
+        v.dir = reinterpret_cast<const Dir<C>*>(P->d_dir[l]);
+        v.parent = l + 1 < L ? reinterpret_cast<const int*>(P->d_parent[l]) : nullptr;
+        v.nx = A.nx;
+        v.ny = A.ny;
+        v.nd = A.nd;
+        v.fx = A.fx;
+        v.fy = A.fy;
+      }
+      if ((e = timed(P, PC_UP_COARSE, s, [&] { return launch_scat_tail<C>(t, s); })) != cudaSuccess) return e;
+      top = P->scat_tail - 1;
+    }
+    for (int l = top; l >= 1; --l) {
+      if (P->scat_on[l] && !P->scat_off) {
         const int im = (l == L - 1) ? INIT_ZERO : INIT_UPSAMPLE;
         if ((e = scat_level(P, l, g, dptr<C>(P->d_s[l]), im, nullptr, P->d.nu_jacobi, nullptr, nullptr, nullptr,
                             PC_UP_COARSE, s)) != cudaSuccess)
@@ -472,7 +501,7 @@ template <typename T, typename C> struct Impl {
         return e;
     }
     // 4./5. finest level: nu sweeps from UpSamp(delta_2), psi_tmp = psi + delta
-    if (P->scat_on[0]) {
+    if (P->scat_on[0] && !P->scat_off) {
       C* ph = homog ? dptr<C>(P->d_lphi) : dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
       if ((e = scat_level(P, 0, g, dptr<C>(P->d_s[0]), L > 1 ? INIT_UPSAMPLE : INIT_ZERO, nullptr, P->d.nu_jacobi,
                           psi_g, dptr<T>(P->d_psi_tmp), ph, PC_UP_FINE, s)) != cudaSuccess)
@@ -667,6 +696,7 @@ template <typename T, typename C> struct Impl {
     const int check = (info && info->check_every > 0) ? info->check_every : 1;
     if (P->graph_psi != psi || P->graph_stream != s) free_graphs(P);
     P->learn_off = false;
+    P->scat_off = false;
     int cycles = 0, status = BTMG_OK;
     CK(phi_partials(P, ps, s));
     int max_outer = (info && info->max_outer > 0) ? info->max_outer : (P->upscatter ? 8 : 1);
@@ -723,6 +753,14 @@ template <typename T, typename C> struct Impl {
               P->learn_off = true;
               ++P->learn_fallbacks;
             }
+            // and the scattering smoother likewise: the rest of this solve
+            // runs the published cycle (recaptured, first cycle eager)
+            if (P->d.scat_levels && !P->scat_off && best < 1e299 && rel > 2.0 * best) {
+              P->scat_off = true;
+              ++P->scat_fallbacks;
+              free_graphs(P);
+              warm[0] = warm[1] = false;
+            }
             if (rel < best) best = rel;
             if (rel <= rtol) break;
           }
@@ -737,6 +775,10 @@ template <typename T, typename C> struct Impl {
       CK(phi_partials(P, ps, s));
     }
     if (status == BTMG_OK && !(rel_all <= rtol)) status = std::isnan(rel_all) ? BTMG_ERR_NAN : BTMG_ERR_NOT_CONVERGED;
+    if (P->scat_off) {  // later calls start with the smoother again
+      P->scat_off = false;
+      free_graphs(P);
+    }
     if (info) {
       info->cycles = cycles;
       info->rel_resid = rel_all;
@@ -765,6 +807,7 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
     d2.source = P->h_source.data();
     d2.psi_dtype = BTMG_F64;
     d2.max_levels = 1;
+    d2.scat_levels = 0;  // residuals only
     int rc = create(&d2, &P->twin);
     if (rc) return rc;
   }
@@ -780,6 +823,7 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
   int cycles = 0, status = BTMG_ERR_NOT_CONVERGED;
   double rel = 0.0, best = 1e300;
   P->learn_off = false;
+  P->scat_off = false;
   for (int outer = 0; outer <= max_outer; ++outer) {
     CK(Impl<double, double>::residual_all(Q, psi64, P->d_r64, s));
     int rc = Impl<double, double>::read_rel(Q, s, 0, nullptr, &rel);
@@ -800,6 +844,11 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
       P->learn_off = true;
       ++P->learn_fallbacks;
     }
+    if (P->d.scat_levels && !P->scat_off && rel > 1.5 * best) {  // and the scattering smoother
+      P->scat_off = true;
+      ++P->scat_fallbacks;
+      free_graphs(P);
+    }
     if (rel < best) best = rel;
     double rn2 = 0.0;
     for (int g = 0; g < P->G; ++g) rn2 += Q->h_pinned[g];
@@ -818,6 +867,10 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
     CK(launch_refine_update<T>(psi64, dptr<T>(P->d_delta_all), 1.0 / alpha, n_all, s));
   }
   CK(cudaStreamSynchronize(s));
+  if (P->scat_off) {  // later calls start with the smoother again
+    P->scat_off = false;
+    free_graphs(P);
+  }
   if (info) {
     info->cycles = cycles;
     info->rel_resid = rel;
@@ -1212,6 +1265,7 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
   // ratio sigma_s / sigma_t), sweep scratch for the largest smoothed level
   P->scat_on.assign(P->L, 0);
   P->d_scat_w.assign(P->L, nullptr);
+  P->scat_tail = P->L;
   if (d->scat_levels) {
     std::vector<double> crat((size_t)G * npix, 0.0);
     for (size_t i = 0; i < npix; ++i)
@@ -1271,6 +1325,12 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
       if (l == 0 && cudaMalloc(&P->d_delta[0], A.n() * P->csize) != cudaSuccess)
         return bail(fail(BTMG_ERR_OOM, "workspace delta"));
     }
+    // the coarsest levels that fit the single-CTA tail kernel (not level 0)
+    const int tmax = P->f64 ? scat_tail_max<double>() : scat_tail_max<float>();
+    P->scat_tail = P->L;
+    while (P->scat_tail - 1 >= 1 && P->L - (P->scat_tail - 1) <= kScatTailLevels && P->scat_on[P->scat_tail - 1] &&
+           P->lev[P->scat_tail - 1].n() <= (size_t)tmax)
+      --P->scat_tail;
     if (max_n && (cudaMalloc(&P->d_scat_j, max_n * P->csize) != cudaSuccess ||
                   cudaMalloc(&P->d_scat_part, max_part * P->csize) != cudaSuccess ||
                   cudaMalloc(&P->d_scat_c, max_pix * P->csize) != cudaSuccess))
@@ -1776,6 +1836,12 @@ int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every) {
   p->learn_count = 0;
   p->learn_fallbacks = 0;
   if (p->d_lstat) CK(cudaMemset(p->d_lstat, 0, sizeof(double) * 3));
+  return BTMG_OK;
+}
+
+int btmg_scatter_fallbacks(const btmg_problem* p, int32_t* fallbacks) {
+  if (!p || !fallbacks) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  *fallbacks = p->scat_fallbacks;
   return BTMG_OK;
 }
 

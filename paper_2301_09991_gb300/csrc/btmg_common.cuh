@@ -154,6 +154,25 @@ template <typename T, typename C> cudaError_t launch_scat_final(const ScatFinal<
 template <typename C>
 cudaError_t launch_scat_gain(const C* sig, const C* crat, const Dir<C>* dir, int nd, int npix, C* w, cudaStream_t s);
 int scat_chunks(int nx, int ny, int nd);  // direction chunks of a sweep on a level
+// The coarsest levels, each of at most scat_tail_max<C>() unknowns, run in
+// one single-CTA launch (k_scat_tail); lev[0] is the finest of them.
+constexpr int kScatTailLevels = 16;
+template <typename C> constexpr int scat_tail_max() { return sizeof(C) == 8 ? 4096 : 8192; }
+template <typename C> struct ScatTailLevel {
+  const C* src;       // [nd][ny][nx] restricted residual of the level
+  const C* w;         // [ny][nx] gain
+  const C* sig;       // [ny][nx]
+  const Dir<C>* dir;  // [nd]
+  const int* parent;  // coarser-level direction of each direction (not for the coarsest)
+  int nx, ny, nd, fx, fy;  // fx, fy: factors to the coarser level
+};
+template <typename C> struct ScatTail {
+  ScatTailLevel<C> lev[kScatTailLevels];
+  int count, nu;
+  Bc bc;
+  C* out;  // delta of lev[0], [nd][ny][nx]
+};
+template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStream_t s);
 
 template <typename C>
 cudaError_t launch_restrict(const C* fine, C* coarse, const C* rcoef, int nx, int ny, int nr, int nc,

@@ -81,6 +81,7 @@ template <typename C> __global__ void __launch_bounds__(SX * SY) k_scat_sweep(co
   }
   const size_t npixc = (size_t)a.nxc * a.nyc;
   C acc = C(0);
+#pragma unroll 4
   for (int n = n_begin; n < n_end; ++n) {
     const Dir<C> dr = a.dir[n];
     const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
@@ -125,6 +126,7 @@ template <typename T, typename C, bool UPDATE> __global__ void __launch_bounds__
   for (int k = 0; k < f.nchunk_in; ++k) s += f.part[(size_t)k * npix + g.i0];
   const C c0 = f.w[g.i0] * s, s0 = f.sig[g.i0];
   C acc = C(0);
+#pragma unroll 4
   for (int n = n_begin; n < n_end; ++n) {
     const Dir<C> dr = f.dir[n];
     const size_t gi = (size_t)n * npix + g.i0;
@@ -150,6 +152,72 @@ __global__ void k_scat_gain(const C* __restrict__ sig, const C* __restrict__ cra
   for (int n = 0; n < nd; ++n) S += (double)dir[n].w / ((double)dir[n].ax + (double)dir[n].ay + st);
   const double kappa = (double)crat[i] * st / (4.0 * 3.14159265358979323846);
   w[i] = (C)(kappa / (1.0 - kappa * S));
+}
+
+// The small coarsest levels in one CTA (they are launch-bound as separate
+// kernels): for each level from the coarsest up, nu sweeps and the final
+// pass with block barriers between the phases; the sweep iterates, the
+// isotropic field and the coarser level's correction live in shared memory.
+// Same arithmetic as the per-level kernels, the scalar flux of a sweep
+// summed over all directions at once.
+template <typename C, int TMAX> __global__ void __launch_bounds__(1024) k_scat_tail(const ScatTail<C> t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Ja = reinterpret_cast<C*>(smem_raw);
+  C* Jb = Ja + TMAX;
+  C* Dc = Jb + TMAX;  // the coarser level's delta, then this level's
+  C* cf = Dc + TMAX;  // isotropic correction c of the last sweep, [ny][nx]
+  for (int li = t.count - 1; li >= 0; --li) {
+    const ScatTailLevel<C> L = t.lev[li];
+    const int npix = L.nx * L.ny, n_all = npix * L.nd;
+    const bool has_coarse = li + 1 < t.count;
+    const int nxc = has_coarse ? t.lev[li + 1].nx : 1, npixc = has_coarse ? nxc * t.lev[li + 1].ny : 1;
+    C* Jprev = nullptr;
+    C* Jcur = Ja;
+    for (int k = 1; k <= t.nu; ++k) {
+      for (int idx = threadIdx.x; idx < n_all; idx += blockDim.x) {
+        const int dn = idx / npix, i = idx - dn * npix;
+        const int x = i % L.nx, y = i / L.nx;
+        const Dir<C> dr = L.dir[dn];
+        const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
+        int xu = sxp ? x - 1 : x + 1, yu = syp ? y - 1 : y + 1;
+        const bool outx = xu < 0 || xu >= L.nx, outy = yu < 0 || yu >= L.ny;
+        const bool zx = outx && (sxp ? t.bc.xlo : t.bc.xhi) == BC_VACUUM;
+        const bool zy = outy && (syp ? t.bc.ylo : t.bc.yhi) == BC_VACUUM;
+        if (outx) xu = x;  // reflective: the adjacent interior node
+        if (outy) yu = y;
+        const int ix = y * L.nx + xu, iy = yu * L.nx + x;
+        C ux = C(0), uy = C(0);
+        if (k > 1) {
+          if (!zx) ux = Jprev[dn * npix + ix] + cf[ix] * srcp(dr.ax + dr.ay + L.sig[ix]);
+          if (!zy) uy = Jprev[dn * npix + iy] + cf[iy] * srcp(dr.ax + dr.ay + L.sig[iy]);
+        } else if (has_coarse) {
+          const C* cn = Dc + L.parent[dn] * npixc;
+          if (!zx) ux = cn[(y / L.fy) * nxc + xu / L.fx];
+          if (!zy) uy = cn[(yu / L.fy) * nxc + x / L.fx];
+        }
+        Jcur[idx] = (L.src[idx] + dr.ax * ux + dr.ay * uy) * srcp(dr.ax + dr.ay + L.sig[i]);
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < npix; i += blockDim.x) {
+        C sum = C(0);
+        for (int dn = 0; dn < L.nd; ++dn) sum += L.dir[dn].w * Jcur[dn * npix + i];
+        cf[i] = L.w[i] * sum;
+      }
+      __syncthreads();
+      Jprev = Jcur;
+      Jcur = Jcur == Ja ? Jb : Ja;
+    }
+    for (int idx = threadIdx.x; idx < n_all; idx += blockDim.x) {
+      const int dn = idx / npix, i = idx - dn * npix;
+      const Dir<C> dr = L.dir[dn];
+      const C d = Jprev[idx] + cf[i] * srcp(dr.ax + dr.ay + L.sig[i]);
+      if (li == 0)
+        t.out[idx] = d;
+      else
+        Dc[idx] = d;
+    }
+    __syncthreads();
+  }
 }
 
 dim3 node_grid(int nx, int ny, int nchunk) {
@@ -183,6 +251,19 @@ cudaError_t launch_scat_gain(const C* sig, const C* crat, const Dir<C>* dir, int
   return cudaGetLastError();
 }
 
+template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStream_t s) {
+  constexpr int TMAX = scat_tail_max<C>();
+  constexpr size_t smem = (3 * (size_t)TMAX + TMAX / 8) * sizeof(C);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_scat_tail<C, TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_scat_tail<C, TMAX><<<1, 1024, smem, s>>>(t);
+  return cudaGetLastError();
+}
+
 // node-tile chunking shared by the sweep launches and the workspace sizing
 int scat_chunks(int nx, int ny, int nd) {
   const int tiles = ((nx + SX - 1) / SX) * ((ny + SY - 1) / SY);
@@ -196,7 +277,8 @@ int scat_chunks(int nx, int ny, int nd) {
 #define INST_SC(C)                                                                                       \
   template cudaError_t launch_scat_sweep<C>(const ScatArgs<C>&, int, cudaStream_t);                      \
   template cudaError_t launch_scat_corr<C>(const C*, int, const C*, int, C*, cudaStream_t);              \
-  template cudaError_t launch_scat_gain<C>(const C*, const C*, const Dir<C>*, int, int, C*, cudaStream_t);
+  template cudaError_t launch_scat_gain<C>(const C*, const C*, const Dir<C>*, int, int, C*, cudaStream_t); \
+  template cudaError_t launch_scat_tail<C>(const ScatTail<C>&, cudaStream_t);
 INST_SC(double)
 INST_SC(float)
 template cudaError_t launch_scat_final<double, double>(const ScatFinal<double, double>&, int, cudaStream_t);
