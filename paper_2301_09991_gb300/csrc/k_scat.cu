@@ -41,10 +41,10 @@ struct NodeGeo {
   bool in;
   size_t i0, ixm, ixp, iym, iyp;
   bool oxm, oxp, oym, oyp;
-  __device__ NodeGeo(int nx, int ny) {
+  __device__ NodeGeo(int nx, int ny, int tile) {
     const int tiles_x = (nx + SX - 1) / SX;
-    x = (blockIdx.x % tiles_x) * SX + threadIdx.x;
-    y = (blockIdx.x / tiles_x) * SY + threadIdx.y;
+    x = (tile % tiles_x) * SX + threadIdx.x;
+    y = (tile / tiles_x) * SY + threadIdx.y;
     in = x < nx && y < ny;
     const int xi = min(x, nx - 1), yi = min(y, ny - 1);
     oxm = xi == 0;
@@ -59,10 +59,22 @@ struct NodeGeo {
   }
 };
 
-template <typename C> __global__ void __launch_bounds__(SX * SY) k_scat_sweep(const ScatArgs<C> a) {
-  const NodeGeo g(a.nx, a.ny);
+// IM: how the previous iterate is read (INIT_SAME: J + c / d of the last
+// sweep; INIT_UPSAMPLE: the coarser level's delta; INIT_ZERO: 0).  Both
+// neighbours in x and in y are loaded whatever the signs of mu and nu (the
+// extra ones hit L1), so no load address waits for the direction table and
+// the loads of several directions are in flight together.  Grid: tiles x
+// direction chunks.
+constexpr int kSweepBlocksPerSM = 5;
+template <typename C, int IM> __device__ __forceinline__ void sweep_item(const ScatArgs<C>& a, int tile, int chunk) {
+  const NodeGeo g(a.nx, a.ny, tile);
+  // distinct buffers (ping-pong): restrict lets the loads of the next
+  // directions move above this direction's store
+  const C* __restrict__ src = a.src;
+  const C* __restrict__ jin = a.jin;
+  const C* __restrict__ coarse = a.coarse;
+  C* __restrict__ jout = a.jout;
   const size_t npix = (size_t)a.nx * a.ny;
-  const int chunk = blockIdx.y;
   const int n_begin = chunk * a.dpc, n_end = min(n_begin + a.dpc, a.nd);
   // materials and the isotropic correction of the previous sweep at the
   // node and its neighbours (scalars: the upstream pair is chosen per
@@ -70,9 +82,9 @@ template <typename C> __global__ void __launch_bounds__(SX * SY) k_scat_sweep(co
   const C s0 = a.sig[g.i0];
   const C sxm = a.sig[g.ixm], sxq = a.sig[g.ixp], sym = a.sig[g.iym], syq = a.sig[g.iyp];
   C cxm = C(0), cxq = C(0), cym = C(0), cyq = C(0);
-  if (a.cin) cxm = a.cin[g.ixm], cxq = a.cin[g.ixp], cym = a.cin[g.iym], cyq = a.cin[g.iyp];
+  if (IM == INIT_SAME && a.cin) cxm = a.cin[g.ixm], cxq = a.cin[g.ixp], cym = a.cin[g.iym], cyq = a.cin[g.iyp];
   size_t oxm = 0, oxq = 0, oym = 0, oyq = 0;  // UpSamp parents of the neighbours
-  if (a.init_mode == INIT_UPSAMPLE) {
+  if (IM == INIT_UPSAMPLE) {
     auto parent_of = [&](size_t i) {
       const int px = (int)(i % a.nx), py = (int)(i / a.nx);
       return (size_t)(py / a.fy) * a.nxc + px / a.fx;
@@ -80,30 +92,40 @@ template <typename C> __global__ void __launch_bounds__(SX * SY) k_scat_sweep(co
     oxm = parent_of(g.ixm), oxq = parent_of(g.ixp), oym = parent_of(g.iym), oyq = parent_of(g.iyp);
   }
   const size_t npixc = (size_t)a.nxc * a.nyc;
+  // vacuum incoming sides of this node: the upstream value is 0 there
+  const bool zxm = g.oxm && a.bc.xlo == BC_VACUUM, zxp = g.oxp && a.bc.xhi == BC_VACUUM;
+  const bool zym = g.oym && a.bc.ylo == BC_VACUUM, zyp = g.oyp && a.bc.yhi == BC_VACUUM;
   C acc = C(0);
 #pragma unroll 4
   for (int n = n_begin; n < n_end; ++n) {
+    C vxm = C(0), vxp = C(0), vym = C(0), vyp = C(0);
+    if (IM == INIT_SAME) {
+      const C* jn = jin + (size_t)n * npix;
+      vxm = jn[g.ixm], vxp = jn[g.ixp], vym = jn[g.iym], vyp = jn[g.iyp];
+    } else if (IM == INIT_UPSAMPLE) {
+      const C* cn = coarse + (size_t)a.parent[n] * npixc;
+      vxm = cn[oxm], vxp = cn[oxq], vym = cn[oym], vyp = cn[oyq];
+    }
+    const C sv = src[(size_t)n * a.src_stride + g.i0];
     const Dir<C> dr = a.dir[n];
     const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
-    const bool out_x = sxp ? g.oxm : g.oxp, out_y = syp ? g.oym : g.oyp;
-    const bool zx = out_x && (sxp ? a.bc.xlo : a.bc.xhi) == BC_VACUUM;
-    const bool zy = out_y && (syp ? a.bc.ylo : a.bc.yhi) == BC_VACUUM;
-    const size_t ix = sxp ? g.ixm : g.ixp, iy = syp ? g.iym : g.iyp;  // upstream neighbours
-    C ux = C(0), uy = C(0);
-    if (a.init_mode == INIT_SAME) {
-      const C* jn = a.jin + (size_t)n * npix;
-      if (!zx) ux = jn[ix] + (sxp ? cxm : cxq) * srcp(dr.ax + dr.ay + (sxp ? sxm : sxq));
-      if (!zy) uy = jn[iy] + (syp ? cym : cyq) * srcp(dr.ax + dr.ay + (syp ? sym : syq));
-    } else if (a.init_mode == INIT_UPSAMPLE) {
-      const C* cn = a.coarse + (size_t)a.parent[n] * npixc;
-      if (!zx) ux = cn[sxp ? oxm : oxq];
-      if (!zy) uy = cn[syp ? oym : oyq];
+    C ux = sxp ? vxm : vxp, uy = syp ? vym : vyp;
+    if (IM == INIT_SAME) {
+      ux += (sxp ? cxm : cxq) * srcp(dr.ax + dr.ay + (sxp ? sxm : sxq));
+      uy += (syp ? cym : cyq) * srcp(dr.ax + dr.ay + (syp ? sym : syq));
     }
-    const C J = (a.src[(size_t)n * a.src_stride + g.i0] + dr.ax * ux + dr.ay * uy) * srcp(dr.ax + dr.ay + s0);
-    if (g.in) a.jout[(size_t)n * npix + g.i0] = J;
+    if (sxp ? zxm : zxp) ux = C(0);
+    if (syp ? zym : zyp) uy = C(0);
+    const C J = (sv + dr.ax * ux + dr.ay * uy) * srcp(dr.ax + dr.ay + s0);
+    if (g.in) jout[(size_t)n * npix + g.i0] = J;
     acc += dr.w * J;
   }
   if (g.in) a.part[(size_t)chunk * npix + g.i0] = acc;
+}
+
+template <typename C, int IM>
+__global__ void __launch_bounds__(SX * SY, kSweepBlocksPerSM) k_scat_sweep(const ScatArgs<C> a) {
+  sweep_item<C, IM>(a, blockIdx.x, blockIdx.y);
 }
 
 template <typename C>
@@ -117,7 +139,7 @@ __global__ void k_scat_corr(const C* __restrict__ part, int nchunk, const C* __r
 }
 
 template <typename T, typename C, bool UPDATE> __global__ void __launch_bounds__(SX * SY) k_scat_final(const ScatFinal<T, C> f) {
-  const NodeGeo g(f.nx, f.ny);
+  const NodeGeo g(f.nx, f.ny, blockIdx.x);
   if (!g.in) return;
   const size_t npix = (size_t)f.nx * f.ny;
   const int chunk = blockIdx.y;
@@ -227,7 +249,13 @@ dim3 node_grid(int nx, int ny, int nchunk) {
 }  // namespace
 
 template <typename C> cudaError_t launch_scat_sweep(const ScatArgs<C>& a, int nchunk, cudaStream_t s) {
-  k_scat_sweep<C><<<node_grid(a.nx, a.ny, nchunk), dim3(SX, SY), 0, s>>>(a);
+  const dim3 grid = node_grid(a.nx, a.ny, nchunk), block(SX, SY);
+  if (a.init_mode == INIT_SAME)
+    k_scat_sweep<C, INIT_SAME><<<grid, block, 0, s>>>(a);
+  else if (a.init_mode == INIT_UPSAMPLE)
+    k_scat_sweep<C, INIT_UPSAMPLE><<<grid, block, 0, s>>>(a);
+  else
+    k_scat_sweep<C, INIT_ZERO><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -267,7 +295,7 @@ template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStr
 // node-tile chunking shared by the sweep launches and the workspace sizing
 int scat_chunks(int nx, int ny, int nd) {
   const int tiles = ((nx + SX - 1) / SX) * ((ny + SY - 1) / SY);
-  const int want = (2432 + tiles - 1) / tiles;  // about two waves of 8 blocks on 152 SMs
+  const int want = (2432 + tiles - 1) / tiles;  // about 16 blocks per SM over the launch
   int c = want < 1 ? 1 : (want > 64 ? 64 : want);
   if (c > nd) c = nd;
   const int dpc = (nd + c - 1) / c;
