@@ -355,7 +355,7 @@ template <typename T, typename C> struct Impl {
   static cudaError_t scat_level(btmg_problem* P, int l, int g, const C* src, int init_mode, const C* init,
                                 int sweeps, const T* psi_in, T* psi_out, C* phi_part, int cls, cudaStream_t s) {
     const LevelH& A = P->lev[l];
-    const int nch = scat_chunks(A.nx, A.ny, A.nd);
+    const int nch = scat_chunks(A.nx, A.ny, A.nd, (int)P->csize);
     const int dpc = (A.nd + nch - 1) / nch;
     C* X = dptr<C>(P->d_delta[l]);  // the last sweep writes here
     C* Y = dptr<C>(P->d_scat_j);
@@ -1321,7 +1321,7 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
       if (ge != cudaSuccess) return bail(fail(BTMG_ERR_CUDA, cudaGetErrorString(ge)));
       max_n = std::max(max_n, A.n());
       max_pix = std::max(max_pix, A.npix());
-      max_part = std::max(max_part, (size_t)scat_chunks(A.nx, A.ny, A.nd) * A.npix());
+      max_part = std::max(max_part, (size_t)scat_chunks(A.nx, A.ny, A.nd, (int)P->csize) * A.npix());
       if (l == 0 && cudaMalloc(&P->d_delta[0], A.n() * P->csize) != cudaSuccess)
         return bail(fail(BTMG_ERR_OOM, "workspace delta"));
     }

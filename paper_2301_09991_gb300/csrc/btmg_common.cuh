@@ -153,7 +153,10 @@ cudaError_t launch_scat_corr(const C* part, int nchunk, const C* w, int npix, C*
 template <typename T, typename C> cudaError_t launch_scat_final(const ScatFinal<T, C>& f, int nchunk, cudaStream_t s);
 template <typename C>
 cudaError_t launch_scat_gain(const C* sig, const C* crat, const Dir<C>* dir, int nd, int npix, C* w, cudaStream_t s);
-int scat_chunks(int nx, int ny, int nd);  // direction chunks of a sweep on a level
+// direction chunks of the sweeps on a level (csize: bytes of the compute
+// type); scat_vec: whether its sweeps from J take four nodes per thread
+int scat_chunks(int nx, int ny, int nd, int csize);
+bool scat_vec(int nx, int csize);
 // The coarsest levels, each of at most scat_tail_max<C>() unknowns, run in
 // one single-CTA launch (k_scat_tail); lev[0] is the finest of them.
 constexpr int kScatTailLevels = 16;

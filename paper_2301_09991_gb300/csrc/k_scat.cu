@@ -128,6 +128,82 @@ __global__ void __launch_bounds__(SX * SY, kSweepBlocksPerSM) k_scat_sweep(const
   sweep_item<C, IM>(a, blockIdx.x, blockIdx.y);
 }
 
+// FP32 sweeps from J + c / d (sweeps 2..nu) with four consecutive nodes per
+// thread (128 x 8 node tiles): 128-bit loads of the node's row, of the rows
+// above and below and of the source, the x-upstream values from the
+// neighbouring lanes (warp-edge lanes load theirs), so a thread has four
+// times the bytes in flight of the one-node sweep.  Needs nx % 4 == 0.
+constexpr int VX = 4 * SX;
+__global__ void __launch_bounds__(SX * SY, 3) k_scat_sweep_v4(const ScatArgs<float> a) {
+  const int tiles_x = (a.nx + VX - 1) / VX;
+  const int nx = a.nx, ny = a.ny;
+  const int tx = threadIdx.x;
+  int x0 = (blockIdx.x % tiles_x) * VX + 4 * tx;
+  int y = (blockIdx.x / tiles_x) * SY + threadIdx.y;
+  const bool in = x0 < nx && y < ny;
+  x0 = min(x0, nx - 4);  // inactive lanes read in-domain values and store nothing
+  y = min(y, ny - 1);
+  const size_t npix = (size_t)nx * ny;
+  const size_t r0 = (size_t)y * nx + x0;
+  const size_t rm = y > 0 ? r0 - nx : r0, rp = y < ny - 1 ? r0 + nx : r0;
+  const size_t il = x0 > 0 ? r0 - 1 : r0, ir = x0 + 4 < nx ? r0 + 4 : r0 + 3;
+  const bool zl = x0 == 0 && a.bc.xlo == BC_VACUUM, zr = x0 + 4 >= nx && a.bc.xhi == BC_VACUUM;
+  const bool zym = y == 0 && a.bc.ylo == BC_VACUUM, zyp = y == ny - 1 && a.bc.yhi == BC_VACUUM;
+  auto ld4g = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
+  const float4 sg = ld4g(a.sig + r0), sgm = ld4g(a.sig + rm), sgp = ld4g(a.sig + rp);
+  const float sgl = a.sig[il], sgr = a.sig[ir];
+  float4 cc = make_float4(0.f, 0.f, 0.f, 0.f), ccm = cc, ccp = cc;
+  float ccl = 0.f, ccr = 0.f;
+  if (a.cin) cc = ld4g(a.cin + r0), ccm = ld4g(a.cin + rm), ccp = ld4g(a.cin + rp), ccl = a.cin[il], ccr = a.cin[ir];
+  const float* __restrict__ src = a.src;
+  const float* __restrict__ jin = a.jin;
+  float* __restrict__ jout = a.jout;
+  const int chunk = blockIdx.y;
+  const int n_begin = chunk * a.dpc, n_end = min(n_begin + a.dpc, a.nd);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+  for (int n = n_begin; n < n_end; ++n) {
+    const float* jn = jin + (size_t)n * npix;
+    const float4 v = ld4g(jn + r0), vm = ld4g(jn + rm), vp = ld4g(jn + rp);
+    const float4 sv = ld4g(src + (size_t)n * a.src_stride + r0);
+    float left = __shfl_up_sync(0xffffffffu, v.w, 1), right = __shfl_down_sync(0xffffffffu, v.x, 1);
+    if (tx == 0 || x0 == 0) left = jn[il];   // warp edge, or the node itself at the boundary
+    if (tx == SX - 1 || x0 + 4 >= nx) right = jn[ir];
+    const Dir<float> dr = a.dir[n];
+    const bool sxp = dr.mu > 0.f, syp = dr.nu > 0.f;
+    const float dd = dr.ax + dr.ay;
+    const float vv[4] = {v.x, v.y, v.z, v.w}, sgv[4] = {sg.x, sg.y, sg.z, sg.w}, ssv[4] = {sv.x, sv.y, sv.z, sv.w};
+    const float yv[4] = {syp ? vm.x : vp.x, syp ? vm.y : vp.y, syp ? vm.z : vp.z, syp ? vm.w : vp.w};
+    const float yc[4] = {syp ? ccm.x : ccp.x, syp ? ccm.y : ccp.y, syp ? ccm.z : ccp.z, syp ? ccm.w : ccp.w};
+    const float ys[4] = {syp ? sgm.x : sgp.x, syp ? sgm.y : sgp.y, syp ? sgm.z : sgp.z, syp ? sgm.w : sgp.w};
+    const float cv[4] = {cc.x, cc.y, cc.z, cc.w};
+    const bool zy = syp ? zym : zyp;
+    float J[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // x-upstream node: k - 1 (mu > 0) or k + 1, the lane neighbours at the ends
+      float ux, cx, sx;
+      if (sxp) {
+        ux = k == 0 ? left : vv[k - 1];
+        cx = k == 0 ? ccl : cv[k - 1];
+        sx = k == 0 ? sgl : sgv[k - 1];
+      } else {
+        ux = k == 3 ? right : vv[k + 1];
+        cx = k == 3 ? ccr : cv[k + 1];
+        sx = k == 3 ? sgr : sgv[k + 1];
+      }
+      ux += cx * srcp(dd + sx);
+      if (sxp ? (k == 0 && zl) : (k == 3 && zr)) ux = 0.f;
+      float uy = yv[k] + yc[k] * srcp(dd + ys[k]);
+      if (zy) uy = 0.f;
+      J[k] = (ssv[k] + dr.ax * ux + dr.ay * uy) * srcp(dd + sgv[k]);
+      acc[k] += dr.w * J[k];
+    }
+    if (in) *reinterpret_cast<float4*>(jout + (size_t)n * npix + r0) = make_float4(J[0], J[1], J[2], J[3]);
+  }
+  if (in) *reinterpret_cast<float4*>(a.part + (size_t)chunk * npix + r0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+
 template <typename C>
 __global__ void k_scat_corr(const C* __restrict__ part, int nchunk, const C* __restrict__ w, int npix,
                             C* __restrict__ c) {
@@ -250,6 +326,13 @@ dim3 node_grid(int nx, int ny, int nchunk) {
 
 template <typename C> cudaError_t launch_scat_sweep(const ScatArgs<C>& a, int nchunk, cudaStream_t s) {
   const dim3 grid = node_grid(a.nx, a.ny, nchunk), block(SX, SY);
+  if constexpr (sizeof(C) == 4) {
+    if (a.init_mode == INIT_SAME && scat_vec(a.nx, 4)) {
+      const dim3 g4(((a.nx + VX - 1) / VX) * ((a.ny + SY - 1) / SY), nchunk);
+      k_scat_sweep_v4<<<g4, block, 0, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   if (a.init_mode == INIT_SAME)
     k_scat_sweep<C, INIT_SAME><<<grid, block, 0, s>>>(a);
   else if (a.init_mode == INIT_UPSAMPLE)
@@ -293,8 +376,11 @@ template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStr
 }
 
 // node-tile chunking shared by the sweep launches and the workspace sizing
-int scat_chunks(int nx, int ny, int nd) {
-  const int tiles = ((nx + SX - 1) / SX) * ((ny + SY - 1) / SY);
+bool scat_vec(int nx, int csize) { return csize == 4 && nx % 4 == 0; }
+
+int scat_chunks(int nx, int ny, int nd, int csize) {
+  const int tw = scat_vec(nx, csize) ? VX : SX;  // node tile width of the sweeps from J
+  const int tiles = ((nx + tw - 1) / tw) * ((ny + SY - 1) / SY);
   const int want = (2432 + tiles - 1) / tiles;  // about 16 blocks per SM over the launch
   int c = want < 1 ? 1 : (want > 64 ? 64 : want);
   if (c > nd) c = nd;
