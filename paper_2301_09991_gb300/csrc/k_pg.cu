@@ -91,6 +91,21 @@ template <typename C> __device__ __forceinline__ void ld8(const C* p, C (&o)[8])
 }
 
 template <typename C> __device__ __forceinline__ C cmin(C a, C b) { return a < b ? a : b; }
+
+// Item it of a pass over `rows` row blocks of 8 + E quads: the quads 0..7 of
+// a row block first (eight consecutive items = the eight threads of one
+// 128-bit access phase read one 32-element row segment, no bank
+// conflicts), then the E remaining quads of every row block.
+template <int E> __device__ __forceinline__ void split_item(int it, int rows, int& rb, int& q) {
+  if (it < rows * 8) {
+    rb = it >> 3;
+    q = it & 7;
+  } else {
+    const int e = it - rows * 8;
+    rb = e / E;
+    q = 8 + e % E;
+  }
+}
 // FP32: the fast division intrinsic (2 ulp; the PG coefficients and the
 // Jacobi step tolerate it); FP64: exact division.
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
@@ -256,7 +271,9 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
 #pragma unroll
         for (int it = tid; it < NA + NB; it += NT) {
           if (it < NA) {
-            const int r = it / (W4 / 4), c = (it % (W4 / 4)) * 4;
+            int r, q;
+            split_item<W4 / 4 - 8>(it, H6, r, q);
+            const int c = q * 4;
             // inputs at (r-6, c-6 .. c+1) = tile columns c+2 .. c+9: three
             // aligned quads starting at tile column c (P - 2 is the tile base)
             C q0[4], q1[4], q2[4], o[4];
@@ -295,7 +312,9 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
 #pragma unroll
         for (int it = tid; it < NX + NY; it += NT) {
           if (it < NX) {
-            const int r = (it / (W4 / 4)) * 2, c = (it % (W4 / 4)) * 4;
+            int rb, q;
+            split_item<W4 / 4 - 8>(it, H4 / 2, rb, q);
+            const int r = rb * 2, c = q * 4;
             C p[6][4];
 #pragma unroll
             for (int v = 0; v < 6; ++v) ld4(A + (r + v) * W4 + c, p[v]);
@@ -344,11 +363,15 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
       // ---- stage 3: T = m1_y Psi (4-row blocks), then k on the 2-halo -------
       {
         constexpr int NT3 = (H2 / 4) * (W4 / 4);  // per array
+        constexpr int NT3P = (NT3 + 7) / 8 * 8;    // the second array starts on a phase
 #pragma unroll
-        for (int it = tid; it < 2 * NT3; it += NT) {
-          const bool isx = it < NT3;
-          const int j = isx ? it : it - NT3;
-          const int r = (j / (W4 / 4)) * 4, c = (j % (W4 / 4)) * 4;
+        for (int it = tid; it < 2 * NT3P; it += NT) {
+          const bool isx = it < NT3P;
+          const int j = isx ? it : it - NT3P;
+          if (j >= NT3) continue;
+          int rb, q;
+          split_item<W4 / 4 - 8>(j, H2 / 4, rb, q);
+          const int r = rb * 4, c = q * 4;
           const C* src = isx ? Px : Py;
           C* dst = isx ? Tx : Ty;
           C p[8][4];
@@ -376,7 +399,9 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
         constexpr int NK = H2 * (W2 / 4);
 #pragma unroll
         for (int it = tid; it < NK; it += NT) {
-          const int r = it / (W2 / 4), c = (it % (W2 / 4)) * 4;
+          int r, q;
+          split_item<W2 / 4 - 8>(it, H2, r, q);
+          const int c = q * 4;
           C tx[8], ty[8];
           ld8(Tx + r * W4 + c, tx);
           ld8(Ty + r * W4 + c, ty);
@@ -419,13 +444,13 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
       // ---- stage 4: y passes of the k-Diff terms (2-row blocks) -------------
       //   x group: u1 = m1_y (k_x P), u2 = m1_y k_x, w1 = m1_y P
       //   y group: v1 = s1_y (k_y P), v2 = s1_y k_y, v3 = s1_y P
+      // Items (group, row pair, quad): the eight quads 0..7 of a row pair go
+      // to the eight threads of one 128-bit access phase, which then read
+      // one 32-element row segment (no bank conflicts); the ninth quad
+      // (columns 32..35) of every row pair is a second pass of one warp.
       {
-        constexpr int N4 = (TY / 2) * (W2 / 4);  // per group
-#pragma unroll
-        for (int it = tid; it < 2 * N4; it += NT) {
-          const bool xg = it < N4;
-          const int j = xg ? it : it - N4;
-          const int r = (j / (W2 / 4)) * 2, c = (j % (W2 / 4)) * 4;
+        static_assert(W2 == 36 && TY == 32 && NT == 256, "stage-4 item mapping");
+        auto s4item = [&](const bool xg, const int r, const int c) {
           const C* K = xg ? Kx : Ky;
           // the 6 input rows stream through: row v adds to output row 0 with
           // tap v and to output row 1 with tap v - 1 (same sums, same order)
@@ -464,7 +489,9 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
             st4(d1 + (r + q) * W2 + c, o[q][1]);
             st4(d2 + (r + q) * W2 + c, o[q][2]);
           }
-        }
+        };
+        s4item(tid < 128, ((tid & 127) >> 3) * 2, (tid & 7) * 4);
+        if (tid < 32) s4item(tid < 16, (tid & 15) * 2, 32);
       }
       __syncthreads();
     }  // PGON
