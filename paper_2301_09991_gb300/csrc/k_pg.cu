@@ -118,7 +118,8 @@ __device__ __forceinline__ double cabs_(double v) { return fabs(v); }
 //   P   two H6 x PS tiles (double buffer), origin (-6,-8): psi   stages 0-5
 //       (the pointer P used below is offset by 2: P[r * PS + c] is (r-6, c-6))
 //   A   H6 x W4, origin (-6,-4): d1_x P                   stages 1-2
-//   B   H4 x W6, origin (-4,-6): d1_y P                   stages 1-2
+//   B   H4 x PS, origin (-4,-8): d1_y P (the staged tile's 16-byte aligned
+//       column quads; columns -8, -7, 38, 39 are never read)  stages 1-2
 //   Px, Py  H4 x W4, origin (-4,-4)                       stages 2-5
 //   Kx, Ky  H2 x W2, origin (-2,-2)                       stages 3-5
 //   Tx, Ty  H2 x W4, origin (-2,-4): m1_y Psi  (in the dead A/B region)  stage 3
@@ -129,7 +130,7 @@ constexpr int PBUF = H6 * PS;          // one staged tile: rows -6.., cols -8..
 constexpr int OFF_P = 0;               // two tiles (double buffer)
 constexpr int OFF_A = OFF_P + 2 * PBUF;
 constexpr int OFF_B = OFF_A + H6 * W4;
-constexpr int OFF_PX = OFF_B + H4 * W6;
+constexpr int OFF_PX = OFF_B + H4 * PS;
 constexpr int OFF_PY = OFF_PX + H4 * W4;
 constexpr int OFF_KX = OFF_PY + H4 * W4;
 constexpr int OFF_KY = OFF_KX + H2 * W2;
@@ -244,8 +245,8 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
       }
     } else {
 #pragma unroll 2
-      for (int i = tid; i < H6 * W6; i += NT) {
-        const int gx = x0 + (i % W6) - 6, gy = y0 + (i / W6) - 6;
+      for (int i = tid; i < H6 * PS; i += NT) {  // the box's 48 columns, like the TMA copy
+        const int gx = x0 + (i % PS) - 8, gy = y0 + (i / PS) - 6;
         C v;
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny)
           v = Conv<T>::ld(psin + (size_t)gy * nx + gx);
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
           v = C(0);
         else
           v = Conv<T>::ld(psin + (size_t)clampi(gy, 0, ny - 1) * nx + clampi(gx, 0, nx - 1));
-        P[(i / W6) * PS + i % W6] = v;
+        P[i - 2] = v;  // P - 2 is the tile base
       }
       __syncthreads();
     }
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
       // ---- stage 1: derivative passes in difference form --------------------
       // A = d1_x P: items (row, quad); B = d1_y P: items (row pair, quad)
       {
-        constexpr int NA = H6 * (W4 / 4), NB = (H4 / 2) * (W6 / 4);
+        constexpr int NA = H6 * (W4 / 4), NB = (H4 / 2) * (PS / 4);
 #pragma unroll
         for (int it = tid; it < NA + NB; it += NT) {
           if (it < NA) {
@@ -289,19 +290,20 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
               st4(Pk + (r - 4) * W2 + (c - 4), pk);
             }
           } else {
-            const int j = it - NA;
-            const int r = (j / (W6 / 4)) * 2, c = (j % (W6 / 4)) * 4;
+            int rb, q;
+            split_item<PS / 4 - 8>(it - NA, H4 / 2, rb, q);
+            const int r = rb * 2, c = q * 4;  // B column c = tile column c - 8
             C p[6][4];
 #pragma unroll
-            for (int v = 0; v < 6; ++v) ld2x2(P + (r + v) * PS + c, p[v]);
+            for (int v = 0; v < 6; ++v) ld4(P - 2 + (r + v) * PS + c, p[v]);
             C o0[4], o1[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               o0[k] = D1<C, ORD>(p[0][k], p[1][k], p[3][k], p[4][k]);
               o1[k] = D1<C, ORD>(p[1][k], p[2][k], p[4][k], p[5][k]);
             }
-            st4(B + r * W6 + c, o0);
-            st4(B + (r + 1) * W6 + c, o1);
+            st4(B + r * PS + c, o0);
+            st4(B + (r + 1) * PS + c, o1);
           }
         }
       }
@@ -333,10 +335,16 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
             st4(Px + r * W4 + c, o0);
             st4(Px + (r + 1) * W4 + c, o1);
           } else {
-            const int j = it - NX;
-            const int r = j / (W4 / 4), c = (j % (W4 / 4)) * 4;
-            C p[8], o[4];
-            ld8(B + r * W6 + c, p);
+            int r, q;
+            split_item<W4 / 4 - 8>(it - NX, H4, r, q);
+            const int c = q * 4;
+            // inputs at tile columns c - 6 .. c + 1 = B columns c + 2 .. c + 9:
+            // three aligned quads starting at B column c
+            C b0[4], b1[4], b2[4], o[4];
+            ld4(B + r * PS + c, b0);
+            ld4(B + r * PS + c + 4, b1);
+            ld4(B + r * PS + c + 8, b2);
+            const C p[8] = {b0[2], b0[3], b1[0], b1[1], b1[2], b1[3], b2[0], b2[1]};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               C s = C(0);
