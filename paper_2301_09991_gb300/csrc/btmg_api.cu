@@ -136,7 +136,8 @@ struct btmg_problem {
   void* d_scat_j = nullptr;     // [nd][ny][nx]
   void* d_scat_part = nullptr;  // [chunks][ny][nx]
   void* d_scat_c = nullptr;     // [ny][nx]
-  int scat_tail = 0;            // first level of the single-CTA tail (L: none)
+  int scat_tail = 0;            // first level of the smoother's single-CTA tail (L: none)
+  int plain_tail = 0;           // first level of the published cycle's single-CTA tail
   bool scat_off = false;        // solve-time fallback to the plain sweeps
   int32_t scat_fallbacks = 0;   // solves that fell back
   void* d_sigs = nullptr;      // [G][G][npix]
@@ -447,8 +448,19 @@ template <typename T, typename C> struct Impl {
     cudaError_t e;
     const int L = P->L;
     const LevelH& L0 = P->lev[0];
-    // 2. restriction to every coarser level
-    for (int l = 0; l + 1 < L; ++l) {
+    // the smallest levels run in one single-CTA launch (restrictions and
+    // sweeps): the smoother's levels while it is active, else the
+    // published cycle's when the smoother is off
+    int tail = L;
+    bool tail_scat = false;
+    if (P->scat_tail < L && !P->scat_off) {
+      tail = P->scat_tail;
+      tail_scat = true;
+    } else if (P->d.scat_levels == 0 || P->scat_off) {
+      tail = P->plain_tail;
+    }
+    // 2. restriction to every coarser level (those of the tail inside it)
+    for (int l = 0; l + 1 < L && l < tail; ++l) {
       const LevelH &A = P->lev[l], &B = P->lev[l + 1];
       if ((e = timed(P, PC_RESTRICT, s, [&] {
              return launch_restrict<C>(dptr<C>(P->d_s[l]), dptr<C>(P->d_s[l + 1]), dptr<C>(P->d_rcoef[l]), A.nx,
@@ -456,32 +468,37 @@ template <typename T, typename C> struct Impl {
            })) != cudaSuccess)
         return e;
     }
-    // 3./4. upwind Jacobi from the coarsest level up, UpSamp in between (the
-    // smallest levels of the scattering smoother in one launch)
+    // 3./4. upwind Jacobi from the coarsest level up, UpSamp in between
     int top = L - 1;
-    if (P->scat_tail < L && !P->scat_off) {
+    if (tail < L) {
       ScatTail<C> t{};
-      t.count = L - P->scat_tail;
+      t.count = L - tail;
       t.nu = P->d.nu_jacobi;
+      t.scat = tail_scat ? 1 : 0;
       t.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
-      t.out = dptr<C>(P->d_delta[P->scat_tail]);
+      t.out = dptr<C>(P->d_delta[tail]);
       for (int k = 0; k < t.count; ++k) {
-        const int l = P->scat_tail + k;
+        const int l = tail + k;
         const LevelH& A = P->lev[l];
         ScatTailLevel<C>& v = t.lev[k];
-        v.src = dptr<C>(P->d_s[l]);
-        v.w = dptr<C>(P->d_scat_w[l]) + (size_t)g * A.npix();
+        v.s = dptr<C>(P->d_s[l]);
+        v.rcoef = l + 1 < L ? dptr<C>(P->d_rcoef[l]) : nullptr;
+        v.w = tail_scat ? dptr<C>(P->d_scat_w[l]) + (size_t)g * A.npix() : nullptr;
         v.sig = dptr<C>(P->d_sig[l]) + (size_t)g * A.npix();
         v.dir = reinterpret_cast<const Dir<C>*>(P->d_dir[l]);
         v.parent = l + 1 < L ? reinterpret_cast<const int*>(P->d_parent[l]) : nullptr;
         v.nx = A.nx;
         v.ny = A.ny;
+        v.nr = A.nr;
+        v.nc = A.nc;
         v.nd = A.nd;
         v.fx = A.fx;
         v.fy = A.fy;
+        v.fr = A.fr;
+        v.fc = A.fc;
       }
       if ((e = timed(P, PC_UP_COARSE, s, [&] { return launch_scat_tail<C>(t, s); })) != cudaSuccess) return e;
-      top = P->scat_tail - 1;
+      top = tail - 1;
     }
     for (int l = top; l >= 1; --l) {
       if (P->scat_on[l] && !P->scat_off) {
@@ -1199,6 +1216,13 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
     P->lev.push_back(B);
   }
   P->L = (int)P->lev.size();
+  {  // the coarsest levels that fit the single-CTA tail kernel (not level 0)
+    const size_t tmax = (size_t)(P->f64 ? scat_tail_max<double>() : scat_tail_max<float>());
+    P->plain_tail = P->L;
+    while (P->plain_tail - 1 >= 1 && P->L - (P->plain_tail - 1) <= kScatTailLevels &&
+           P->lev[P->plain_tail - 1].n() <= tmax)
+      --P->plain_tail;
+  }
   for (int r = 0; r < d->n_regions; ++r)
     for (int g = 0; g < G; ++g)
       for (int h = g + 1; h < G; ++h)

@@ -158,20 +158,24 @@ cudaError_t launch_scat_gain(const C* sig, const C* crat, const Dir<C>* dir, int
 int scat_chunks(int nx, int ny, int nd, int csize);
 bool scat_vec(int nx, int csize);
 // The coarsest levels, each of at most scat_tail_max<C>() unknowns, run in
-// one single-CTA launch (k_scat_tail); lev[0] is the finest of them.
+// one single-CTA launch (k_tail): the restrictions down these levels, then
+// their nu sweeps from the coarsest up, for the published cycle's upwind
+// Jacobi (scat = 0) or the scattering smoother (scat = 1); lev[0] is the
+// finest of them, its restricted residual an input.
 constexpr int kScatTailLevels = 16;
 template <typename C> constexpr int scat_tail_max() { return sizeof(C) == 8 ? 4096 : 8192; }
 template <typename C> struct ScatTailLevel {
-  const C* src;       // [nd][ny][nx] restricted residual of the level
-  const C* w;         // [ny][nx] gain
+  C* s;               // [nd][ny][nx] restricted residual (written here for lev[1..])
+  const C* rcoef;     // [nd] restriction weights to the next coarser level
+  const C* w;         // [ny][nx] smoother gain (scat = 1)
   const C* sig;       // [ny][nx]
   const Dir<C>* dir;  // [nd]
   const int* parent;  // coarser-level direction of each direction (not for the coarsest)
-  int nx, ny, nd, fx, fy;  // fx, fy: factors to the coarser level
+  int nx, ny, nr, nc, nd, fx, fy, fr, fc;  // factors to the coarser level
 };
 template <typename C> struct ScatTail {
   ScatTailLevel<C> lev[kScatTailLevels];
-  int count, nu;
+  int count, nu, scat;
   Bc bc;
   C* out;  // delta of lev[0], [nd][ny][nx]
 };

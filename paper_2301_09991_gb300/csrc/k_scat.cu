@@ -252,26 +252,62 @@ __global__ void k_scat_gain(const C* __restrict__ sig, const C* __restrict__ cra
   w[i] = (C)(kappa / (1.0 - kappa * S));
 }
 
-// The small coarsest levels in one CTA (they are launch-bound as separate
-// kernels): for each level from the coarsest up, nu sweeps and the final
-// pass with block barriers between the phases; the sweep iterates, the
-// isotropic field and the coarser level's correction live in shared memory.
-// Same arithmetic as the per-level kernels, the scalar flux of a sweep
-// summed over all directions at once.
-template <typename C, int TMAX> __global__ void __launch_bounds__(1024) k_scat_tail(const ScatTail<C> t) {
+// The small coarsest levels in one CTA (as separate kernels they are
+// launch-bound): the restrictions down these levels (the restriction of
+// Sec. 2.5 as k_restrict computes it), then for each level from the
+// coarsest up nu sweeps and the final pass with block barriers between the
+// phases; the sweep iterates, the isotropic field and the coarser level's
+// correction live in shared memory.  SCAT = false: the published upwind
+// Jacobi (delta = J of the last sweep); SCAT = true: the scattering
+// smoother, its scalar flux summed over all directions at once.
+template <typename C, int TMAX, bool SCAT> __global__ void __launch_bounds__(1024) k_tail(const ScatTail<C> t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* Ja = reinterpret_cast<C*>(smem_raw);
   C* Jb = Ja + TMAX;
   C* Dc = Jb + TMAX;  // the coarser level's delta, then this level's
   C* cf = Dc + TMAX;  // isotropic correction c of the last sweep, [ny][nx]
+  for (int li = 0; li + 1 < t.count; ++li) {
+    const ScatTailLevel<C> F = t.lev[li], Q = t.lev[li + 1];
+    const int total = Q.nd * Q.ny * Q.nx;
+#pragma unroll 4
+    for (int id = threadIdx.x; id < total; id += blockDim.x) {
+      const int X = id % Q.nx, Y = (id / Q.nx) % Q.ny, N = id / (Q.nx * Q.ny);
+      const int f = N / (Q.nr * Q.nc), J = (N % (Q.nr * Q.nc)) / Q.nc, I = N % Q.nc;
+      C acc = C(0);
+      for (int aa = 0; aa < F.fr; ++aa) {
+        const int j = J * F.fr + aa;
+        if (j >= F.nr) continue;
+        for (int bb = 0; bb < F.fc; ++bb) {
+          const int i = I * F.fc + bb;
+          if (i >= F.nc) continue;
+          const int n = f * F.nr * F.nc + j * F.nc + i;
+          const C w = F.rcoef[n];
+          for (int yy = 0; yy < F.fy; ++yy) {
+            const int y = Y * F.fy + yy;
+            if (y >= F.ny) continue;
+            for (int xx = 0; xx < F.fx; ++xx) {
+              const int x = X * F.fx + xx;
+              if (x >= F.nx) continue;
+              acc += w * F.s[(n * F.ny + y) * F.nx + x];
+            }
+          }
+        }
+      }
+      Q.s[id] = acc;
+    }
+    __syncthreads();
+  }
   for (int li = t.count - 1; li >= 0; --li) {
     const ScatTailLevel<C> L = t.lev[li];
+    const C* __restrict__ ls = L.s;
+    const C* __restrict__ lsig = L.sig;
     const int npix = L.nx * L.ny, n_all = npix * L.nd;
     const bool has_coarse = li + 1 < t.count;
     const int nxc = has_coarse ? t.lev[li + 1].nx : 1, npixc = has_coarse ? nxc * t.lev[li + 1].ny : 1;
     C* Jprev = nullptr;
     C* Jcur = Ja;
     for (int k = 1; k <= t.nu; ++k) {
+#pragma unroll 4
       for (int idx = threadIdx.x; idx < n_all; idx += blockDim.x) {
         const int dn = idx / npix, i = idx - dn * npix;
         const int x = i % L.nx, y = i / L.nx;
@@ -286,29 +322,39 @@ template <typename C, int TMAX> __global__ void __launch_bounds__(1024) k_scat_t
         const int ix = y * L.nx + xu, iy = yu * L.nx + x;
         C ux = C(0), uy = C(0);
         if (k > 1) {
-          if (!zx) ux = Jprev[dn * npix + ix] + cf[ix] * srcp(dr.ax + dr.ay + L.sig[ix]);
-          if (!zy) uy = Jprev[dn * npix + iy] + cf[iy] * srcp(dr.ax + dr.ay + L.sig[iy]);
+          if (!zx) ux = Jprev[dn * npix + ix];
+          if (!zy) uy = Jprev[dn * npix + iy];
+          if (SCAT) {
+            if (!zx) ux += cf[ix] * srcp(dr.ax + dr.ay + L.sig[ix]);
+            if (!zy) uy += cf[iy] * srcp(dr.ax + dr.ay + L.sig[iy]);
+          }
         } else if (has_coarse) {
           const C* cn = Dc + L.parent[dn] * npixc;
           if (!zx) ux = cn[(y / L.fy) * nxc + xu / L.fx];
           if (!zy) uy = cn[(yu / L.fy) * nxc + x / L.fx];
         }
-        Jcur[idx] = (L.src[idx] + dr.ax * ux + dr.ay * uy) * srcp(dr.ax + dr.ay + L.sig[i]);
+        Jcur[idx] = (ls[idx] + dr.ax * ux + dr.ay * uy) * srcp(dr.ax + dr.ay + lsig[i]);
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < npix; i += blockDim.x) {
-        C sum = C(0);
-        for (int dn = 0; dn < L.nd; ++dn) sum += L.dir[dn].w * Jcur[dn * npix + i];
-        cf[i] = L.w[i] * sum;
+      if (SCAT) {
+        for (int i = threadIdx.x; i < npix; i += blockDim.x) {
+          C sum = C(0);
+          for (int dn = 0; dn < L.nd; ++dn) sum += L.dir[dn].w * Jcur[dn * npix + i];
+          cf[i] = L.w[i] * sum;
+        }
+        __syncthreads();
       }
-      __syncthreads();
       Jprev = Jcur;
       Jcur = Jcur == Ja ? Jb : Ja;
     }
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < n_all; idx += blockDim.x) {
-      const int dn = idx / npix, i = idx - dn * npix;
-      const Dir<C> dr = L.dir[dn];
-      const C d = Jprev[idx] + cf[i] * srcp(dr.ax + dr.ay + L.sig[i]);
+      C d = Jprev[idx];
+      if (SCAT) {
+        const int dn = idx / npix, i = idx - dn * npix;
+        const Dir<C> dr = L.dir[dn];
+        d += cf[i] * srcp(dr.ax + dr.ay + L.sig[i]);
+      }
       if (li == 0)
         t.out[idx] = d;
       else
@@ -362,17 +408,20 @@ cudaError_t launch_scat_gain(const C* sig, const C* crat, const Dir<C>* dir, int
   return cudaGetLastError();
 }
 
-template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStream_t s) {
+template <typename C, bool SCAT> cudaError_t launch_tail_mode(const ScatTail<C>& t, cudaStream_t s) {
   constexpr int TMAX = scat_tail_max<C>();
   constexpr size_t smem = (3 * (size_t)TMAX + TMAX / 8) * sizeof(C);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_scat_tail<C, TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tail<C, TMAX, SCAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_scat_tail<C, TMAX><<<1, 1024, smem, s>>>(t);
+  k_tail<C, TMAX, SCAT><<<1, 1024, smem, s>>>(t);
   return cudaGetLastError();
+}
+template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStream_t s) {
+  return t.scat ? launch_tail_mode<C, true>(t, s) : launch_tail_mode<C, false>(t, s);
 }
 
 // node-tile chunking shared by the sweep launches and the workspace sizing
