@@ -269,7 +269,7 @@ def sweep_rooflines(btmg, torch, prob, pk, peak_src, cycles=10):
     bpu = 12 * (nu + 1)
     fine_s = prof["upwind_fine"][0] / cycles / 1000.0
     ach = n * bpu / fine_s / 1e9
-    out["scatter_fine"] = {"kernel": "finest-level scattering smoother (k_scat_sweep x 3, k_scat_corr x 2, "
+    out["scatter_fine"] = {"kernel": "finest-level scattering smoother (k_scat_sweep x 3, k_scat_corr x 3, "
                                      "k_scat_final)", "bytes_per_unknown_per_cycle": bpu,
                            "ms_per_cycle": round(fine_s * 1e3, 4), "achieved": ach, "frac": ach / peak,
                            "launches_per_cycle": prof["upwind_fine"][1] // cycles,

@@ -393,17 +393,14 @@ template <typename T, typename C> struct Impl {
       a.dpc = dpc;
       a.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
       if ((e = timed(P, cls, s, [&] { return launch_scat_sweep<C>(a, nch, s); })) != cudaSuccess) return e;
-      if (k < sweeps &&
-          (e = timed(P, cls, s, [&] { return launch_scat_corr<C>(part, nch, w, (int)A.npix(), cf, s); })) !=
-              cudaSuccess)
+      if ((e = timed(P, cls, s, [&] { return launch_scat_corr<C>(part, nch, w, (int)A.npix(), cf, s); })) !=
+          cudaSuccess)
         return e;
       prev = a.jout;
     }
     ScatFinal<T, C> f{};
     f.j = X;
-    f.part = part;
-    f.nchunk_in = nch;
-    f.w = w;
+    f.c = cf;
     f.sig = sig;
     f.dir = dir;
     f.nx = A.nx;

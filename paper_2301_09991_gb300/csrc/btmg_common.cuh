@@ -136,9 +136,7 @@ template <typename C> struct ScatArgs {
 };
 template <typename T, typename C> struct ScatFinal {
   const C* j;          // [nd][ny][nx] J of the last sweep (may alias delta_out)
-  const C* part;       // [nchunk_in][ny][nx] its partial sums
-  int nchunk_in;
-  const C* w;          // [ny][nx] gain kappa / (1 - kappa sum p / d)
+  const C* c;          // [ny][nx] isotropic correction of the last sweep
   const C* sig;
   const Dir<C>* dir;
   int nx, ny, nd, dpc; // output chunking (dpc directions per block row)

@@ -23,6 +23,8 @@
 // Layout: one thread per node of a 32 x 8 tile, looping over the directions
 // of its chunk; consecutive threads read consecutive x (coalesced), the
 // upstream row is mostly read by the same block (L1).
+#include <type_traits>
+
 #include "btmg_common.cuh"
 
 namespace btmg {
@@ -220,9 +222,7 @@ template <typename T, typename C, bool UPDATE> __global__ void __launch_bounds__
   const size_t npix = (size_t)f.nx * f.ny;
   const int chunk = blockIdx.y;
   const int n_begin = chunk * f.dpc, n_end = min(n_begin + f.dpc, f.nd);
-  C s = C(0);
-  for (int k = 0; k < f.nchunk_in; ++k) s += f.part[(size_t)k * npix + g.i0];
-  const C c0 = f.w[g.i0] * s, s0 = f.sig[g.i0];
+  const C c0 = f.c[g.i0], s0 = f.sig[g.i0];
   C acc = C(0);
 #pragma unroll 4
   for (int n = n_begin; n < n_end; ++n) {
@@ -238,6 +238,43 @@ template <typename T, typename C, bool UPDATE> __global__ void __launch_bounds__
     }
   }
   if (UPDATE) f.phi_part[(size_t)chunk * npix + g.i0] = acc;
+}
+
+// FP32 final pass with four consecutive nodes per thread (128-bit loads and
+// stores of J and psi).  Needs nx % 4 == 0.
+template <bool UPDATE> __global__ void __launch_bounds__(SX * SY) k_scat_final_v4(const ScatFinal<float, float> f) {
+  const int tiles_x = (f.nx + VX - 1) / VX;
+  const int x0 = (blockIdx.x % tiles_x) * VX + 4 * threadIdx.x;
+  const int y = (blockIdx.x / tiles_x) * SY + threadIdx.y;
+  if (x0 >= f.nx || y >= f.ny) return;
+  const size_t npix = (size_t)f.nx * f.ny, r0 = (size_t)y * f.nx + x0;
+  const int chunk = blockIdx.y;
+  const int n_begin = chunk * f.dpc, n_end = min(n_begin + f.dpc, f.nd);
+  const float4 c4 = *reinterpret_cast<const float4*>(f.c + r0);
+  const float4 s4 = *reinterpret_cast<const float4*>(f.sig + r0);
+  const float cv[4] = {c4.x, c4.y, c4.z, c4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+  for (int n = n_begin; n < n_end; ++n) {
+    const Dir<float> dr = f.dir[n];
+    const size_t gi = (size_t)n * npix + r0;
+    const float4 j4 = *reinterpret_cast<const float4*>(f.j + gi);
+    const float jv[4] = {j4.x, j4.y, j4.z, j4.w};
+    float d[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = jv[k] + cv[k] * srcp(dr.ax + dr.ay + sv[k]);
+    if (UPDATE) {
+      const float4 p4 = *reinterpret_cast<const float4*>(f.psi_in + gi);
+      const float pn[4] = {p4.x + d[0], p4.y + d[1], p4.z + d[2], p4.w + d[3]};
+      *reinterpret_cast<float4*>(f.psi_out + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] += dr.w * pn[k];
+    } else {
+      *reinterpret_cast<float4*>(f.delta_out + gi) = make_float4(d[0], d[1], d[2], d[3]);
+    }
+  }
+  if (UPDATE)
+    *reinterpret_cast<float4*>(f.phi_part + (size_t)chunk * npix + r0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
 template <typename C>
@@ -364,6 +401,9 @@ template <typename C, int TMAX, bool SCAT> __global__ void __launch_bounds__(102
   }
 }
 
+// 16-byte aligned (or absent) buffer: the four-node kernels use 128-bit accesses
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 dim3 node_grid(int nx, int ny, int nchunk) {
   return dim3(((nx + SX - 1) / SX) * ((ny + SY - 1) / SY), nchunk);
 }
@@ -373,7 +413,8 @@ dim3 node_grid(int nx, int ny, int nchunk) {
 template <typename C> cudaError_t launch_scat_sweep(const ScatArgs<C>& a, int nchunk, cudaStream_t s) {
   const dim3 grid = node_grid(a.nx, a.ny, nchunk), block(SX, SY);
   if constexpr (sizeof(C) == 4) {
-    if (a.init_mode == INIT_SAME && scat_vec(a.nx, 4)) {
+    if (a.init_mode == INIT_SAME && scat_vec(a.nx, 4) && al16(a.src) && al16(a.jin) && al16(a.jout) &&
+        al16(a.cin) && al16(a.part) && al16(a.sig)) {
       const dim3 g4(((a.nx + VX - 1) / VX) * ((a.ny + SY - 1) / SY), nchunk);
       k_scat_sweep_v4<<<g4, block, 0, s>>>(a);
       return cudaGetLastError();
@@ -395,6 +436,17 @@ cudaError_t launch_scat_corr(const C* part, int nchunk, const C* w, int npix, C*
 }
 
 template <typename T, typename C> cudaError_t launch_scat_final(const ScatFinal<T, C>& f, int nchunk, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<C, float>::value) {
+    if (scat_vec(f.nx, 4) && al16(f.j) && al16(f.c) && al16(f.sig) && al16(f.psi_in) && al16(f.psi_out) &&
+        al16(f.delta_out) && al16(f.phi_part)) {
+      const dim3 g4(((f.nx + VX - 1) / VX) * ((f.ny + SY - 1) / SY), nchunk);
+      if (f.psi_out)
+        k_scat_final_v4<true><<<g4, dim3(SX, SY), 0, s>>>(f);
+      else
+        k_scat_final_v4<false><<<g4, dim3(SX, SY), 0, s>>>(f);
+      return cudaGetLastError();
+    }
+  }
   if (f.psi_out)
     k_scat_final<T, C, true><<<node_grid(f.nx, f.ny, nchunk), dim3(SX, SY), 0, s>>>(f);
   else
