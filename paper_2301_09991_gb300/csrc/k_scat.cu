@@ -206,6 +206,67 @@ __global__ void __launch_bounds__(SX * SY, 3) k_scat_sweep_v4(const ScatArgs<flo
   if (in) *reinterpret_cast<float4*>(a.part + (size_t)chunk * npix + r0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
+// FP32 first sweep from the UpSamp of the coarser correction with four
+// consecutive nodes per thread: a node pair shares its coarse parent (the
+// level coarsens by 2 in x and y), so each of the three rows takes one
+// 64-bit load of the coarse plane.  Needs nx % 4 == 0 and fx = fy = 2.
+__global__ void __launch_bounds__(SX * SY, 3) k_scat_sweep_v4_up(const ScatArgs<float> a) {
+  const int tiles_x = (a.nx + VX - 1) / VX;
+  const int nx = a.nx, ny = a.ny;
+  const int tx = threadIdx.x;
+  int x0 = (blockIdx.x % tiles_x) * VX + 4 * tx;
+  int y = (blockIdx.x / tiles_x) * SY + threadIdx.y;
+  const bool in = x0 < nx && y < ny;
+  x0 = min(x0, nx - 4);
+  y = min(y, ny - 1);
+  const size_t npix = (size_t)nx * ny, npixc = (size_t)a.nxc * a.nyc;
+  const size_t r0 = (size_t)y * nx + x0;
+  const int xc = x0 / 2;  // even
+  const size_t c0 = (size_t)(y / 2) * a.nxc + xc;
+  const size_t cm = (size_t)((y > 0 ? y - 1 : y) / 2) * a.nxc + xc;
+  const size_t cp = (size_t)((y < ny - 1 ? y + 1 : y) / 2) * a.nxc + xc;
+  const size_t cl = x0 > 0 ? c0 - 1 : c0, cr = x0 + 4 < nx ? c0 + 2 : c0 + 1;
+  const bool zl = x0 == 0 && a.bc.xlo == BC_VACUUM, zr = x0 + 4 >= nx && a.bc.xhi == BC_VACUUM;
+  const bool zym = y == 0 && a.bc.ylo == BC_VACUUM, zyp = y == ny - 1 && a.bc.yhi == BC_VACUUM;
+  const float4 sg = *reinterpret_cast<const float4*>(a.sig + r0);
+  const float sgv[4] = {sg.x, sg.y, sg.z, sg.w};
+  const float* __restrict__ src = a.src;
+  const float* __restrict__ coarse = a.coarse;
+  float* __restrict__ jout = a.jout;
+  const int chunk = blockIdx.y;
+  const int n_begin = chunk * a.dpc, n_end = min(n_begin + a.dpc, a.nd);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+  for (int n = n_begin; n < n_end; ++n) {
+    const float* cn = coarse + (size_t)a.parent[n] * npixc;
+    const float2 v = *reinterpret_cast<const float2*>(cn + c0);
+    const float2 vm = *reinterpret_cast<const float2*>(cn + cm);
+    const float2 vp = *reinterpret_cast<const float2*>(cn + cp);
+    const float4 sv = *reinterpret_cast<const float4*>(src + (size_t)n * a.src_stride + r0);
+    float left = __shfl_up_sync(0xffffffffu, v.y, 1), right = __shfl_down_sync(0xffffffffu, v.x, 1);
+    if (tx == 0 || x0 == 0) left = cn[cl];  // warp edge, or the node itself at the boundary
+    if (tx == SX - 1 || x0 + 4 >= nx) right = cn[cr];
+    const Dir<float> dr = a.dir[n];
+    const bool sxp = dr.mu > 0.f, syp = dr.nu > 0.f;
+    const float dd = dr.ax + dr.ay;
+    const float vv[4] = {v.x, v.x, v.y, v.y}, ssv[4] = {sv.x, sv.y, sv.z, sv.w};
+    const float2 yr = syp ? vm : vp;
+    const float yv[4] = {yr.x, yr.x, yr.y, yr.y};
+    const bool zy = syp ? zym : zyp;
+    float J[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float ux = sxp ? (k == 0 ? left : vv[k - 1]) : (k == 3 ? right : vv[k + 1]);
+      if (sxp ? (k == 0 && zl) : (k == 3 && zr)) ux = 0.f;
+      const float uy = zy ? 0.f : yv[k];
+      J[k] = (ssv[k] + dr.ax * ux + dr.ay * uy) * srcp(dd + sgv[k]);
+      acc[k] += dr.w * J[k];
+    }
+    if (in) *reinterpret_cast<float4*>(jout + (size_t)n * npix + r0) = make_float4(J[0], J[1], J[2], J[3]);
+  }
+  if (in) *reinterpret_cast<float4*>(a.part + (size_t)chunk * npix + r0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+
 template <typename C>
 __global__ void k_scat_corr(const C* __restrict__ part, int nchunk, const C* __restrict__ w, int npix,
                             C* __restrict__ c) {
@@ -417,6 +478,12 @@ template <typename C> cudaError_t launch_scat_sweep(const ScatArgs<C>& a, int nc
         al16(a.cin) && al16(a.part) && al16(a.sig)) {
       const dim3 g4(((a.nx + VX - 1) / VX) * ((a.ny + SY - 1) / SY), nchunk);
       k_scat_sweep_v4<<<g4, block, 0, s>>>(a);
+      return cudaGetLastError();
+    }
+    if (a.init_mode == INIT_UPSAMPLE && scat_vec(a.nx, 4) && a.fx == 2 && a.fy == 2 && al16(a.src) &&
+        al16(a.jout) && al16(a.part) && al16(a.sig) && ((uintptr_t)a.coarse & 7u) == 0) {
+      const dim3 g4(((a.nx + VX - 1) / VX) * ((a.ny + SY - 1) / SY), nchunk);
+      k_scat_sweep_v4_up<<<g4, block, 0, s>>>(a);
       return cudaGetLastError();
     }
   }
