@@ -165,17 +165,17 @@ __global__ void __launch_bounds__(SX * SY, 3) k_scat_sweep_v4(const ScatArgs<flo
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
   for (int n = n_begin; n < n_end; ++n) {
+    const Dir<float> dr = a.dir[n];  // uniform: one load per warp, ahead of the row loads
+    const bool sxp = dr.mu > 0.f, syp = dr.nu > 0.f;
     const float* jn = jin + (size_t)n * npix;
-    const float4 v = ld4g(jn + r0), vm = ld4g(jn + rm), vp = ld4g(jn + rp);
+    const float4 v = ld4g(jn + r0), vy = ld4g(jn + (syp ? rm : rp));  // own row, upstream row
     const float4 sv = ld4g(src + (size_t)n * a.src_stride + r0);
     float left = __shfl_up_sync(0xffffffffu, v.w, 1), right = __shfl_down_sync(0xffffffffu, v.x, 1);
     if (tx == 0 || x0 == 0) left = jn[il];   // warp edge, or the node itself at the boundary
     if (tx == SX - 1 || x0 + 4 >= nx) right = jn[ir];
-    const Dir<float> dr = a.dir[n];
-    const bool sxp = dr.mu > 0.f, syp = dr.nu > 0.f;
     const float dd = dr.ax + dr.ay;
     const float vv[4] = {v.x, v.y, v.z, v.w}, sgv[4] = {sg.x, sg.y, sg.z, sg.w}, ssv[4] = {sv.x, sv.y, sv.z, sv.w};
-    const float yv[4] = {syp ? vm.x : vp.x, syp ? vm.y : vp.y, syp ? vm.z : vp.z, syp ? vm.w : vp.w};
+    const float yv[4] = {vy.x, vy.y, vy.z, vy.w};
     const float yc[4] = {syp ? ccm.x : ccp.x, syp ? ccm.y : ccp.y, syp ? ccm.z : ccp.z, syp ? ccm.w : ccp.w};
     const float ys[4] = {syp ? sgm.x : sgp.x, syp ? sgm.y : sgp.y, syp ? sgm.z : sgp.z, syp ? sgm.w : sgp.w};
     const float cv[4] = {cc.x, cc.y, cc.z, cc.w};

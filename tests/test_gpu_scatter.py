@@ -86,6 +86,22 @@ def test_mg_cycle_sequence_fp64(name, mk, pg, scat):
         assert rel(host(psi), ref) < 1e-10, k
 
 
+@pytest.mark.parametrize("n,ny,bc", [(96, 72, (0, 0, 0, 0)), (100, 37, (1, 0, 0, 1)), (132, 20, (0, 1, 1, 0))])
+def test_mg_cycle_sequence_fp32_four_node_kernels(n, ny, bc):
+    """x sizes that are multiples of 4 take the four-nodes-per-thread FP32
+    kernels (first sweep from the UpSamp, sweeps from J, final pass);
+    ragged tiles and reflective sides included."""
+    prob = I.checkerboard(n=n, ny=ny, n_polar=8, n_azim=16, blocks=4, seed=21, c=0.97, length=6.0, bc=bc)
+    gp = btmg.Problem(prob, dtype=btmg.F32, pg=0, scat_levels=2)
+    op = O.OracleProblem(prob, pg=0, scat_levels=2)
+    psi = gp.zeros()
+    ref = op.zeros()
+    for k in range(3):
+        gp.mg_cycle(psi)
+        ref, _, _ = op.mg_cycle(ref)
+        assert rel(host(psi), ref) < 1e-5, k
+
+
 def test_mg_cycle_multigroup_fp64():
     prob = I.multigroup(n=24, n_polar=4, n_azim=8, G=3, blocks=3, seed=5)
     gp = btmg.Problem(prob, dtype=btmg.F64, pg=0, scat_levels=2)
