@@ -66,7 +66,9 @@ typedef struct btmg_problem btmg_problem;
 typedef struct {
   int32_t nx, ny;          /* nodes in x and y (>= 1)                        */
   double lx, ly;           /* domain size (> 0)                              */
-  int32_t order;           /* ConvFEM order: 2 (quadratic 5x5 filters) or 1 (linear 3x3; PG in FP64/FP32 only) */
+  int32_t order;           /* ConvFEM order: 2 (quadratic 5x5 filters), 1 (linear
+                              3x3; PG in FP64/FP32 only) or 3 (cubic 7x7, halo 9:
+                              direct-pass kernels with a 4 x psi-sized scratch) */
   int32_t n_polar, n_azim; /* direction grid: 8 faces of (n_polar/2)x(n_azim/4) */
   int32_t n_groups;        /* energy groups G (>= 1)                         */
   const int32_t* region;   /* host [ny][nx] region id per node               */
@@ -111,11 +113,11 @@ typedef struct {
 
 /* Builds the quadrature (Sec. 2.2), the space-angle hierarchy with harmonic
  * averaged cross sections (Sec. 2.5) and the device workspaces.  Copies every
- * host array.  Errors: INVALID_ARG (bad sizes, region ids, dtype, chunks,
+ * host array.  Errors: INVALID_ARG (bad sizes, region ids, dtype, order outside 1..3, chunks,
  * a non-finite or negative cross section, a non-finite source, scat_levels
  * outside 0..2 or, with scat_levels, an in-group sigma_s above sigma_t),
- * UNSUPPORTED (pg = 1 with an order other than 2, except order 1 with FP64 or
- * FP32 storage), OOM, CUDA.  *out is NULL on failure.                       */
+ * UNSUPPORTED (pg = 1 with order 1 and BF16/FP16 storage), OOM, CUDA.
+ * *out is NULL on failure.                                                 */
 int btmg_create_problem(const btmg_problem_desc* desc, void* stream, btmg_problem** out);
 
 /* Frees every library-owned device buffer.  NULL is accepted.              */
@@ -247,6 +249,13 @@ const char* btmg_unet_last_error(void);
  * without the step as CUDA graphs.  The U-net must outlive its use.
  * Errors: INVALID_ARG (null problem, every < 1), OOM.                      */
 int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every);
+/* The ConvFEM 1D stencils of an order (Sec. 2.7 and the Appendix) as the
+ * library derives them: m1 (mass over lumped mass), d1 (advection) and s1
+ * (stiffness) at offsets -3..3 (host arrays of 7; taps beyond the order's
+ * half width are 0), h = 1.  Host-only (no device needed).
+ * Errors: INVALID_ARG (order outside 1..3, NULL output).                   */
+int btmg_convfem_stencils(int32_t order, double* m1, double* d1, double* s1);
+
 /* Number of solves on p that dropped the scattering smoother
  * (desc.scat_levels) for the rest of the call: plain multigrid judges it as
  * it judges the learned step, btmg_solve when a residual exceeds twice its

@@ -31,7 +31,7 @@ EXPORTS = (
     "btmg_launch_count", "btmg_apply_operator_noalloc", "btmg_solve_refined",
     "btmg_unet_create", "btmg_unet_destroy", "btmg_unet_num_params", "btmg_unet_get_params",
     "btmg_unet_set_params", "btmg_unet_get_grads", "btmg_unet_forward", "btmg_unet_train_step",
-    "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_scatter_fallbacks", "btmg_learn_canvas",
+    "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_scatter_fallbacks", "btmg_convfem_stencils", "btmg_learn_canvas",
     "btmg_learn_features", "btmg_create_batch", "btmg_destroy_batch", "btmg_batch_problem",
     "btmg_batch_chunks", "btmg_solve_batch", "btmg_wait_selftest", "btmg_fp32_fma_rate",
 )
@@ -120,6 +120,8 @@ def load(build_if_missing: bool = True):
     L.btmg_set_learned.argtypes = [vp, vp, i32]
     L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i32)]
     L.btmg_scatter_fallbacks.argtypes = [vp, C.POINTER(i32)]
+    L.btmg_convfem_stencils.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]
     L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     L.btmg_learn_features.argtypes = [vp, vp, vp, vp, vp, vp]
     L.btmg_wait_selftest.argtypes = [i32, vp]
@@ -219,6 +221,14 @@ def make_desc(prob, dtype=F32, pg=1, nu=3, beta_pg=3.0, max_levels=0, pg_half=0,
     d.chunks = int(chunks)
     d.scat_levels = int(scat_levels)
     return d, keep
+
+
+def convfem_stencils(order):
+    """(m1, d1, s1) ConvFEM 1D stencils of the order at offsets -3..3, as the
+    library derives them (host computation, no device needed)."""
+    arrs = [np.zeros(7) for _ in range(3)]
+    _check(load().btmg_convfem_stencils(int(order), *[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs]))
+    return tuple(arrs)
 
 
 class Problem:

@@ -105,6 +105,60 @@ void octahedral_quadrature(int nr, int nc, std::vector<double>& mu, std::vector<
   for (int n = 0; n < nd; ++n) p[n] *= 4.0 * kPi / total;
 }
 
+// ConvFEM 1D stencils of order p (Sec. 2.7 and the Appendix), h = 1, stored
+// at offsets -3..3 (zero beyond -p..p): the Lagrange element of order p on [0, p] with nodes 0..p gives the
+// mass, advection and stiffness matrices M_ab = int N_a N_b,
+// C_ab = int N_a N_b', K_ab = int N_a' N_b'; the assembled rows of the p
+// node types (the corner, shared by two elements, and the p - 1 interior
+// nodes) are averaged and divided by the lumped mass.  The basis functions
+// are expanded into monomial coefficients and the products integrated
+// exactly (int_0^p x^k dx = p^(k+1) / (k+1)).
+void convfem_stencils(int p, double* m1, double* d1, double* s1) {
+  double N[4][4] = {}, D[4][4] = {};  // coefficient of x^k of N_a and of N_a'
+  for (int a = 0; a <= p; ++a) {
+    double c[4] = {1.0, 0.0, 0.0, 0.0};  // prod_{m != a} (x - m) / (a - m)
+    int deg = 0;
+    for (int m = 0; m <= p; ++m) {
+      if (m == a) continue;
+      double nc[4] = {};
+      for (int k = 0; k <= deg; ++k) {
+        nc[k + 1] += c[k] / (a - m);
+        nc[k] -= c[k] * m / (a - m);
+      }
+      ++deg;
+      for (int k = 0; k < 4; ++k) c[k] = nc[k];
+    }
+    for (int k = 0; k <= p; ++k) N[a][k] = c[k];
+    for (int k = 1; k <= p; ++k) D[a][k - 1] = k * c[k];
+  }
+  auto integ = [p](const double* f, const double* g) {  // int_0^p f g, both of degree <= 3
+    double s = 0.0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j)
+        if (f[i] != 0.0 && g[j] != 0.0) s += f[i] * g[j] * std::pow((double)p, i + j + 1) / (i + j + 1);
+    return s;
+  };
+  double am[7] = {}, ac[7] = {}, ak[7] = {};
+  auto add_row = [&](int a, int self) {  // row of local node a; the node sits at local index self
+    for (int b = 0; b <= p; ++b) {
+      am[b - self + p] += integ(N[a], N[b]);
+      ac[b - self + p] += integ(N[a], D[b]);
+      ak[b - self + p] += integ(D[a], D[b]);
+    }
+  };
+  add_row(p, p);  // corner: last node of the left element ...
+  add_row(0, 0);  // ... and first node of the right one
+  for (int k = 1; k < p; ++k) add_row(k, k);
+  double mL = 0.0;
+  for (int o = 0; o <= 2 * p; ++o) mL += am[o] / p;
+  for (int o = 0; o < 7; ++o) m1[o] = d1[o] = s1[o] = 0.0;
+  for (int o = 0; o <= 2 * p; ++o) {  // stored at offsets -3..3
+    m1[o + 3 - p] = am[o] / p / mL;
+    d1[o + 3 - p] = ac[o] / p / mL;
+    s1[o + 3 - p] = ak[o] / p / mL;
+  }
+}
+
 struct LevelH {
   int nx, ny, nr, nc, nd;
   double dx, dy;
@@ -139,6 +193,8 @@ struct btmg_problem {
   int scat_tail = 0;            // first level of the smoother's single-CTA tail (L: none)
   int plain_tail = 0;           // first level of the published cycle's single-CTA tail
   bool scat_off = false;        // solve-time fallback to the plain sweeps
+  double st_m1[7] = {}, st_d1[7] = {}, st_s1[7] = {};  // ConvFEM 1D stencils of the order
+  void* d_pgd = nullptr;        // cubic PG scratch: Psi_x, Psi_y, k_x, k_y [4][nd][ny][nx]
   int32_t scat_fallbacks = 0;   // solves that fell back
   void* d_sigs = nullptr;      // [G][G][npix]
   void* d_src = nullptr;       // [G][npix]
@@ -267,9 +323,22 @@ template <typename T, typename C> struct Impl {
     // Sec. 2.6 constants for order p: eps_k = 1e-3, alpha_kabs = 2^p/16,
     // alpha_ksquare = 2^p/2; alpha_r = beta_r = 3.
     a.eps_k = (C)1e-3;
-    a.a_kabs = (C)(P->d.order == 1 ? 0.125 : 0.25);  // 2^p / 16
-    a.a_ksq = (C)(P->d.order == 1 ? 1.0 : 2.0);      // 2^p / 2
+    a.a_kabs = (C)(std::ldexp(1.0, P->d.order) / 16.0);  // 2^p / 16
+    a.a_ksq = (C)(std::ldexp(1.0, P->d.order) / 2.0);    // 2^p / 2
     a.order = P->d.order;
+    if (P->d.order == 3) {  // the cubic path's stencils (offsets -3..3) and scratch
+      for (int o = 0; o < 7; ++o) {
+        a.cm1[o] = (C)P->st_m1[o];
+        a.cd1[o] = (C)P->st_d1[o];
+        a.cs1[o] = (C)P->st_s1[o];
+      }
+      const size_t n = L0.n();
+      C* base = dptr<C>(P->d_pgd);
+      a.gpx = base;
+      a.gpy = base + n;
+      a.gkx = base + 2 * n;
+      a.gky = base + 3 * n;
+    }
     a.a_r = (C)3.0;
     a.half = (C)(P->d.pg_half ? 0.5 : 1.0);
     a.beta = (C)(P->d.pg ? P->d.beta_pg : 1.0);
@@ -1023,7 +1092,7 @@ void destroy(btmg_problem* P) {
   for (auto v : {&P->d_dir, &P->d_rcoef, &P->d_sig, &P->d_s, &P->d_delta, &P->d_parent, &P->d_scat_w})
     for (void* p : *v)
       if (p) cudaFree(p);
-  for (void* p : {P->d_scat_j, P->d_scat_part, P->d_scat_c})
+  for (void* p : {P->d_scat_j, P->d_scat_part, P->d_scat_c, P->d_pgd})
     if (p) cudaFree(p);
   for (void* p : {P->d_sigs, P->d_src, P->d_b, P->d_phi_part, P->d_psi_tmp, (void*)P->d_norm_part, (void*)P->d_err,
                   (void*)P->d_qn2_part, (void*)P->d_rn2, (void*)P->d_qn2})
@@ -1103,8 +1172,9 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
     if (d->chunks < 0 || d->chunks > 64 || (d->chunks > 0 && nd % d->chunks))
       return fail(BTMG_ERR_INVALID_ARG, "chunks must be 0 or a divisor of the direction count, at most 64");
   }
-  if (d->pg && d->order != 2 && !(d->order == 1 && d->psi_dtype <= BTMG_F32))
-    return fail(BTMG_ERR_UNSUPPORTED, "the GPU PG operator implements order 2, and order 1 in FP64/FP32");
+  if (d->order < 1 || d->order > 3) return fail(BTMG_ERR_INVALID_ARG, "order must be 1, 2 or 3");
+  if (d->pg && d->order == 1 && d->psi_dtype > BTMG_F32)
+    return fail(BTMG_ERR_UNSUPPORTED, "the linear-order PG operator is built for FP64 and FP32 storage");
   for (int i = 0; i < 4; ++i)
     if (d->bc[i] != BTMG_VACUUM && d->bc[i] != BTMG_REFLECTIVE) return fail(BTMG_ERR_INVALID_ARG, "bad bc");
   const int G = d->n_groups, nx = d->nx, ny = d->ny;
@@ -1367,6 +1437,9 @@ int create(const btmg_problem_desc* d, btmg_problem** out) {
       cudaMalloc(&P->d_phi_part, (size_t)G * P->nchunk * npix * P->csize) != cudaSuccess ||
       cudaMalloc(&P->d_psi_tmp, F.n() * dtype_size(P->dtype)) != cudaSuccess)
     return bail(fail(BTMG_ERR_OOM, "workspace"));
+  convfem_stencils(d->order, P->st_m1, P->st_d1, P->st_s1);
+  if (d->pg && d->order == 3 && cudaMalloc(&P->d_pgd, 4 * F.n() * P->csize) != cudaSuccess)
+    return bail(fail(BTMG_ERR_OOM, "cubic PG scratch"));
   P->n_norm_sum = d->pg ? tiles * P->nchunk : upres_norm_blocks(F.nx, F.ny, P->nchunk);
   P->n_norm_part = std::max(tiles * P->nchunk, upres_norm_blocks(F.nx, F.ny, P->nchunk));
   P->n_q_blocks = (int)((npix + 255) / 256 < 1024 ? (npix + 255) / 256 : 1024);
@@ -1857,6 +1930,12 @@ int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every) {
   p->learn_count = 0;
   p->learn_fallbacks = 0;
   if (p->d_lstat) CK(cudaMemset(p->d_lstat, 0, sizeof(double) * 3));
+  return BTMG_OK;
+}
+
+int btmg_convfem_stencils(int32_t order, double* m1, double* d1, double* s1) {
+  if (order < 1 || order > 3 || !m1 || !d1 || !s1) return fail(BTMG_ERR_INVALID_ARG, "bad order or NULL output");
+  convfem_stencils(order, m1, d1, s1);
   return BTMG_OK;
 }
 

@@ -77,7 +77,11 @@ template <typename T, typename C> struct PgArgs {
   C eps_k, a_kabs, a_ksq, a_r, half, beta;
   Bc bc;
   int* err;  // set to nonzero when a bounded wait gave up (device word)
-  int order;  // ConvFEM order of the PG kernel: 2 (quadratic) or 1 (linear)
+  int order;  // ConvFEM order: 2 (quadratic) or 1 (linear) in the staged kernel, 3 (cubic) in k_pgd
+  // cubic path (k_pgd.cu): 1D stencils m1, d1, s1 at offsets -3..3 and the
+  // [nd][ny][nx] scratch of Psi_x, Psi_y, k_x, k_y
+  C cm1[7], cd1[7], cs1[7];
+  C *gpx, *gpy, *gkx, *gky;
 };
 
 // ------------------------------------------------------- upwind Jacobi ----
@@ -111,6 +115,8 @@ int upres_norm_blocks(int nx, int ny, int nchunk);  // norm partials of the upwi
 cudaError_t launch_wait_selftest(int* err, int polls, cudaStream_t s);
 template <typename T, typename C>
 cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cudaStream_t s);
+template <typename T, typename C>
+cudaError_t launch_pgd(const PgArgs<T, C>& a, int mode, int nchunk, cudaStream_t s);
 // resident CTAs per SM of the PG kernel (for choosing whole-wave grids)
 template <typename T, typename C> int pg_blocks_per_sm(bool pg);
 template <typename T, typename C>

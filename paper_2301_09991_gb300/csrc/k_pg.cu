@@ -674,6 +674,7 @@ template <typename T, typename C, int MODE, bool PGON> int occupancy_mode() {
 // tile: it runs in the streaming kernel of k_upres.cu.
 template <typename T, typename C>
 cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cudaStream_t s) {
+  if (pg && a.order == 3) return launch_pgd<T, C>(a, mode, nchunk, s);  // cubic: halo 9, direct passes
   if (pg)
     return mode == PG_RESID ? launch_mode<T, C, PG_RESID, true>(a, nchunk, s)
                             : launch_mode<T, C, PG_JACOBI, true>(a, nchunk, s);

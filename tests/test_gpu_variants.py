@@ -53,12 +53,53 @@ def test_linear_order_operator_fp32_and_cycle_fp64():
     assert rel(x.cpu().numpy(), ref) < 1e-10
 
 
-def test_linear_order_lowp_and_cubic_are_rejected():
+def test_linear_order_lowp_rejected_and_bad_order():
     prob = I.checkerboard(n=24, n_polar=4, n_azim=8, blocks=2, seed=15)
-    for order, dt in ((1, btmg.BF16), (3, btmg.F32)):
-        with pytest.raises(btmg.BtmgError) as e:
-            btmg.Problem(dict(prob, order=order), dtype=dt, pg=1)
-        assert e.value.code == btmg.ERR_UNSUPPORTED
+    with pytest.raises(btmg.BtmgError) as e:
+        btmg.Problem(dict(prob, order=1), dtype=btmg.BF16, pg=1)
+    assert e.value.code == btmg.ERR_UNSUPPORTED
+    with pytest.raises(btmg.BtmgError) as e:
+        btmg.Problem(dict(prob, order=4), dtype=btmg.F32, pg=1)
+    assert e.value.code == btmg.ERR_INVALID_ARG
+
+
+CUBIC = [
+    ("checker_40x29", lambda: I.checkerboard(n=40, ny=29, n_polar=8, n_azim=8, blocks=4, seed=16)),
+    ("reflective_37x35", lambda: I.checkerboard(n=37, ny=35, n_polar=4, n_azim=8, blocks=3, seed=17,
+                                                bc=(1, 0, 0, 1))),
+    ("tiny_5x4", lambda: I.checkerboard(n=5, ny=4, n_polar=4, n_azim=8, blocks=2, seed=18)),
+]
+
+
+@pytest.mark.parametrize("name,mk", CUBIC)
+def test_cubic_order_operator_and_cycle(name, mk):
+    """Cubic ConvFEM (7 x 7 filters, halo 9) in the direct-pass PG kernels:
+    the operator in FP64 (1e-12) and FP32 (1e-6), two FP64 cycles (1e-10)."""
+    prob = dict(mk(), order=3)
+    op = O.OracleProblem(prob, pg=1)
+    g64 = btmg.Problem(prob, dtype=btmg.F64, pg=1)
+    psi = I.random_field(g64.shape, seed=33)
+    r64 = g64.apply_operator(torch.tensor(psi, device="cuda")).cpu().numpy()
+    ref = op.apply(psi)
+    assert rel(r64, ref) < 1e-12
+    g32 = btmg.Problem(prob, dtype=btmg.F32, pg=1)
+    r32 = g32.apply_operator(torch.tensor(psi.astype(np.float32), device="cuda")).double().cpu().numpy()
+    assert rel(r32, op.apply(psi.astype(np.float32).astype(np.float64))) < 1e-6
+    x = g64.zeros()
+    refc = op.zeros()
+    for _ in range(2):
+        g64.mg_cycle(x, want_residual=False)
+        refc, _, _ = op.mg_cycle(refc)
+    assert rel(x.cpu().numpy(), refc) < 1e-10
+
+
+def test_cubic_order_bf16_storage_operator():
+    prob = dict(I.checkerboard(n=48, ny=40, n_polar=8, n_azim=8, blocks=4, seed=19), order=3)
+    op = O.OracleProblem(prob, pg=1)
+    gb = btmg.Problem(prob, dtype=btmg.BF16, pg=1)
+    psi = torch.tensor(I.random_field(gb.shape, seed=34), dtype=torch.bfloat16, device="cuda")
+    r = gb.apply_operator(psi).double().cpu().numpy()
+    assert rel(r, op.apply(psi.double().cpu().numpy())) < 1e-6
 
 
 def test_duct_streaming_qualitative():

@@ -43,3 +43,24 @@ def test_error_strings_without_gpu():
     from paper_2301_09991_gb300 import btmg
     assert btmg.error_string(0) == "ok"
     assert "invalid" in btmg.error_string(-1)
+
+
+def test_library_stencils_match_the_pinned_oracle():
+    """The library derives its ConvFEM stencils itself (exact polynomial
+    integration, host code, no device needed); they must equal the oracle's,
+    which the pins tie to the paper's printed tables (Appendix A.1-A.3), and
+    the quadratic ones the closed forms."""
+    import numpy as np
+    import oracle as O
+    from paper_2301_09991_gb300 import btmg
+    for p in (1, 2, 3):
+        m1, d1, s1 = btmg.convfem_stencils(p)
+        om1, od1, os1, _ = O.convfem_1d(p)
+        pad = 3 - p
+        for got, ref in ((m1, om1), (d1, od1), (s1, os1)):
+            np.testing.assert_allclose(got[pad:7 - pad], ref, rtol=0, atol=1e-13)
+            assert np.all(got[:pad] == 0) and np.all(got[7 - pad:] == 0)
+    m1, d1, s1 = btmg.convfem_stencils(2)
+    np.testing.assert_allclose(m1[1:6], np.array([-1, 4, 24, 4, -1]) / 30, atol=1e-15)
+    np.testing.assert_allclose(d1[1:6], np.array([1, -8, 0, 8, -1]) / 12, atol=1e-15)
+    np.testing.assert_allclose(s1[1:6], np.array([1, -16, 30, -16, 1]) / 12, atol=1e-15)
