@@ -276,6 +276,25 @@ def sweep_rooflines(btmg, torch, prob, pk, peak_src, cycles=10):
                            "coarse_ms_per_cycle": round(prof["upwind_coarse"][0] / cycles, 4),
                            "cycle_ms": round(sum(v[0] for v in prof.values()) / cycles, 4)}
     del gp, psi
+    # cubic ConvFEM order (7 x 7 filters, halo 9), PG on: the fine PG
+    # residual and Jacobi in three direct passes (k_pgd_grad, k_pgd_k,
+    # k_pgd_apply), per launch of the operator
+    prob3 = dict(prob, order=3)
+    gp = btmg.Problem(prob3, dtype=btmg.F32, pg=1)
+    psi = gp.zeros()
+    for _ in range(3):
+        gp.mg_cycle(psi, want_residual=False)
+    gp.profile(True)
+    for _ in range(cycles):
+        gp.mg_cycle(psi, want_residual=False)
+    torch.cuda.synchronize()
+    prof = gp.profile_read()
+    gp.profile(False)
+    out["cubic_pg"] = {"kernel": "cubic PG operator (k_pgd_grad, k_pgd_k, k_pgd_apply)",
+                       "resid_ms": round(prof["pg_residual"][0] / max(prof["pg_residual"][1], 1), 4),
+                       "jacobi_ms": round(prof["pg_jacobi"][0] / max(prof["pg_jacobi"][1], 1), 4),
+                       "cycle_ms": round(sum(v[0] for v in prof.values()) / cycles, 4)}
+    del gp, psi
     return out
 
 
