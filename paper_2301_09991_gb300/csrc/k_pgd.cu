@@ -17,15 +17,15 @@
 // too.  The staged shared-memory kernel (k_pg.cu) covers orders 1 and 2;
 // this path trades its speed for a halo of 9 nodes.
 //
-// Layout: 32 x 32 node tiles of 256 threads, a thread owning column tx and
-// rows ty + 8k; grad and k run one direction per block row, apply a chunk
+// Layout: 32 x 32 node tiles of 128 threads, a thread owning an 8-row strip
+// of one column; grad and k run one direction per block row, apply a chunk
 // of directions per block (scalar-flux and norm partials as in k_pg).
 #include "btmg_common.cuh"
 
 namespace btmg {
 namespace {
 
-constexpr int DT = 32, DNT = 256;
+constexpr int DT = 32;
 
 template <typename C> __device__ __forceinline__ C dabs(C v) { return v < C(0) ? -v : v; }
 __device__ __forceinline__ float ddiv(float a, float b) { return __fdividef(a, b); }
@@ -42,136 +42,193 @@ template <typename C> __device__ __forceinline__ C der_ext(const C* f, int x, in
   return f[(size_t)clampi(y, 0, ny - 1) * nx + clampi(x, 0, nx - 1)];
 }
 
-template <typename T, typename C, int L> __global__ void __launch_bounds__(DNT) k_pgd_grad(const PgArgs<T, C> a) {
+// A thread owns an 8-row strip of one column (SR rows, 128 threads per
+// 32 x 32 tile): the row sums of a 7-tap x pass are computed once per row and
+// slide through a 7-deep register window for the y pass, so an output reads
+// (SR + 2L) / SR rows of 7 taps instead of its full 49-point stencil.  Every
+// shift below is constant along the strip (the first node's value): the
+// filters it enters sum to zero or act through (m1 m1 - I), so the results
+// are those of the definition.
+constexpr int SR = 8, SNT = 128;
+
+template <typename T, typename C, int L> __global__ void __launch_bounds__(SNT) k_pgd_grad(const PgArgs<T, C> a) {
   const int n = blockIdx.y;
   const int x = (blockIdx.x % a.tiles_x) * DT + (threadIdx.x & 31);
-  const int y0 = (blockIdx.x / a.tiles_x) * DT + (threadIdx.x >> 5);
-  if (x >= a.nx) return;
+  const int ys = (blockIdx.x / a.tiles_x) * DT + (threadIdx.x >> 5) * SR;
+  if (x >= a.nx || ys >= a.ny) return;
   const Dir<C> dr = a.dir[n];
   const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
   const size_t npix = (size_t)a.nx * a.ny;
   const T* pn = a.psi + (size_t)n * npix;
-  for (int y = y0; y < min(y0 + DT, a.ny); y += 8) {
-    const C c0 = (C)Conv<T>::ld(pn + (size_t)y * a.nx + x);
-    C gx = C(0), gy = C(0);
+  const C c0 = (C)Conv<T>::ld(pn + (size_t)ys * a.nx + x);
+  C wd[2 * L + 1], wm[2 * L + 1];  // row sums d1_x q and m1_x q of rows y - L .. y + L
+#pragma unroll 1
+  for (int r = 0; r < SR + 2 * L; ++r) {
+    const int yr = ys - L + r;
+    C sd = C(0), sm = C(0);
 #pragma unroll
-    for (int v = -L; v <= L; ++v) {
-      C sd = C(0), sm = C(0);  // d1_x and m1_x of row y + v
-#pragma unroll
-      for (int u = -L; u <= L; ++u) {
-        const C q = psi_ext<T, C>(pn, x + u, y + v, a.nx, a.ny, a.bc, sxp, syp) - c0;
-        sd += a.cd1[u + L] * q;
-        sm += a.cm1[u + L] * q;
-      }
-      gx += a.cm1[v + L] * sd;
-      gy += a.cd1[v + L] * sm;
+    for (int u = -L; u <= L; ++u) {
+      const C q = psi_ext<T, C>(pn, x + u, yr, a.nx, a.ny, a.bc, sxp, syp) - c0;
+      sd += a.cd1[u + L] * q;
+      sm += a.cm1[u + L] * q;
     }
-    const size_t gi = (size_t)n * npix + (size_t)y * a.nx + x;
-    a.gpx[gi] = gx * a.inv_dx;
-    a.gpy[gi] = gy * a.inv_dy;
+#pragma unroll
+    for (int k = 0; k < 2 * L; ++k) wd[k] = wd[k + 1], wm[k] = wm[k + 1];
+    wd[2 * L] = sd;
+    wm[2 * L] = sm;
+    if (r >= 2 * L) {
+      const int y = yr - L;
+      if (y < a.ny) {
+        C gx = C(0), gy = C(0);
+#pragma unroll
+        for (int v = 0; v <= 2 * L; ++v) {
+          gx += a.cm1[v] * wd[v];
+          gy += a.cd1[v] * wm[v];
+        }
+        const size_t gi = (size_t)n * npix + (size_t)y * a.nx + x;
+        a.gpx[gi] = gx * a.inv_dx;
+        a.gpy[gi] = gy * a.inv_dy;
+      }
+    }
   }
 }
 
-template <typename T, typename C, int L> __global__ void __launch_bounds__(DNT) k_pgd_k(const PgArgs<T, C> a) {
+template <typename T, typename C, int L> __global__ void __launch_bounds__(SNT) k_pgd_k(const PgArgs<T, C> a) {
   const int n = blockIdx.y;
   const int x = (blockIdx.x % a.tiles_x) * DT + (threadIdx.x & 31);
-  const int y0 = (blockIdx.x / a.tiles_x) * DT + (threadIdx.x >> 5);
-  if (x >= a.nx) return;
+  const int ys = (blockIdx.x / a.tiles_x) * DT + (threadIdx.x >> 5) * SR;
+  if (x >= a.nx || ys >= a.ny) return;
   const Dir<C> dr = a.dir[n];
   const size_t npix = (size_t)a.nx * a.ny;
   const C* px = a.gpx + (size_t)n * npix;
   const C* py = a.gpy + (size_t)n * npix;
   const C amu = dabs(dr.mu), anu = dabs(dr.nu);
-  for (int y = y0; y < min(y0 + DT, a.ny); y += 8) {
-    const size_t i = (size_t)y * a.nx + x;
-    const C px0 = px[i], py0 = py[i];
-    C mx = C(0), my = C(0);
+  const C cx = px[(size_t)ys * a.nx + x], cy = py[(size_t)ys * a.nx + x];
+  C wx[2 * L + 1], wy[2 * L + 1];  // row sums m1_x (Psi - c) of rows y - L .. y + L
+#pragma unroll 1
+  for (int r = 0; r < SR + 2 * L; ++r) {
+    const int yr = ys - L + r;
+    C sx = C(0), sy = C(0);
 #pragma unroll
-    for (int v = -L; v <= L; ++v) {
-      C rx = C(0), ry = C(0);
-#pragma unroll
-      for (int u = -L; u <= L; ++u) {
-        rx += a.cm1[u + L] * (der_ext(px, x + u, y + v, a.nx, a.ny) - px0);
-        ry += a.cm1[u + L] * (der_ext(py, x + u, y + v, a.nx, a.ny) - py0);
-      }
-      mx += a.cm1[v + L] * rx;
-      my += a.cm1[v + L] * ry;
+    for (int u = -L; u <= L; ++u) {
+      sx += a.cm1[u + L] * (der_ext(px, x + u, yr, a.nx, a.ny) - cx);
+      sy += a.cm1[u + L] * (der_ext(py, x + u, yr, a.nx, a.ny) - cy);
     }
-    const C Rx = a.a_r * dr.mu * mx, Ry = a.a_r * dr.nu * my;
-    const C kxa = ddiv(a.a_kabs * dabs(Rx) * a.dx, a.eps_k + dabs(px0));
-    const C kya = ddiv(a.a_kabs * dabs(Ry) * a.dy, a.eps_k + dabs(py0));
-    const C kxs = ddiv(a.a_ksq * Rx * Rx * a.dx, a.eps_k + amu * px0 * px0);
-    const C kys = ddiv(a.a_ksq * Ry * Ry * a.dy, a.eps_k + anu * py0 * py0);
-    const C kxm = a.dx * amu, kym = a.dy * anu;
-    const size_t gi = (size_t)n * npix + i;
-    a.gkx[gi] = kxm < kxa ? (kxm < kxs ? kxm : kxs) : (kxa < kxs ? kxa : kxs);
-    a.gky[gi] = kym < kya ? (kym < kys ? kym : kys) : (kya < kys ? kya : kys);
+#pragma unroll
+    for (int k = 0; k < 2 * L; ++k) wx[k] = wx[k + 1], wy[k] = wy[k + 1];
+    wx[2 * L] = sx;
+    wy[2 * L] = sy;
+    if (r >= 2 * L) {
+      const int y = yr - L;
+      if (y < a.ny) {
+        const size_t i = (size_t)y * a.nx + x;
+        const C px0 = px[i], py0 = py[i];
+        C mx = C(0), my = C(0);
+#pragma unroll
+        for (int v = 0; v <= 2 * L; ++v) {
+          mx += a.cm1[v] * wx[v];
+          my += a.cm1[v] * wy[v];
+        }
+        const C Rx = a.a_r * dr.mu * (mx - (px0 - cx)), Ry = a.a_r * dr.nu * (my - (py0 - cy));
+        const C kxa = ddiv(a.a_kabs * dabs(Rx) * a.dx, a.eps_k + dabs(px0));
+        const C kya = ddiv(a.a_kabs * dabs(Ry) * a.dy, a.eps_k + dabs(py0));
+        const C kxs = ddiv(a.a_ksq * Rx * Rx * a.dx, a.eps_k + amu * px0 * px0);
+        const C kys = ddiv(a.a_ksq * Ry * Ry * a.dy, a.eps_k + anu * py0 * py0);
+        const C kxm = a.dx * amu, kym = a.dy * anu;
+        const size_t gi = (size_t)n * npix + i;
+        a.gkx[gi] = kxm < kxa ? (kxm < kxs ? kxm : kxs) : (kxa < kxs ? kxa : kxs);
+        a.gky[gi] = kym < kya ? (kym < kys ? kym : kys) : (kya < kys ? kya : kys);
+      }
+    }
   }
 }
 
 template <typename T, typename C, int MODE, int L>
-__global__ void __launch_bounds__(DNT) k_pgd_apply(const PgArgs<T, C> a) {
-  __shared__ double red[DNT / 32];
+__global__ void __launch_bounds__(SNT) k_pgd_apply(const PgArgs<T, C> a) {
+  __shared__ double red[SNT / 32];
   const int tile = blockIdx.x, chunk = blockIdx.y;
   const int x = (tile % a.tiles_x) * DT + (threadIdx.x & 31);
-  const int y0 = (tile / a.tiles_x) * DT + (threadIdx.x >> 5);
+  const int ys = (tile / a.tiles_x) * DT + (threadIdx.x >> 5) * SR;
   const size_t npix = (size_t)a.nx * a.ny;
   const int n_begin = chunk * a.dpc, n_end = min(n_begin + a.dpc, a.nd);
   double nrm = 0.0;
-  C acc[4] = {C(0), C(0), C(0), C(0)};
-  if (x < a.nx) {
+  C acc[SR];
+#pragma unroll
+  for (int k = 0; k < SR; ++k) acc[k] = C(0);
+  const bool live = x < a.nx && ys < a.ny;
+  if (live) {
     for (int n = n_begin; n < n_end; ++n) {
       const Dir<C> dr = a.dir[n];
       const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
       const T* pn = a.psi + (size_t)n * npix;
       const C* kxn = a.gkx + (size_t)n * npix;
       const C* kyn = a.gky + (size_t)n * npix;
+      const C c0 = (C)Conv<T>::ld(pn + (size_t)ys * a.nx + x);
+      // row sums of rows y - L .. y + L: s1_x (k_x q), s1_x q, s1_x k_x and
+      // m1_x (k_y q), m1_x q, m1_x k_y, with q = psi - c0
+      C w1[2 * L + 1], w2[2 * L + 1], w3[2 * L + 1], w4[2 * L + 1], w5[2 * L + 1], w6[2 * L + 1];
       C nrm_dir = C(0);
 #pragma unroll 1
-      for (int k = 0; k < 4; ++k) {
-        const int y = y0 + 8 * k;
-        if (y >= a.ny) break;
-        const size_t i = (size_t)y * a.nx + x, gi = (size_t)n * npix + i;
-        const C p0 = (C)Conv<T>::ld(pn + i);
-        const C kx0 = kxn[i], ky0 = kyn[i];
-        C fkx = C(0), fpx = C(0), fky = C(0), fpy = C(0);  // f(k q; w), f(q; w) with q = psi - p0
+      for (int r = 0; r < SR + 2 * L; ++r) {
+        const int yr = ys - L + r;
+        C s1a = C(0), s1b = C(0), s1c = C(0), m1a = C(0), m1b = C(0), m1c = C(0);
 #pragma unroll
-        for (int v = -L; v <= L; ++v) {
-          C ax1 = C(0), ax2 = C(0), ay1 = C(0), ay2 = C(0);
-#pragma unroll
-          for (int u = -L; u <= L; ++u) {
-            const C q = psi_ext<T, C>(pn, x + u, y + v, a.nx, a.ny, a.bc, sxp, syp) - p0;
-            const C kxe = der_ext(kxn, x + u, y + v, a.nx, a.ny), kye = der_ext(kyn, x + u, y + v, a.nx, a.ny);
-            ax1 += a.cs1[u + L] * (kxe * q);
-            ax2 += a.cs1[u + L] * q;
-            ay1 += a.cm1[u + L] * (kye * q);
-            ay2 += a.cm1[u + L] * q;
-          }
-          fkx += a.cm1[v + L] * ax1;
-          fpx += a.cm1[v + L] * ax2;
-          fky += a.cs1[v + L] * ay1;
-          fpy += a.cs1[v + L] * ay2;
+        for (int u = -L; u <= L; ++u) {
+          const C q = psi_ext<T, C>(pn, x + u, yr, a.nx, a.ny, a.bc, sxp, syp) - c0;
+          const C kxe = der_ext(kxn, x + u, yr, a.nx, a.ny), kye = der_ext(kyn, x + u, yr, a.nx, a.ny);
+          s1a += a.cs1[u + L] * (kxe * q);
+          s1b += a.cs1[u + L] * q;
+          s1c += a.cs1[u + L] * kxe;
+          m1a += a.cm1[u + L] * (kye * q);
+          m1b += a.cm1[u + L] * q;
+          m1c += a.cm1[u + L] * kye;
         }
-        const C Dx = (fkx + kx0 * fpx) * a.inv_dx2, Dy = (fky + ky0 * fpy) * a.inv_dy2;
-        const C sig = a.sigt[i];
-        const C Apsi = dr.mu * a.gpx[gi] + dr.nu * a.gpy[gi] + a.half * (Dx + Dy) + sig * p0;
-        const C r = a.b[i] + (a.extra ? a.extra[gi] : C(0)) - Apsi;
-        if (MODE == PG_RESID) {
-          a.r_out[gi] = r;
-          nrm_dir += r * r;
-          acc[k] += dr.w * r;
-        } else {
-          const C pnew = p0 + ddiv(r, a.beta * (dr.ax + dr.ay + sig));
-          Conv<T>::st(a.psi_out + gi, pnew);
-          acc[k] += dr.w * stored<T, C>(pnew);
+#pragma unroll
+        for (int k = 0; k < 2 * L; ++k)
+          w1[k] = w1[k + 1], w2[k] = w2[k + 1], w3[k] = w3[k + 1], w4[k] = w4[k + 1], w5[k] = w5[k + 1],
+          w6[k] = w6[k + 1];
+        w1[2 * L] = s1a, w2[2 * L] = s1b, w3[2 * L] = s1c, w4[2 * L] = m1a, w5[2 * L] = m1b, w6[2 * L] = m1c;
+        if (r >= 2 * L) {
+          const int y = yr - L;
+          if (y < a.ny) {
+            const size_t i = (size_t)y * a.nx + x, gi = (size_t)n * npix + i;
+            const C p0 = (C)Conv<T>::ld(pn + i), q0 = p0 - c0;
+            const C kx0 = kxn[i], ky0 = kyn[i];
+            C fkx = C(0), fpx = C(0), fxk = C(0), fky = C(0), fpy = C(0), fyk = C(0);
+#pragma unroll
+            for (int v = 0; v <= 2 * L; ++v) {
+              fkx += a.cm1[v] * w1[v];
+              fpx += a.cm1[v] * w2[v];
+              fxk += a.cm1[v] * w3[v];
+              fky += a.cs1[v] * w4[v];
+              fpy += a.cs1[v] * w5[v];
+              fyk += a.cs1[v] * w6[v];
+            }
+            const C Dx = (fkx + kx0 * fpx - q0 * fxk) * a.inv_dx2;
+            const C Dy = (fky + ky0 * fpy - q0 * fyk) * a.inv_dy2;
+            const C sig = a.sigt[i];
+            const C Apsi = dr.mu * a.gpx[gi] + dr.nu * a.gpy[gi] + a.half * (Dx + Dy) + sig * p0;
+            const C res = a.b[i] + (a.extra ? a.extra[gi] : C(0)) - Apsi;
+            const int k = r - 2 * L;
+            if (MODE == PG_RESID) {
+              a.r_out[gi] = res;
+              nrm_dir += res * res;
+              acc[k] += dr.w * res;
+            } else {
+              const C pnew = p0 + ddiv(res, a.beta * (dr.ax + dr.ay + sig));
+              Conv<T>::st(a.psi_out + gi, pnew);
+              acc[k] += dr.w * stored<T, C>(pnew);
+            }
+          }
         }
       }
       if (MODE == PG_RESID) nrm += (double)dr.w * (double)nrm_dir;
     }
     C* part = MODE == PG_JACOBI ? a.phi_part : a.rho_part;
     if (part) {
-      for (int k = 0; k < 4; ++k) {
-        const int y = y0 + 8 * k;
+#pragma unroll
+      for (int k = 0; k < SR; ++k) {
+        const int y = ys + k;
         if (y < a.ny) part[(size_t)chunk * npix + (size_t)y * a.nx + x] = acc[k];
       }
     }
@@ -182,7 +239,7 @@ __global__ void __launch_bounds__(DNT) k_pgd_apply(const PgArgs<T, C> a) {
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
-      for (int w = 0; w < DNT / 32; ++w) s += red[w];
+      for (int w = 0; w < SNT / 32; ++w) s += red[w];
       a.norm_part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s * (double)a.dxdy;
     }
   }
@@ -196,12 +253,12 @@ cudaError_t launch_pgd(const PgArgs<T, C>& a, int mode, int nchunk, cudaStream_t
   if (a.order != 3) return cudaErrorNotSupported;
   const int tiles_y = (a.ny + DT - 1) / DT;
   const dim3 gdir(a.tiles_x * tiles_y, a.nd), gchunk(a.tiles_x * tiles_y, nchunk);
-  k_pgd_grad<T, C, 3><<<gdir, DNT, 0, s>>>(a);
-  k_pgd_k<T, C, 3><<<gdir, DNT, 0, s>>>(a);
+  k_pgd_grad<T, C, 3><<<gdir, SNT, 0, s>>>(a);
+  k_pgd_k<T, C, 3><<<gdir, SNT, 0, s>>>(a);
   if (mode == PG_RESID)
-    k_pgd_apply<T, C, PG_RESID, 3><<<gchunk, DNT, 0, s>>>(a);
+    k_pgd_apply<T, C, PG_RESID, 3><<<gchunk, SNT, 0, s>>>(a);
   else
-    k_pgd_apply<T, C, PG_JACOBI, 3><<<gchunk, DNT, 0, s>>>(a);
+    k_pgd_apply<T, C, PG_JACOBI, 3><<<gchunk, SNT, 0, s>>>(a);
   return cudaGetLastError();
 }
 

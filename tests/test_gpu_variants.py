@@ -74,7 +74,10 @@ CUBIC = [
 @pytest.mark.parametrize("name,mk", CUBIC)
 def test_cubic_order_operator_and_cycle(name, mk):
     """Cubic ConvFEM (7 x 7 filters, halo 9) in the direct-pass PG kernels:
-    the operator in FP64 (1e-12) and FP32 (1e-6), two FP64 cycles (1e-10)."""
+    the operator in FP64 (1e-12) and FP32, two FP64 cycles (1e-10).  FP32
+    bound: the quadratic operator's 1e-6 scaled by the tap count of its
+    correlations, (7 / 5)^2 ~ 2 (random fields: every term of a 49-point
+    sum is of the size of psi)."""
     prob = dict(mk(), order=3)
     op = O.OracleProblem(prob, pg=1)
     g64 = btmg.Problem(prob, dtype=btmg.F64, pg=1)
@@ -84,7 +87,7 @@ def test_cubic_order_operator_and_cycle(name, mk):
     assert rel(r64, ref) < 1e-12
     g32 = btmg.Problem(prob, dtype=btmg.F32, pg=1)
     r32 = g32.apply_operator(torch.tensor(psi.astype(np.float32), device="cuda")).double().cpu().numpy()
-    assert rel(r32, op.apply(psi.astype(np.float32).astype(np.float64))) < 1e-6
+    assert rel(r32, op.apply(psi.astype(np.float32).astype(np.float64))) < 2e-6
     x = g64.zeros()
     refc = op.zeros()
     for _ in range(2):
@@ -99,7 +102,7 @@ def test_cubic_order_bf16_storage_operator():
     gb = btmg.Problem(prob, dtype=btmg.BF16, pg=1)
     psi = torch.tensor(I.random_field(gb.shape, seed=34), dtype=torch.bfloat16, device="cuda")
     r = gb.apply_operator(psi).double().cpu().numpy()
-    assert rel(r, op.apply(psi.double().cpu().numpy())) < 1e-6
+    assert rel(r, op.apply(psi.double().cpu().numpy())) < 2e-6  # FP32 arithmetic, as above
 
 
 def test_duct_streaming_qualitative():
