@@ -305,7 +305,7 @@ def time_to_residual(btmg, torch, rtol=1e-6):
     step on this GPU, whose FP64 rate is a small fraction of its FP32 rate) and
     FP64-refined FP32 with the learned correction (upwind fine operator,
     pg = 0, for which the FP64 refinement is defined), and FP64-refined FP32 /
-    BF16 with the scattering smoother on every level (scat_levels = 2, judged
+    BF16 with the scattering smoother on every level (scat_levels = 2, arbitrated
     by plain multigrid: an outer residual above 1.5 times the best drops it
     for the rest of the solve)."""
     from paper_2301_09991_gb300 import learned as LN

@@ -245,7 +245,7 @@ const char* btmg_unet_last_error(void);
  *      |alpha| rms(phi(c')) <= 1e3 rms(phi(psi') - phi0).
  * The step cannot raise the residual norm of the linear (pg = 0) operator;
  * alpha = 0 is the plain cycle (plain multigrid is the fallback and the
- * judge).  Everything runs on the device and solves capture cycles with and
+ * arbiter).  Everything runs on the device and solves capture cycles with and
  * without the step as CUDA graphs.  The U-net must outlive its use.
  * Errors: INVALID_ARG (null problem, every < 1), OOM.                      */
 int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every);
@@ -257,8 +257,8 @@ int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every);
 int btmg_convfem_stencils(int32_t order, double* m1, double* d1, double* s1);
 
 /* Number of solves on p that dropped the scattering smoother
- * (desc.scat_levels) for the rest of the call: plain multigrid judges it as
- * it judges the learned step, btmg_solve when a residual exceeds twice its
+ * (desc.scat_levels) for the rest of the call: plain multigrid arbitrates it as
+ * it arbitrates the learned step, btmg_solve when a residual exceeds twice its
  * best so far, btmg_solve_refined when an outer FP64 residual exceeds 1.5
  * times its best; the next call starts with the smoother again.  Batched
  * solves do not fall back.  Errors: INVALID_ARG (NULL argument).          */

@@ -339,7 +339,7 @@ class Problem:
 
     def scatter_fallbacks(self):
         """Solves on this problem that dropped the scattering smoother
-        (plain-judged fallback)."""
+        (fallback arbitrated by plain multigrid)."""
         n = C.c_int32()
         _check(load().btmg_scatter_fallbacks(self.h, C.byref(n)))
         return n.value

@@ -638,7 +638,7 @@ template <typename T, typename C> struct Impl {
   }
 
   // A cycle of group g with the learned step (plain multigrid stays the
-  // judge and the fallback):
+  // arbiter and the fallback):
   //  1. phi0 = scalar flux of psi; psi' = the plain cycle of psi;
   //  2. r' = residual of psi', rho' = sum_n p_n r'_n;
   //  3. the U-net predicts the shape of the scalar-flux error e of psi' from
@@ -830,7 +830,7 @@ template <typename T, typename C> struct Impl {
               status = BTMG_ERR_DIVERGED;
               break;
             }
-            // plain multigrid judges the learned step: a residual above
+            // plain multigrid is the arbiter of the learned step: a residual above
             // twice the best so far ends it for the rest of this solve
             if (P->learned && !P->learn_off && best < 1e299 && rel > 2.0 * best) {
               P->learn_off = true;
@@ -921,7 +921,7 @@ int refine_solve(btmg_problem* P, double* psi64, double rtol, int max_outer, int
       break;
     }
     if (outer == max_outer) break;
-    // plain multigrid judges the learned step: an outer residual above 1.5
+    // plain multigrid is the arbiter of the learned step: an outer residual above 1.5
     // times the best so far ends it for the rest of this solve
     if (P->learned && !P->learn_off && rel > 1.5 * best) {
       P->learn_off = true;

@@ -169,7 +169,7 @@ def test_batch_members_equal_single_cycles():
         assert torch.equal(psi, q)
 
 
-def test_plain_multigrid_judges_the_smoother():
+def test_plain_multigrid_arbitrates_the_smoother():
     """Thin unit square at 512^2 x 1024 directions, c = 0.9: the smoother's
     cycle grows the residual in mid-solve (a transient the published cycle
     also shows, weaker); the solve drops it when the residual passes twice
