@@ -42,9 +42,12 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
   constexpr int WS = UT + 2 * NU;   // sigma region covering both upwind sides
   constexpr int NS = (W * W + UNT - 1) / UNT;  // region cells per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // two sweep buffers, each followed by one spare cell that the unused
+  // slots of the last thread row read and write (no per-cell tests)
+  constexpr int DB = WP * WP + 1;
   C* D0 = reinterpret_cast<C*>(smem_raw);
-  C* D1 = D0 + WP * WP;
-  C* SG = D1 + WP * WP;
+  C* D1 = D0 + DB;
+  C* SG = D1 + DB;
 
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int tile = blockIdx.x, chunk = blockIdx.y;
@@ -56,21 +59,23 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
     const int gx = x0 - NU + i % WS, gy = y0 - NU + i / WS;
     SG[i] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? a.sig[gy * nx + gx] : C(0);
   }
-  for (int i = tid; i < 2 * WP * WP; i += UNT) D0[i] = C(0);  // zero rings of D0 and D1
+  for (int i = tid; i < 2 * DB; i += UNT) D0[i] = C(0);  // zero rings of D0 and D1
 
-  // owned cells: shared-memory index of slot s in D0/D1, or -1 when unused
-  int sidx[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const int i = tid + UNT * s;
-    sidx[s] = i < W * W ? (i / W + 1) * WP + i % W + 1 : -1;
-  }
   // The region's placement depends only on the signs of mu and nu, which a
   // chunk of directions (inside one octant face) shares: the global offset
   // of each owned cell (-1 outside the domain), its UpSamp parent offset and
   // its sigma are computed once per sign combination, not per direction.
   int gofs[NS], cofs[NS];
   C sgv[NS];
+  // byte offset into a sweep buffer of each slot's cell (one-cell ring
+  // around the region), or of the spare cell for an unused slot (whose
+  // upstream reads stay inside the shared allocation and are never used)
+  unsigned cb[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int i = tid + UNT * s;
+    cb[s] = (unsigned)(i < W * W ? (i / W + 1) * WP + i % W + 1 : WP * WP) * sizeof(C);
+  }
   int combo = -1;
   const int shx = a.fx >> 1, shy = a.fy >> 1;
   auto geom = [&](int cmb) {
@@ -139,13 +144,26 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
   // not hold the previous direction's result: the last reads of that buffer
   // were in the previous direction's final sweep, which ended at a barrier,
   // so no barrier is needed before the write.
+  // With nu odd the result of a direction lands in D1 and the next one
+  // starts from D0 again: the buffers stay fixed (constant offsets).
   C* Dinit = D0;
   C* Dother = D1;
+  auto at = [](C* D, unsigned off) -> C& { return *reinterpret_cast<C*>(reinterpret_cast<char*>(D) + off); };
+
   for (int n = n_begin; n < n_end; ++n) {
     const Dir<C> dr = a.dir[n];
     const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
     const int ox = x0 - (sxp ? NU : 0), oy = y0 - (syp ? NU : 0);
     const C ax = dr.ax, ay = dr.ay, axy = dr.ax + dr.ay;
+    // this direction's upstream cells as byte offsets (register + constant
+    // buffer offset in the sweeps)
+    unsigned ofx[NS], ofy[NS];
+    {
+      const unsigned ub = sxp ? (unsigned)-(int)sizeof(C) : (unsigned)sizeof(C);
+      const unsigned vb = syp ? (unsigned)(-WP * (int)sizeof(C)) : (unsigned)(WP * sizeof(C));
+#pragma unroll
+      for (int s = 0; s < NS; ++s) ofx[s] = cb[s] + ub, ofy[s] = cb[s] + vb;
+    }
     // reflective incoming sides touching this region: column / row to re-copy
     const bool rx_ = sxp ? (a.bc.xlo == BC_REFLECTIVE && ox < 0) : (a.bc.xhi == BC_REFLECTIVE && ox + W > nx);
     const bool ry_ = syp ? (a.bc.ylo == BC_REFLECTIVE && oy < 0) : (a.bc.yhi == BC_REFLECTIVE && oy + W > ny);
@@ -158,7 +176,7 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
     for (int s = 0; s < NS; ++s) {  // the geometry of this direction's signs (set by its fetch)
       sreg[s] = rs[s];
       ireg[s] = gofs[s] >= 0 ? rcp_(axy + sgv[s]) : C(0);
-      if (sidx[s] >= 0) Dinit[sidx[s]] = rd[s];
+      at(Dinit, cb[s]) = rd[s];
     }
     C pin[4];
 #pragma unroll
@@ -167,7 +185,6 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
     __syncthreads();
     C* Dold = Dinit;
     C* Dnew = Dother;
-    const int ux = sxp ? -1 : 1, uy = syp ? -WP : WP;
     auto recopy = [&](C* D) {  // reflective halo = adjacent interior node
       if (rx_)
         for (int ly = tid; ly < W; ly += UNT)
@@ -183,11 +200,7 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
 #pragma unroll
     for (int k = 1; k <= NU; ++k) {
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        if (sidx[s] < 0) continue;
-        const int i = sidx[s];
-        Dnew[i] = (sreg[s] + ax * Dold[i + ux] + ay * Dold[i + uy]) * ireg[s];
-      }
+      for (int s = 0; s < NS; ++s) at(Dnew, cb[s]) = (sreg[s] + ax * at(Dold, ofx[s]) + ay * at(Dold, ofy[s])) * ireg[s];
       __syncthreads();
       if (rx_ || ry_) {
         recopy(Dnew);
@@ -214,8 +227,10 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
         phi_acc[k] += dr.w * stored<T, C>(pn);
       }
     }
-    Dinit = Dnew;  // the buffer without this direction's result
-    Dother = Dold;
+    if (!(NU & 1)) {  // the buffer without this direction's result starts the next one
+      Dinit = Dnew;
+      Dother = Dold;
+    }
   }
   if (MODE == UP_UPDATE) {
     C* ph = a.phi_part + (size_t)chunk * npix;
@@ -367,7 +382,7 @@ inline int grid_for(size_t total, int threads) {
 template <typename T, typename C, int MODE, int NU>
 cudaError_t launch_up_nu(const UpArgs<T, C>& a, int nchunk, cudaStream_t s) {
   constexpr int WP = UT + NU + 2, WS = UT + 2 * NU;
-  const size_t smem = (2 * (size_t)WP * WP + (size_t)WS * WS) * sizeof(C);
+  const size_t smem = (2 * ((size_t)WP * WP + 1) + (size_t)WS * WS) * sizeof(C);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_upwind<T, C, MODE, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
