@@ -471,9 +471,14 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
               for (int k = 0; k < 4; ++k) o[q][m][k] = C(0);
 #pragma unroll
           for (int v = 0; v < 6; ++v) {
-            C kk[4], pp[4];
+            C kk[4], pp[4], pk[4], kp[4];
             ld4(K + (r + v) * W2 + c, kk);
             ld4(Pk + (r + v) * W2 + c, pp);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              pk[k] = pp[k] - c0;
+              kp[k] = kk[k] * pk[k];  // shared by both output rows
+            }
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
               const int tap = v - q;
@@ -481,10 +486,9 @@ __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
               const C w = xg ? M1<C, ORD>(tap) : S1<C, ORD>(tap);
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
-                const C pk = pp[k] - c0;
-                o[q][0][k] += w * kk[k] * pk;
+                o[q][0][k] += w * kp[k];
                 o[q][1][k] += w * kk[k];
-                o[q][2][k] += w * pk;
+                o[q][2][k] += w * pk[k];
               }
             }
           }
