@@ -349,16 +349,18 @@ template <typename T, typename C> struct Impl {
     return a;
   }
 
-  // b for group g from the scalar-flux partials of every group.
-  static cudaError_t source(btmg_problem* P, int g, cudaStream_t s) {
+  // b for group g from the scalar-flux partials of every group; with
+  // want_norm the squared norm of its fixed part (external source and the
+  // other groups' scattering) lands in d_qn2[g] for the relative residual.
+  static cudaError_t source(btmg_problem* P, int g, cudaStream_t s, bool want_norm = true) {
     const size_t npix = P->lev[0].npix();
     cudaError_t e = timed(P, PC_MISC, s, [&] {
       const C* src = P->zero_src ? dptr<C>(P->d_zero_src) : dptr<C>(P->d_src);
       return launch_source<C>(src + g * npix, dptr<C>(P->d_sigs) + (size_t)g * P->G * npix,
                               dptr<C>(P->d_phi_part), P->G, g, P->nchunk, (int)npix, dptr<C>(P->d_b), nullptr,
-                              P->d_qn2_part, P->n_q_blocks, s);
+                              want_norm ? P->d_qn2_part : nullptr, P->n_q_blocks, s);
     });
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !want_norm) return e;
     return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_qn2_part, P->n_q_blocks, P->d_qn2 + g, s); });
   }
 
@@ -603,7 +605,7 @@ template <typename T, typename C> struct Impl {
         return e;
     }
     // 6. fine PG Jacobi sweep with diagonal beta d (Eq. matrix_full)
-    if ((e = homog ? homog_source(P, g, s) : source(P, g, s)) != cudaSuccess) return e;
+    if ((e = homog ? homog_source(P, g, s) : source(P, g, s, false)) != cudaSuccess) return e;
     PgArgs<T, C> j = pg_args(P, g, dptr<T>(P->d_psi_tmp));
     j.psi_out = psi_g;
     j.phi_part = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
@@ -1042,7 +1044,7 @@ template <typename T, typename C> struct RunSmoothPG {
     CK(Impl<T, C>::phi_partials(P, ps, s));
     for (int k = 0; k < sweeps; ++k)
       for (int g = 0; g < P->G; ++g) {
-        CK(Impl<T, C>::source(P, g, s));
+        CK(Impl<T, C>::source(P, g, s, false));
         PgArgs<T, C> j = Impl<T, C>::pg_args(P, g, ps + (size_t)g * L0.n());
         j.psi_out = dptr<T>(P->d_psi_tmp);
         j.phi_part = dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();

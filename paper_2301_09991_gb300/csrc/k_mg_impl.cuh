@@ -324,6 +324,7 @@ __global__ void k_source(const C* __restrict__ src_g, const C* __restrict__ sigs
     if (qfix) qfix[pix] = q;
     acc += (double)q * (double)q;
   }
+  if (!qn2_part) return;  // no norm wanted (uniform over the grid)
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
