@@ -263,3 +263,21 @@ def test_invalid_arguments_return_codes():
     bad = dict(prob, region=np.full((8, 8), 5, dtype=np.int32))
     with pytest.raises(btmg.BtmgError):
         btmg.Problem(bad)
+
+
+@pytest.mark.parametrize("pg", [1, 0])
+def test_multigroup_upscatter_infinite_medium(pg):
+    """Three groups with down- and upscatter, reflective, uniform: the GPU
+    solve (outer passes over the groups) reaches the closed form of the
+    3 x 3 system (diag(sigma_t) - Sigma_s) psi = s."""
+    st = np.array([[1.0, 2.0, 1.5]])
+    ss = np.array([[[0.3, 0.0, 0.2], [0.4, 0.9, 0.0], [0.1, 0.6, 0.8]]])
+    src = np.array([[1.0, 0.5, 0.25]])
+    nx, ny = (16, 8) if pg else (12, 10)
+    prob = I._prob(nx, ny, 8, 8, np.zeros((ny, nx), np.int32), st, ss, src, bc=(1, 1, 1, 1))
+    gp = btmg.Problem(prob, dtype=btmg.F64, pg=pg)
+    psi = gp.zeros()
+    out = gp.solve(psi, rtol=1e-12, max_cycles=200, max_outer=40)
+    exact_g = np.linalg.solve(np.diag(st[0]) - ss[0], src[0])
+    assert out["status"] == btmg.OK, out
+    np.testing.assert_allclose(host(psi), np.broadcast_to(exact_g[:, None, None, None], psi.shape), rtol=1e-9)

@@ -4,7 +4,8 @@ fix (never against the oracle itself).  CPU only.
 P1  filters equal the paper's printed Appendix tables (A.1, A.2, A.3)
 P2  filters are consistent on polynomials (signs and orientation)
 P3  quadrature: closed-form octant area, symmetry, self-convergence (Sec. 2.2)
-P4  infinite medium: psi = s / (sigma_t - sigma_s) is the fixed point
+P4  infinite medium: psi = s / (sigma_t - sigma_s) is the fixed point; with
+    three groups (down- and upscatter) the 3 x 3 system's solution
 P5  upwind mode converges to an independent transport sweep
 P6  frozen-k linear system: MG fixed point equals a dense direct solve
 P7  particle balance of the upwind discretisation
@@ -156,6 +157,28 @@ def test_p4_infinite_medium_closed_form(pg):
     psi, n, rel, _ = op.solve(rtol=1e-13, max_cycles=200)
     assert rel < 1e-12
     np.testing.assert_allclose(psi, exact, rtol=1e-11)
+
+
+@pytest.mark.parametrize("pg", [1, 0])
+def test_p4_multigroup_infinite_medium_closed_form(pg):
+    """Three groups with down- and upscatter ([to][from] matrix), reflective
+    on every side, uniform: the flux is isotropic and constant, and per
+    steradian it solves (diag(sigma_t) - Sigma_s) psi = s, a 3 x 3 system
+    solved here by numpy (R3, R18)."""
+    st = np.array([[1.0, 2.0, 1.5]])
+    ss = np.array([[[0.3, 0.0, 0.2],     # to group 0 from 0, 1, 2 (upscatter from 2)
+                    [0.4, 0.9, 0.0],     # to group 1
+                    [0.1, 0.6, 0.8]]])   # to group 2
+    src = np.array([[1.0, 0.5, 0.25]])
+    nx, ny = (16, 8) if pg else (12, 10)
+    prob = I._prob(nx, ny, 8, 8, np.zeros((ny, nx), np.int32), st, ss, src, bc=(1, 1, 1, 1))
+    op = O.OracleProblem(prob, pg=pg)
+    exact_g = np.linalg.solve(np.diag(st[0]) - ss[0], src[0])
+    exact = np.broadcast_to(exact_g[:, None, None, None], op.shape).copy()
+    assert np.max(np.abs(op.apply(exact))) < 1e-12
+    psi, n, rel, _ = op.solve(rtol=1e-12, max_cycles=200, max_outer=40)
+    assert rel < 1e-11
+    np.testing.assert_allclose(psi, exact, rtol=1e-9)
 
 
 # ---------------------------------------------------------------- P5 -----
