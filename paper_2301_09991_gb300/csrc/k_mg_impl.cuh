@@ -210,15 +210,16 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
       Dold = Dnew;
       Dnew = t;
     }
-    // store the tile: column tx, rows ty + 8k
-    const int tx0 = sxp ? NU : 0, ty0 = syp ? NU : 0;
+    // store the tile: column tx, rows ty + 8k (pofs and pmask give the
+    // global offset of row 0 and the rows inside the domain; the region's
+    // cell of row 0 moves by a constant 8 WP per row block)
+    const unsigned db = (unsigned)((ty + (syp ? NU : 0) + 1) * WP + tx + (sxp ? NU : 0) + 1) * sizeof(C);
+    const size_t nbase = (size_t)n * npix + pofs;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int rx = tx, ry = ty + 8 * k;
-      const int gx = x0 + rx, gy = y0 + ry;
-      if (gx >= nx || gy >= ny) continue;
-      const C d = Dold[(ry + ty0 + 1) * WP + rx + tx0 + 1];
-      const size_t gi = (size_t)n * npix + (size_t)(gy * nx + gx);
+      if (!((pmask >> k) & 1)) continue;
+      const C d = at(Dold, db + (unsigned)(8 * k * WP * sizeof(C)));
+      const size_t gi = nbase + (size_t)(8 * k) * nx;
       if (MODE == UP_CORR) {
         a.delta_out[gi] = d;
       } else {
