@@ -249,6 +249,19 @@ const char* btmg_unet_last_error(void);
  * without the step as CUDA graphs.  The U-net must outlive its use.
  * Errors: INVALID_ARG (null problem, every < 1), OOM.                      */
 int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every);
+/* Particle balance of psi per group for the upwind fine scheme (pg = 0),
+ * whose streaming term telescopes over rows and columns so that a converged
+ * solution balances to its residual level: out[4 g + 0] production
+ * dxdy sum (4 pi s_g + sum_{h != g} sigma_s[g<-h] phi_h), out[4 g + 1]
+ * removal dxdy sum (sigma_t,g - sigma_s[g<-g]) phi_g, out[4 g + 2] net
+ * leakage through the boundary (outgoing boundary values minus the
+ * incoming halo values of Sec. 2.3, weighted p_n |mu_n| dy and
+ * p_n |nu_n| dx), out[4 g + 3] (production - removal - leakage) /
+ * production.  psi: device [G][nd][ny][nx] of psi_dtype; out: host array
+ * of 4 G doubles; FP64 accumulation.  Synchronises the stream.
+ * Errors: INVALID_ARG (NULL argument), UNSUPPORTED (pg = 1), CUDA.         */
+int btmg_particle_balance(btmg_problem* p, const void* psi, double* out, void* stream);
+
 /* The ConvFEM 1D stencils of an order (Sec. 2.7 and the Appendix) as the
  * library derives them: m1 (mass over lumped mass), d1 (advection) and s1
  * (stiffness) at offsets -3..3 (host arrays of 7; taps beyond the order's

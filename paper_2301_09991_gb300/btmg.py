@@ -31,7 +31,7 @@ EXPORTS = (
     "btmg_launch_count", "btmg_apply_operator_noalloc", "btmg_solve_refined",
     "btmg_unet_create", "btmg_unet_destroy", "btmg_unet_num_params", "btmg_unet_get_params",
     "btmg_unet_set_params", "btmg_unet_get_grads", "btmg_unet_forward", "btmg_unet_train_step",
-    "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_scatter_fallbacks", "btmg_convfem_stencils", "btmg_learn_canvas",
+    "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_scatter_fallbacks", "btmg_convfem_stencils", "btmg_particle_balance", "btmg_learn_canvas",
     "btmg_learn_features", "btmg_create_batch", "btmg_destroy_batch", "btmg_batch_problem",
     "btmg_batch_chunks", "btmg_solve_batch", "btmg_wait_selftest", "btmg_fp32_fma_rate",
 )
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = True):
     L.btmg_set_learned.argtypes = [vp, vp, i32]
     L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i32)]
     L.btmg_scatter_fallbacks.argtypes = [vp, C.POINTER(i32)]
+    L.btmg_particle_balance.argtypes = [vp, vp, C.POINTER(C.c_double), vp]
     L.btmg_convfem_stencils.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]
     L.btmg_learn_canvas.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
@@ -336,6 +337,15 @@ class Problem:
         """Attach (or with None detach) a learned correction, see btmg.h."""
         self._unet = unet  # keep the network alive while attached
         _check(load().btmg_set_learned(self.h, unet.h if unet is not None else None, int(every)))
+
+    def particle_balance(self, psi, stream=None):
+        """Per group (production, removal, leakage, relative imbalance) of psi
+        for the upwind fine scheme (btmg_particle_balance); [G][4] array."""
+        self._check_psi(psi)
+        out = np.zeros(4 * self.G)
+        _check(load().btmg_particle_balance(self.h, _ptr(psi), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                            _stream_ptr(stream)))
+        return out.reshape(self.G, 4)
 
     def scatter_fallbacks(self):
         """Solves on this problem that dropped the scattering smoother

@@ -1494,6 +1494,49 @@ template <typename T, typename C> struct RunResidual {
   }
 };
 
+// Particle balance of every group of psi (upwind fine scheme): production,
+// removal, leakage and the relative imbalance, per group (k_balance.cu).
+template <typename T, typename C> struct RunBalance {
+  static int run(btmg_problem* P, const void* psi, double* out, cudaStream_t s) {
+    const T* ps = reinterpret_cast<const T*>(psi);
+    const LevelH& L0 = P->lev[0];
+    const size_t npix = L0.npix();
+    CK(Impl<T, C>::phi_partials(P, ps, s));
+    const int nv = (int)std::min<size_t>(1024, (npix + 255) / 256);
+    const int nl = (int)std::min<size_t>(1024, ((size_t)(L0.nx + L0.ny) * L0.nd + 255) / 256);
+    double* part = nullptr;
+    CK(cudaMalloc(&part, sizeof(double) * 2 * (nv + nl)));
+    std::vector<double> h(2 * (nv + nl));
+    const Bc bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
+    int rc = BTMG_OK;
+    for (int g = 0; g < P->G && rc == BTMG_OK; ++g) {
+      cudaError_t e = launch_balance_volume<C>(dptr<C>(P->d_src) + g * npix, dptr<C>(P->d_sigs) + (size_t)g * P->G * npix,
+                                               dptr<C>(P->d_sig[0]) + g * npix, dptr<C>(P->d_phi_part), P->G, g,
+                                               P->nchunk, (int)npix, part, nv, s);
+      if (e == cudaSuccess)
+        e = launch_balance_leak<T, C>(ps + (size_t)g * L0.n(), reinterpret_cast<const Dir<C>*>(P->d_dir[0]), L0.nx,
+                                      L0.ny, L0.nd, bc, L0.dx, L0.dy, part + 2 * nv, nl, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        rc = fail(BTMG_ERR_CUDA, cudaGetErrorString(e));
+        break;
+      }
+      double prod = 0.0, rem = 0.0, leak = 0.0;
+      for (int b = 0; b < nv; ++b) prod += h[2 * b], rem += h[2 * b + 1];
+      for (int b = 0; b < nl; ++b) leak += h[2 * (nv + b)] + h[2 * (nv + b) + 1];
+      prod *= L0.dx * L0.dy;
+      rem *= L0.dx * L0.dy;
+      out[4 * g + 0] = prod;
+      out[4 * g + 1] = rem;
+      out[4 * g + 2] = leak;
+      out[4 * g + 3] = prod != 0.0 ? (prod - rem - leak) / prod : (prod - rem - leak);
+    }
+    cudaFree(part);
+    return rc;
+  }
+};
+
 // Autotuner cache: problem shape -> (chunks, ms per eager cycle).
 struct TuneKey {
   int nx, ny, nd, G, dtype, pg, nu, scat;
@@ -1933,6 +1976,12 @@ int btmg_set_learned(btmg_problem* p, btmg_unet* unet, int32_t every) {
   p->learn_fallbacks = 0;
   if (p->d_lstat) CK(cudaMemset(p->d_lstat, 0, sizeof(double) * 3));
   return BTMG_OK;
+}
+
+int btmg_particle_balance(btmg_problem* p, const void* psi, double* out, void* stream) {
+  if (!p || !psi || !out) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  if (p->d.pg) return fail(BTMG_ERR_UNSUPPORTED, "the particle balance is that of the upwind fine scheme (pg = 0)");
+  return dispatch<RunBalance>(p->dtype, p, psi, out, (cudaStream_t)stream);
 }
 
 int btmg_convfem_stencils(int32_t order, double* m1, double* d1, double* s1) {

@@ -185,6 +185,15 @@ template <typename C> struct ScatTail {
 };
 template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStream_t s);
 
+// particle balance of one group of an upwind-scheme solution (k_balance.cu):
+// per-block FP64 partials (production, removal) and (x leakage, y leakage)
+template <typename C>
+cudaError_t launch_balance_volume(const C* src_g, const C* sigs_g, const C* sigt_g, const C* phi_part, int G, int g,
+                                  int nchunk, int npix, double* part, int nblocks, cudaStream_t s);
+template <typename T, typename C>
+cudaError_t launch_balance_leak(const T* psi, const Dir<C>* dir, int nx, int ny, int nd, Bc bc, double dx, double dy,
+                                double* part, int nblocks, cudaStream_t s);
+
 template <typename C>
 cudaError_t launch_restrict(const C* fine, C* coarse, const C* rcoef, int nx, int ny, int nr, int nc,
                             int nxc, int nyc, int nrc, int ncc, int fx, int fy, int fr, int fc,

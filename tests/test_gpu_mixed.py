@@ -117,3 +117,9 @@ def test_full_size_mixed_precision_sampled_planes():
     # below ~3e-5 ||q||; the external source of group 0 sets the scale
     for (g, n), r in zip(planes, ref):
         assert np.linalg.norm(r) <= 1e-4 * q0, (g, n, np.linalg.norm(r) / q0)
+    # particle balance of the refined solution on the GPU (FP64, per group):
+    # production = removal + leakage to the residual level
+    g64 = btmg.Problem(prob, dtype=btmg.F64, pg=0)
+    bal = g64.particle_balance(psi64)
+    print("particle balance per group (production, removal, leakage, imbalance):\n", bal)
+    assert np.all(np.abs(bal[:, 3]) < 1e-5)

@@ -281,3 +281,57 @@ def test_multigroup_upscatter_infinite_medium(pg):
     exact_g = np.linalg.solve(np.diag(st[0]) - ss[0], src[0])
     assert out["status"] == btmg.OK, out
     np.testing.assert_allclose(host(psi), np.broadcast_to(exact_g[:, None, None, None], psi.shape), rtol=1e-9)
+
+
+def _balance_reference(op, prob, psi):
+    """Production, removal and leakage of every group written out from the
+    definitions in numpy (phi = sum p psi; outgoing boundary values minus the
+    incoming halo of Sec. 2.3), for comparison with btmg_particle_balance."""
+    lv = op.levels[0]
+    dx, dy, G = lv["dx"], lv["dy"], op.G
+    reg = np.asarray(prob["region"])
+    st = np.asarray(prob["sigma_t"])[reg]          # [ny][nx][G]
+    ss = np.asarray(prob["sigma_s"])[reg]          # [ny][nx][G][G] (to, from)
+    src = np.asarray(prob["source"])[reg]          # [ny][nx][G]
+    bc = prob.get("bc", (0, 0, 0, 0))
+    phi = np.einsum("n,gnyx->gyx", lv["p"], psi)
+    out = []
+    for g in range(G):
+        prod = 4 * np.pi * src[..., g].sum() + sum((ss[..., g, h] * phi[h]).sum() for h in range(G) if h != g)
+        rem = ((st[..., g] - ss[..., g, g]) * phi[g]).sum()
+        leak = 0.0
+        for n in range(lv["nd"]):
+            mu, nu, w = lv["mu"][n], lv["nu"][n], lv["p"][n]
+            xo, xi, vx = (-1, 0, bc[0]) if mu > 0 else (0, -1, bc[1])
+            yo, yi, vy = (-1, 0, bc[2]) if nu > 0 else (0, -1, bc[3])
+            inx = 0.0 if vx == 0 else psi[g, n, :, xi].sum()
+            iny = 0.0 if vy == 0 else psi[g, n, yi, :].sum()
+            leak += w * (abs(mu) * dy * (psi[g, n, :, xo].sum() - inx) + abs(nu) * dx * (psi[g, n, yo, :].sum() - iny))
+        out.append((prod * dx * dy, rem * dx * dy, leak))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("name,mk", [
+    ("two_region", lambda: I.two_region()),
+    ("reflective_33x17", lambda: I.checkerboard(n=33, ny=17, n_polar=4, n_azim=8, blocks=3, seed=13,
+                                                bc=(1, 0, 1, 1))),
+    ("multigroup_24", lambda: I.multigroup(n=24, n_polar=4, n_azim=8, G=3, blocks=3, seed=6)),
+])
+def test_particle_balance_of_converged_solutions(name, mk):
+    """Upwind fine scheme, FP64: the GPU's production, removal and leakage
+    equal the numpy evaluation of their definitions on the same psi, and a
+    converged solution balances to its residual level."""
+    prob = mk()
+    gp = btmg.Problem(prob, dtype=btmg.F64, pg=0)
+    op = O.OracleProblem(prob, pg=0)
+    psi = gp.zeros()
+    out = gp.solve(psi, rtol=1e-11, max_cycles=2000, max_outer=20)
+    assert out["status"] == btmg.OK, out
+    bal = gp.particle_balance(psi)
+    ref = _balance_reference(op, prob, host(psi))
+    np.testing.assert_allclose(bal[:, :3], ref, rtol=1e-11, atol=1e-14 * np.abs(ref).max())
+    print(name, "relative imbalance per group", bal[:, 3])
+    assert np.all(np.abs(bal[:, 3]) < 1e-8)
+    with pytest.raises(btmg.BtmgError) as e:
+        btmg.Problem(prob, dtype=btmg.F64, pg=1).particle_balance(psi)
+    assert e.value.code == btmg.ERR_UNSUPPORTED
