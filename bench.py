@@ -315,9 +315,15 @@ def time_to_residual(btmg, torch, rtol=1e-6):
                                       "512x512 nodes, 32x32 dirs, unit square, c=0.9 (held-out seed)"),
         "thick256_16x32_L30_c0.99": (LN.training_problem(5010, n=256, n_polar=16, n_azim=32, c=0.99, length=30.0),
                                      "256x256 nodes, 16x32 dirs, side 30, c=0.99 (held-out seed)"),
+        # the same regime at full size, refined FP32 with and without the smoother only
+        "thick512_32x32_L30_c0.99": (LN.training_problem(5011, n=512, n_polar=32, n_azim=32, c=0.99, length=30.0),
+                                     "512x512 nodes, 32x32 dirs, side 30, c=0.99 (held-out seed)",
+                                     ("refined_f32", "refined_f32_scatter")),
     }
     out = {}
-    for name, (prob, desc) in cases.items():
+    for name, case in cases.items():
+        prob, desc = case[0], case[1]
+        only = case[2] if len(case) > 2 else None
         row = {"description": desc}
 
         def timed(fn):
@@ -328,21 +334,24 @@ def time_to_residual(btmg, torch, rtol=1e-6):
             torch.cuda.synchronize()
             return r, time.perf_counter() - t0
 
-        gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
-        psi = gp.zeros()
+        if only is None or "plain_f32" in only:
+            gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+            psi = gp.zeros()
 
-        def plain():
-            psi.zero_()
-            return gp.solve(psi, rtol=rtol, max_cycles=600, check_every=10, history=False)
-        r, sec = timed(plain)
-        row["plain_f32"] = {"seconds": round(sec, 4), "cycles": r["cycles"], "rel_resid": r["rel_resid"],
-                            "reached": bool(r["rel_resid"] <= rtol)}
-        del gp, psi
+            def plain():
+                psi.zero_()
+                return gp.solve(psi, rtol=rtol, max_cycles=600, check_every=10, history=False)
+            r, sec = timed(plain)
+            row["plain_f32"] = {"seconds": round(sec, 4), "cycles": r["cycles"], "rel_resid": r["rel_resid"],
+                                "reached": bool(r["rel_resid"] <= rtol)}
+            del gp, psi
         for key, dt, nt, scat, inner in (("refined_f32", btmg.F32, None, 0, 32),
                                          ("refined_bf16", btmg.BF16, None, 0, 32),
                                          ("refined_f32_learned", btmg.F32, net, 0, 32),
                                          ("refined_f32_scatter", btmg.F32, None, 2, 32),
                                          ("refined_bf16_scatter", btmg.BF16, None, 2, 32)):
+            if only is not None and key not in only:
+                continue
             gp = btmg.Problem(prob, dtype=dt, pg=0, scat_levels=scat)
             if nt is not None:
                 gp.set_learned(nt, every=4)
