@@ -374,16 +374,19 @@ int btmg_launch_count(const btmg_problem* p, int64_t* n);
 
 /* Allocation-free residual (no counterpart in the paper).
  *
- * For callers that cannot allocate device memory -- code that runs while
- * someone else captures a CUDA graph, an embedded runtime without a device
- * allocator, or a host program that gives every library a fixed budget and
- * forbids cudaMalloc -- this computes what btmg_apply_operator computes for
- * one group in FP32, r = b - A psi with b = s + sigma_s phi / (4 pi), without
- * a problem handle and without allocating: it calls no cudaMalloc, cudaFree
- * or allocating routine.  Its scratch (scalar flux, source, direction table,
- * norm partial sums) is one file-scope device array of
- * BTMG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
- * the process exits.
+ * For callers that cannot allocate device memory: a host program or
+ * framework that reserves the GPU's memory up front for its own pool and
+ * gives every library a fixed budget (an allocation inside the library would
+ * fail or fragment that pool), a latency-critical loop in which cudaMalloc
+ * and cudaFree, which may synchronise the device, are not acceptable, or an
+ * embedded runtime that lends no device allocator to libraries.  It computes
+ * what btmg_apply_operator computes for one group in FP32,
+ * r = b - A psi with b = s + sigma_s phi / (4 pi), without a problem handle
+ * and without allocating: it calls no cudaMalloc, cudaFree or allocating
+ * routine and copies no host memory to the device.  Its scratch (scalar
+ * flux, source, direction table, error word, norm partial sums) is one
+ * file-scope device array of BTMG_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.
  *   nx, ny, lx, ly, n_polar, n_azim, bc, pg, pg_half: as in btmg_problem_desc
  *     (quadratic ConvFEM; nx*ny <= BTMG_NOALLOC_MAX_NODES and
  *     8*(n_polar/2)*(n_azim/4) <= BTMG_NOALLOC_MAX_DIRS, and the norm
@@ -392,14 +395,20 @@ int btmg_launch_count(const btmg_problem* p, int64_t* n);
  *     returned and nothing is launched);
  *   sigma_t, sigma_s, source: caller-owned device float arrays [ny][nx]
  *     (total, in-group isotropic scattering, isotropic source per node);
- *   psi: caller-owned device float [nd][ny][nx]; r: same shape, output.
+ *   psi: caller-owned device float [nd][ny][nx]; r: same shape, output;
+ *   rel_resid: nullable host pointer.  NULL: the call only enqueues its
+ *     kernels on `stream` and returns.  Non-NULL: it also reduces the norms,
+ *     synchronises `stream`, stores ||r||_W / ||s||_W (W = p_n dx dy, FP64
+ *     sums) and returns BTMG_ERR_TIMEOUT if a bounded wait of the residual
+ *     kernel gave up, in which case r is incomplete.  Only a call with
+ *     rel_resid reports such a timeout; the error word is cleared at the
+ *     start of every call.
  * The first call on a device looks up the device address of the scratch
  * array (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call reuses the same scratch and leaves its contents
  * behind; each call writes all scratch it reads before reading it, so none
  * needs clearing, but calls that overlap on the GPU (concurrent streams)
- * race on it.  The direction table is copied from host stack memory, so the
- * call is ordered on `stream` and returns after that copy was staged.      */
+ * race on it.                                                              */
 #define BTMG_NOALLOC_MAX_NODES (512 * 512)
 #define BTMG_NOALLOC_MAX_DIRS 2048
 #define BTMG_NOALLOC_SCRATCH_BYTES (2359296)
@@ -407,7 +416,7 @@ int btmg_launch_count(const btmg_problem* p, int64_t* n);
 int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, double ly, int32_t n_polar,
                                 int32_t n_azim, const int32_t bc[4], int32_t pg, int32_t pg_half,
                                 const float* sigma_t, const float* sigma_s, const float* source,
-                                const float* psi, float* r, void* stream);
+                                const float* psi, float* r, void* stream, double* rel_resid);
 
 const char* btmg_error_string(int status);
 const char* btmg_last_error(void);

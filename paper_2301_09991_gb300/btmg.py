@@ -116,7 +116,7 @@ def load(build_if_missing: bool = True):
     L.btmg_launch_count.argtypes = [vp, i64p]
     L.btmg_solve_refined.argtypes = [vp, vp, C.c_double, i32, i32, C.POINTER(SolveInfo), vp]
     L.btmg_apply_operator_noalloc.argtypes = [i32, i32, C.c_double, C.c_double, i32, i32,
-                                              C.POINTER(i32), i32, i32, vp, vp, vp, vp, vp, vp]
+                                              C.POINTER(i32), i32, i32, vp, vp, vp, vp, vp, vp, dp]
     L.btmg_set_learned.argtypes = [vp, vp, i32]
     L.btmg_learn_stats.argtypes = [vp, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i32)]
     L.btmg_scatter_fallbacks.argtypes = [vp, C.POINTER(i32)]

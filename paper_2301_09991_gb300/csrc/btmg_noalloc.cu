@@ -1,21 +1,25 @@
 // btmg_noalloc.cu -- an allocation-free form of btmg_apply_operator.
 //
-// Some callers cannot allocate device memory: code running inside a CUDA
-// graph being captured by someone else, an allocator-less embedded runtime,
-// or a host program that owns a fixed device-memory budget and forbids any
-// library from calling cudaMalloc.  btmg_apply_operator_noalloc() serves
-// them: the caller passes every input and output as device pointers, and
-// the scratch the operator needs (scalar flux, assembled source, direction
-// table and the partial sums of the residual norm) lives in one file-scope
-// device array of fixed size, g_scratch below.  Nothing here calls
-// cudaMalloc, cudaFree or any allocating routine.
+// Some callers cannot allocate device memory: a host program or framework
+// that reserves the GPU's memory up front for its own pool and gives every
+// library a fixed budget (a cudaMalloc inside the library would fail or
+// fragment that pool), a latency-critical loop in which cudaMalloc and
+// cudaFree, which may synchronise the device, are not acceptable, or an
+// embedded runtime that lends no device allocator to libraries.
+// btmg_apply_operator_noalloc() serves them: the caller passes every input
+// and output as device pointers, and the scratch the operator needs (scalar
+// flux, assembled source, direction table, error word and the partial sums
+// of the norms) lives in one file-scope device array of fixed size,
+// g_scratch below.  Nothing here calls cudaMalloc, cudaFree or any
+// allocating routine, and no host memory is copied to the device: the
+// direction table is computed by a kernel.
 //
 // The array is part of the library image, so every GPU that loads the
 // library holds it (BTMG_NOALLOC_SCRATCH_BYTES) until the process exits.
 // All calls share it and it keeps the last call's contents; every byte a
-// call reads is written by that same call first, so nothing needs clearing,
-// but two calls that overlap on the GPU (different streams, or the same
-// problem issued concurrently) race on it.
+// call reads is written by that same call first (the error word is cleared
+// at the start of each call), but two calls that overlap on the GPU
+// (different streams) race on it.
 #include <cmath>
 #include <cstdint>
 
@@ -51,65 +55,70 @@ __device__ __align__(256) unsigned char g_scratch[BTMG_NOALLOC_SCRATCH_BYTES];
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_dev[kMaxDevices] = {nullptr};
 
-// Gauss-Legendre points on [0,1] into fixed arrays (Newton on P_n).
-void gauss16(double* x, double* w) {
-  const int n = 16;
-  for (int k = 0; k < n; ++k) {
-    double t = std::cos(3.14159265358979323846 * (4.0 * k + 3.0) / (4.0 * n + 2.0)), dp = 1.0;
+// Octahedral directions (Sec. 2.2) of a level with nr x nc patches per
+// face, in one block: thread i of face 0 integrates its patch's solid angle
+// and first moments with 16 x 16 Gauss-Legendre points of the collapsed map
+// X(u, t) = (1-t)((1-u) a + u b) + t c, whose solid-angle element is
+// (1-t)/|X|^3; the other faces are the sign flips of face 0 (same areas,
+// mirrored moments).  Weights are scaled so that they sum to 4 pi.
+constexpr int kGauss = 16;
+constexpr int kDirThreads = 256;  // >= nr * nc for every accepted size
+__global__ void __launch_bounds__(kDirThreads) k_noalloc_directions(int nr, int nc, double dx, double dy,
+                                                                   Dir<float>* out) {
+  __shared__ double gx[kGauss], gw[kGauss], red[kDirThreads / 32];
+  const int tid = threadIdx.x;
+  if (tid < kGauss) {  // node tid of the 16-point rule: Newton on P_16 from a cosine guess
+    const double pi = 3.14159265358979323846;
+    double t = cos(pi * (4.0 * tid + 3.0) / (4.0 * kGauss + 2.0)), dp = 1.0;
     for (int it = 0; it < 100; ++it) {
       double pm = 0.0, p = 1.0;
-      for (int m = 1; m <= n; ++m) {
+      for (int m = 1; m <= kGauss; ++m) {
         const double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm) / m;
         pm = p;
         p = pn;
       }
-      dp = n * (pm - t * p) / (1.0 - t * t);
+      dp = kGauss * (pm - t * p) / (1.0 - t * t);
       const double step = p / dp;
       t -= step;
-      if (std::fabs(step) < 1e-16) break;
+      if (fabs(step) < 1e-16) break;
     }
-    x[k] = 0.5 * (1.0 + t);
-    w[k] = 1.0 / ((1.0 - t * t) * dp * dp);
+    gx[tid] = 0.5 * (1.0 + t);
+    gw[tid] = 1.0 / ((1.0 - t * t) * dp * dp);
   }
-}
-
-// Octahedral directions (Sec. 2.2) into a fixed table: solid-angle element
-// (1-t)/|X|^3 of the collapsed map X(u,t), weights scaled to sum 4 pi.
-void directions(int nr, int nc, double dx, double dy, Dir<float>* out) {
-  double gx[16], gw[16];
-  gauss16(gx, gw);
-  const int nd = 8 * nr * nc;
-  double total = 0.0;
-  double P[kMaxDirs], MU[kMaxDirs], NU[kMaxDirs];  // on the stack
-  for (int f = 0; f < 8; ++f) {
-    const double sx = (f & 1) ? -1 : 1, sy = (f & 2) ? -1 : 1, sz = (f & 4) ? -1 : 1;
-    for (int j = 0; j < nr; ++j)
-      for (int i = 0; i < nc; ++i) {
-        double area = 0, mx = 0, my = 0;
-        for (int a = 0; a < 16; ++a)
-          for (int b = 0; b < 16; ++b) {
-            const double t = (j + gx[a]) / nr, u = (i + gx[b]) / nc;
-            const double X0 = (1 - t) * (1 - u) * sx, X1 = (1 - t) * u * sy, X2 = t * sz;
-            const double r2 = X0 * X0 + X1 * X1 + X2 * X2, r = std::sqrt(r2);
-            const double dS = gw[a] * gw[b] / (double(nr) * nc) * (1 - t) / (r2 * r);
-            area += dS;
-            mx += dS * X0 / r;
-            my += dS * X1 / r;
-          }
-        const int n = f * nr * nc + j * nc + i;
-        P[n] = area;
-        MU[n] = mx / area;
-        NU[n] = my / area;
-        total += area;
+  __syncthreads();
+  const int q = nr * nc;
+  double area = 0.0, mx = 0.0, my = 0.0;
+  if (tid < q) {
+    const int j = tid / nc, i = tid % nc;
+    for (int a = 0; a < kGauss; ++a)
+      for (int b = 0; b < kGauss; ++b) {
+        const double t = (j + gx[a]) / nr, u = (i + gx[b]) / nc;
+        const double X0 = (1 - t) * (1 - u), X1 = (1 - t) * u, X2 = t;
+        const double r2 = X0 * X0 + X1 * X1 + X2 * X2, r = sqrt(r2);
+        const double dS = gw[a] * gw[b] / (double(nr) * nc) * (1 - t) / (r2 * r);
+        area += dS;
+        mx += dS * X0 / r;
+        my += dS * X1 / r;
       }
   }
-  for (int n = 0; n < nd; ++n) {
-    const double w = P[n] * 4.0 * 3.14159265358979323846 / total;
-    out[n].mu = (float)MU[n];
-    out[n].nu = (float)NU[n];
-    out[n].w = (float)w;
-    out[n].ax = (float)(std::fabs(MU[n]) / dx);
-    out[n].ay = (float)(std::fabs(NU[n]) / dy);
+  double s = area;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((tid & 31) == 0) red[tid >> 5] = s;
+  __syncthreads();
+  double face = 0.0;
+  for (int w = 0; w < kDirThreads / 32; ++w) face += red[w];
+  if (tid >= q) return;
+  const double w = area * 4.0 * 3.14159265358979323846 / (8.0 * face);
+  const double mu = mx / area, nu = my / area;
+  for (int f = 0; f < 8; ++f) {
+    const double sx = (f & 1) ? -1.0 : 1.0, sy = (f & 2) ? -1.0 : 1.0;
+    Dir<float> d;
+    d.mu = (float)(sx * mu);
+    d.nu = (float)(sy * nu);
+    d.w = (float)w;
+    d.ax = (float)(mu / dx);
+    d.ay = (float)(nu / dy);
+    out[f * q + tid] = d;
   }
 }
 
@@ -118,7 +127,7 @@ void directions(int nr, int nc, double dx, double dy, Dir<float>* out) {
 extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, double ly, int32_t n_polar,
                                            int32_t n_azim, const int32_t bc[4], int32_t pg, int32_t pg_half,
                                            const float* sigma_t, const float* sigma_s, const float* source,
-                                           const float* psi, float* r, void* stream) {
+                                           const float* psi, float* r, void* stream, double* rel_resid) {
   if (nx < 1 || ny < 1 || !(lx > 0) || !(ly > 0) || !bc || !sigma_t || !sigma_s || !source || !psi || !r)
     return BTMG_ERR_INVALID_ARG;
   if (n_polar < 2 || n_polar % 2 || n_azim < 4 || n_azim % 4) return BTMG_ERR_INVALID_ARG;
@@ -153,15 +162,16 @@ extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, do
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   const double dx = lx / nx, dy = ly / ny;
-  Dir<float> host_dir[kMaxDirs];  // on the stack; copied before return
-  directions(nr, nc, dx, dy, host_dir);
-  if (cudaMemcpyAsync(dir, host_dir, sizeof(Dir<float>) * nd, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return BTMG_ERR_CUDA;
+  if (nr * nc > kDirThreads) return BTMG_ERR_NOALLOC_TOO_LARGE;
+  k_noalloc_directions<<<1, kDirThreads, 0, s>>>(nr, nc, dx, dy, dir);
+  if (cudaGetLastError() != cudaSuccess) return BTMG_ERR_CUDA;
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return BTMG_ERR_CUDA;
   // scalar flux in one chunk, then b = s + sigma_s phi / (4 pi)
   if (launch_phi_partial<float, float>(psi, phi, dir, nx, ny, nd, nd, 1, s) != cudaSuccess) return BTMG_ERR_CUDA;
   const int npix = nx * ny;
   const int qb = (npix + 255) / 256 < kQBlocks ? (npix + 255) / 256 : kQBlocks;
-  if (launch_source<float>(source, sigma_s, phi, 1, 0, 1, npix, b, nullptr, q_part, qb, s) != cudaSuccess)
+  if (launch_source<float>(source, sigma_s, phi, 1, 0, 1, npix, b, nullptr, rel_resid ? q_part : nullptr, qb, s) !=
+      cudaSuccess)
     return BTMG_ERR_CUDA;
   PgArgs<float, float> a{};
   a.psi = psi;
@@ -192,6 +202,20 @@ extern "C" int btmg_apply_operator_noalloc(int32_t nx, int32_t ny, double lx, do
   a.norm_part = norm_part;
   a.err = err;
   if (launch_pg<float, float>(a, PG_RESID, pg != 0, nchunk, s) != cudaSuccess) return BTMG_ERR_CUDA;
-  if (launch_sum(norm_part, (int)parts(nchunk), sums, s) != cudaSuccess) return BTMG_ERR_CUDA;
+  if (!rel_resid) return BTMG_OK;
+  // ||r||_W / ||s||_W (W = p_n dx dy) from the kernels' partial sums, and
+  // the error word, which a bounded wait that gave up has set
+  if (launch_sum(norm_part, (int)parts(nchunk), sums, s) != cudaSuccess ||
+      launch_sum(q_part, qb, sums + 1, s) != cudaSuccess)
+    return BTMG_ERR_CUDA;
+  double host[2];
+  int host_err = 0;
+  if (cudaMemcpyAsync(host, sums, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return BTMG_ERR_CUDA;
+  if (host_err) return BTMG_ERR_TIMEOUT;
+  const double wq = 4.0 * 3.14159265358979323846 * dx * dy;
+  *rel_resid = host[1] > 0 ? std::sqrt(host[0] / (wq * host[1])) : std::sqrt(host[0]);
   return BTMG_OK;
 }
