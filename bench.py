@@ -55,7 +55,7 @@ WORKLOADS = {
     "checker64": (lambda: I.checkerboard(n=64, n_polar=8, n_azim=16, blocks=8, seed=2, c=0.9),
                   "64x64 nodes, 8x16 dirs (128), small case of the same family"),
 }
-# Algorithmic work per unknown ("Roofline"):
+# Algorithmic work per unknown of the fused PG operator:
 PG_FLOPS_PER_UNKNOWN = 250.0  # separable evaluation of Eq. Petrov + Sec. 2.6 on interior nodes
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 
@@ -195,9 +195,9 @@ def run_reference(args):
         return 0
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
-    # bounded sample: the same checkerboard family on a 128x128 window of the
-    # 256^2 grid (4x4 blocks of 32x32 nodes), all 512 directions
-    prob = I.checkerboard(n=128, n_polar=16, n_azim=32, blocks=4, seed=2, c=0.9)
+    # the full workload of the GPU line (about 2 s per FP64 cycle on 16 host
+    # cores), so both arms time the same configuration
+    prob = WORKLOADS[args.workload][0]()
     op = O.OracleProblem(prob)
     psi = op.zeros()
     N = int(np.prod(op.shape))
@@ -208,12 +208,14 @@ def run_reference(args):
         psi, _, _ = op.mg_cycle(psi)
     dt = time.perf_counter() - t0
     value = N * args.steps / dt
-    sample = ("FP64 oracle cycles on a 128x128-node window (4x4 checkerboard blocks) of the %s "
-              "workload, all 512 directions, %d unknowns per step" % (args.workload, N))
+    sample = ("%d FP64 oracle cycles of the full %s workload (%d unknowns per step), after %d warm-up cycles"
+              % (args.steps, args.workload, N, args.warmup))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload},
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
+                       "unknowns_per_gpu": N},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.omp_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -52,8 +52,9 @@ def reference_flux(prob, rtol=1e-9):
     gp = btmg.Problem(prob, dtype=btmg.F32, pg=0)
     psi64 = torch.zeros(gp.shape, dtype=torch.float64, device="cuda")
     out = gp.solve_refined(psi64, rtol=rtol, max_outer=400, inner_cycles=8)
-    p = torch.tensor(gp.levels[0]["p"], dtype=torch.float64, device="cuda")
-    phi = torch.einsum("n,gnyx->gyx", p, psi64)
+    # phi = sum_n p_n psi_n of the FP64 solution by the library's kernel
+    # (an FP64 problem, whose storage type is the solution's)
+    phi = btmg.Problem(prob, dtype=btmg.F64, pg=0).scalar_flux(psi64)
     return phi, out["rel_resid"]
 
 
