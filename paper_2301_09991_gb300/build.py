@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbtmg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["k_pg.cu", "k_pgd.cu", "k_upres.cu", "k_scat.cu", "k_balance.cu", "k_mg_f64.cu", "k_mg_f32.cu", "k_mg_lp.cu", "btmg_api.cu", "btmg_noalloc.cu", "k_unet.cu"]
+SOURCES = ["k_pg.cu", "k_pg2.cu", "k_pgd.cu", "k_upres.cu", "k_scat.cu", "k_balance.cu", "k_mg_f64.cu", "k_mg_f32.cu", "k_mg_lp.cu", "btmg_api.cu", "btmg_noalloc.cu", "k_unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

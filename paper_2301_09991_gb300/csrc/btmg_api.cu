@@ -1147,6 +1147,7 @@ int auto_chunks(int dtype, bool pg, int tiles, int nd) {
   double best_eff = -1.0;
   for (int c = 1; c <= nd && c <= 64; ++c) {
     if (nd % c) continue;
+    if (dtype == BTMG_F32 && pg && (nd / c) % 2) continue;  // the FP32 PG kernel takes direction pairs
     const double items = (double)tiles * c;
     const double waves = std::ceil(items / slots);
     const double eff = items / (waves * slots);

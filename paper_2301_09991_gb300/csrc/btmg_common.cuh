@@ -119,6 +119,12 @@ template <typename T, typename C>
 cudaError_t launch_pgd(const PgArgs<T, C>& a, int mode, int nchunk, cudaStream_t s);
 // resident CTAs per SM of the PG kernel (for choosing whole-wave grids)
 template <typename T, typename C> int pg_blocks_per_sm(bool pg);
+// FP32 quadratic PG operator on direction pairs (k_pg2.cu): whether it takes
+// these arguments (FP32 rows of a multiple of 4 nodes, even directions per
+// chunk), its occupancy and its launch
+bool pg2_applies(const PgArgs<float, float>& a);
+int pg2_blocks_per_sm();
+cudaError_t launch_pg2(const PgArgs<float, float>& a, int mode, int nchunk, cudaStream_t s);
 template <typename T, typename C>
 cudaError_t launch_upwind(const UpArgs<T, C>& a, int mode, int nchunk, cudaStream_t s);
 

@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "btmg_common.cuh"
 #include "tma.cuh"
@@ -679,6 +680,9 @@ template <typename T, typename C, int MODE, bool PGON> int occupancy_mode() {
 template <typename T, typename C>
 cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cudaStream_t s) {
   if (pg && a.order == 3) return launch_pgd<T, C>(a, mode, nchunk, s);  // cubic: halo 9, direct passes
+  if constexpr (std::is_same<T, float>::value && std::is_same<C, float>::value) {
+    if (pg && pg2_applies(a)) return launch_pg2(a, mode, nchunk, s);  // FP32: direction pairs
+  }
   if (pg)
     return mode == PG_RESID ? launch_mode<T, C, PG_RESID, true>(a, nchunk, s)
                             : launch_mode<T, C, PG_JACOBI, true>(a, nchunk, s);
@@ -686,6 +690,9 @@ cudaError_t launch_pg(const PgArgs<T, C>& a, int mode, bool pg, int nchunk, cuda
 }
 
 template <typename T, typename C> int pg_blocks_per_sm(bool pg) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<C, float>::value) {
+    if (pg) return pg2_blocks_per_sm();
+  }
   return pg ? occupancy_mode<T, C, PG_JACOBI, true>() : upres_blocks_per_sm<T, C>();
 }
 

@@ -65,18 +65,18 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 }
 
 // 3D tensor map over a dense [nz][ny][nx] array of element size es with a
-// box of bx x by x 1 elements; out-of-bounds elements of a box read as 0.
+// box of bx x by x bz elements; out-of-bounds elements of a box read as 0.
 // False when the encoder is unavailable or the base / row stride are not
 // 16-byte multiples (TMA's requirement).
 inline bool encode_tmap_3d(CUtensorMap* m, const void* base, CUtensorMapDataType dt, size_t es, int nx, int ny,
-                           int nz, int bx, int by) {
+                           int nz, int bx, int by, int bz = 1) {
   PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
   if (!encode) return false;
   if ((reinterpret_cast<uintptr_t>(base) % 16) != 0 || ((size_t)nx * es) % 16 != 0 || ((size_t)bx * es) % 16 != 0)
     return false;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
   const cuuint64_t strides[2] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1u};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   return encode(m, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
