@@ -404,6 +404,7 @@ template <typename T, typename C> struct Impl {
     u.tiles_x = (A.nx + kTile - 1) / kTile;
     u.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
     u.dpc = 1;
+    u.err = P->d_err;
     if (l + 1 < P->L) {
       const LevelH& B = P->lev[l + 1];
       u.nxc = B.nx;

@@ -104,6 +104,7 @@ template <typename T, typename C> struct UpArgs {
   int fx, fy, fr, fc;      // coarsening factors to the coarse level (1 or 2)
   int nu, init_mode, dpc, tiles_x;
   Bc bc;
+  int* err;  // set to nonzero when a bounded wait gave up (device word)
 };
 
 // ----------------------------------------------------------- launchers -----

@@ -12,7 +12,11 @@
 //   * UpSamp prolongation, scalar-flux partials, source assembly and a
 //     deterministic FP64 sum.
 #pragma once
+#include <cstring>
+#include <type_traits>
+
 #include "btmg_common.cuh"
+#include "tma.cuh"
 
 namespace btmg {
 namespace {
@@ -243,6 +247,206 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
   }
 }
 
+// Finest-level upwind Jacobi with the update (UP_UPDATE) in streaming form,
+// FP32: no barriers after the set-up.  A warp owns 64 consecutive columns
+// (two per lane) and walks a band of USR rows in the sweep order of the
+// direction, all nu sweep levels at once: level k of a node needs level k-1
+// of its x-upstream neighbour (the lane's other column, or the adjacent
+// lane's by shuffle) and of its y-upstream neighbour (the previous row, kept
+// in registers).  The UH = 4 columns on the x-upwind side (nu <= 4; every
+// window starts on a 16-byte boundary, as TMA needs) and the nu rows before
+// the band are halo: a value there is exact only up to the level of its
+// distance from the window's upwind edge, so the 60 downwind columns and the
+// band's rows are exact after nu levels.
+// Each warp stages by TMA, into two buffers of its own with one mbarrier
+// each, the source over the nu + USR rows, psi over the band and the rows of
+// the coarser correction (UpSamp parents, x coarsened by 2), and sigma_t
+// once over the union of the windows of both sign combinations; the next
+// direction's copies are issued before the warp waits on the current one,
+// so they land while it sweeps.  The chunk's direction table sits in shared
+// memory.  Out-of-domain nodes (zero-filled by the copies) get inverse
+// diagonal 0 and stay 0: the vacuum halo; on a reflective incoming side the
+// boundary node reads its own previous level (the halo copy of the tiled
+// kernel).  The update psi += delta and the scalar-flux partial sums over
+// the chunk's directions are fused into the band's rows.
+constexpr int USR = 8;       // output rows per warp band
+constexpr int US_WARPS = 4;  // warps per CTA
+constexpr int US_W = 64;     // columns of a warp's window
+constexpr int US_UH = 4;     // halo columns
+constexpr int US_CW = US_W / 2 + 4;  // coarse window columns (x coarsened by 2, start rounded down to 4)
+constexpr int US_DMAX = 64;  // directions per chunk (at most 64 chunks of the direction count)
+// staging per warp (floats, each part 128-byte aligned): sigma_t over
+// [USR + 2 nu][64 + UH], then two buffers of source [ROWS][64], psi
+// [USR][64] and coarse correction [ROWS][US_CW]
+template <int NU> struct UsBuf {
+  static constexpr int ROWS = USR + NU;
+  static constexpr int rnd(int v) { return (v + 31) / 32 * 32; }
+  static constexpr int SIGW = US_W + US_UH, SIGH = USR + 2 * NU;
+  static constexpr int SIG = 0, B0 = rnd(SIGH * SIGW);
+  static constexpr int SRC = 0, PSI = rnd(ROWS * US_W), CRS = PSI + rnd(USR * US_W), BUF = CRS + rnd(ROWS * US_CW);
+  static constexpr int WARP = B0 + 2 * BUF;
+};
+struct UsMaps {
+  CUtensorMap src, sig, psi, crs;
+};
+
+template <int NU, bool SXP, bool SYP>
+__device__ __forceinline__ void upstream_tile(const UpArgs<float, float>& a, const Dir<float>& dr, int n, int xw,
+                                              int yb, int lane, const float* sigw, const float* buf, int cx0,
+                                              int cy0, float2 (&phi)[USR]) {
+  constexpr int ROWS = USR + NU;
+  using B = UsBuf<NU>;
+  const int nx = a.nx, ny = a.ny;
+  const size_t npix = (size_t)nx * ny;
+  const int x0 = xw - (SXP ? US_UH : 0), r0 = SYP ? yb - NU : yb;  // window origin
+  const int c0 = x0 + 2 * lane;                                     // this lane's columns c0, c0 + 1
+  const bool cin = c0 >= 0 && c0 < nx;                              // nx even: both or neither
+  float* pout = a.psi_out + (size_t)n * npix;
+  const int shy = a.fy >> 1;
+  const bool rx = SXP ? (a.bc.xlo == BC_REFLECTIVE && c0 == 0) : (a.bc.xhi == BC_REFLECTIVE && c0 + 1 == nx - 1);
+  const int ybnd = SYP ? 0 : ny - 1;
+  const bool ry = SYP ? a.bc.ylo == BC_REFLECTIVE : a.bc.yhi == BC_REFLECTIVE;
+  const bool outl = SXP ? 2 * lane >= US_UH : 2 * lane < US_W - US_UH;
+  const bool crs = a.init_mode == INIT_UPSAMPLE;
+  const int cxl = (c0 >> 1) - cx0;                         // both columns' coarse column
+  const int sgc = c0 - (xw - US_UH);                       // column in the sigma window
+  const float2 ax = make_float2(dr.ax, dr.ax), ay = make_float2(dr.ay, dr.ay);
+  const float axy = dr.ax + dr.ay;
+  float2 prev[NU];
+#pragma unroll
+  for (int k = 0; k < NU; ++k) prev[k] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int it = 0; it < ROWS; ++it) {
+    const int y = SYP ? yb - NU + it : yb + USR - 1 + NU - it;
+    const int ri = y - r0;  // row in the staged window
+    const bool in = cin && y >= 0 && y < ny;
+    const float2 src = *reinterpret_cast<const float2*>(buf + B::SRC + ri * US_W + 2 * lane);
+    const float2 sg = *reinterpret_cast<const float2*>(sigw + (y - (yb - NU)) * B::SIGW + sgc);
+    float2 d = make_float2(0.f, 0.f);
+    if (crs) d.x = d.y = buf[B::CRS + ((y >> shy) - cy0) * US_CW + cxl];
+    const float2 inv = in ? make_float2(rcp_(axy + sg.x), rcp_(axy + sg.y)) : make_float2(0.f, 0.f);
+    const bool ryb = ry && y == ybnd;
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      float2 ux;
+      if (SXP) {
+        ux.x = __shfl_up_sync(0xffffffffu, d.y, 1);
+        if (rx) ux.x = d.x;
+        ux.y = d.x;
+      } else {
+        ux.x = d.y;
+        ux.y = __shfl_down_sync(0xffffffffu, d.x, 1);
+        if (rx) ux.y = d.y;
+      }
+      const float2 uy = ryb ? d : prev[k];
+      prev[k] = d;
+      d = __fmul2_rn(__ffma2_rn(ay, uy, __ffma2_rn(ax, ux, src)), inv);
+    }
+    if (it >= NU) {
+      const int orow = SYP ? it - NU : USR - 1 + NU - it;
+      float2 pv = make_float2(0.f, 0.f);
+      if (in && outl) {
+        const float2 p = *reinterpret_cast<const float2*>(buf + B::PSI + orow * US_W + 2 * lane);
+        const float2 pn = make_float2(p.x + d.x, p.y + d.y);
+        *reinterpret_cast<float2*>(pout + (size_t)y * nx + c0) = pn;
+        pv = make_float2(dr.w * pn.x, dr.w * pn.y);
+      }
+      if (SXP) {  // lane j: columns xw + 2j, xw + 2j + 1
+        pv.x = __shfl_down_sync(0xffffffffu, pv.x, US_UH / 2);
+        pv.y = __shfl_down_sync(0xffffffffu, pv.y, US_UH / 2);
+      }
+      phi[orow].x += pv.x;
+      phi[orow].y += pv.y;
+    }
+  }
+}
+
+template <int NU>
+__global__ void __launch_bounds__(US_WARPS * 32, 3) k_upwind_stream(const UpArgs<float, float> a, int ncg, int nbands,
+                                                                    const __grid_constant__ UsMaps maps) {
+  constexpr int OUTW = US_W - US_UH, ROWS = USR + NU;
+  using B = UsBuf<NU>;
+  extern __shared__ __align__(128) unsigned char us_smem[];
+  __shared__ Dir<float> sdir[US_DMAX];
+  __shared__ int spar[US_DMAX];
+  __shared__ __align__(8) uint64_t sbar[US_WARPS][3];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int chunk = blockIdx.y;
+  const int n_begin = chunk * a.dpc, n_end = min((chunk + 1) * a.dpc, a.nd);
+  const bool crs = a.init_mode == INIT_UPSAMPLE;
+  for (int i = threadIdx.x; i < n_end - n_begin; i += blockDim.x) {
+    sdir[i] = a.dir[n_begin + i];
+    spar[i] = crs ? a.parent[n_begin + i] : 0;
+  }
+  __syncthreads();
+  const int wid = blockIdx.x * US_WARPS + wl;
+  if (wid >= ncg * nbands) return;  // whole warps only: no barrier below
+  const int xw = (wid % ncg) * OUTW, yb = (wid / ncg) * USR;
+  float* wbase = reinterpret_cast<float*>(us_smem) + (size_t)wl * B::WARP;
+  const float* sigw = wbase + B::SIG;
+  float* bufs = wbase + B::B0;
+  uint64_t* bar = sbar[wl];
+  const int shy = a.fy >> 1;
+  const uint32_t bytes = (uint32_t)((ROWS + USR) * US_W * sizeof(float) + (crs ? ROWS * US_CW * sizeof(float) : 0));
+  auto issue = [&](int i, int b) {  // lane 0: direction n_begin + i into buffer b
+    const Dir<float>& dr = sdir[i];
+    const int x0 = xw - (dr.mu > 0.f ? US_UH : 0), r0 = dr.nu > 0.f ? yb - NU : yb;
+    float* dst = bufs + b * B::BUF;
+    mbar_expect_tx(&bar[b], bytes);
+    tma_load_3d(dst + B::SRC, &maps.src, &bar[b], x0, r0, n_begin + i);
+    tma_load_3d(dst + B::PSI, &maps.psi, &bar[b], x0, yb, n_begin + i);
+    if (crs) tma_load_3d(dst + B::CRS, &maps.crs, &bar[b], (x0 >> 1) & ~3, r0 >> shy, spar[i]);
+  };
+  if (lane == 0) {
+    for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
+    mbar_fence_init();
+    mbar_expect_tx(&bar[2], (uint32_t)(B::SIGH * B::SIGW * sizeof(float)));
+    tma_load_3d(wbase + B::SIG, &maps.sig, &bar[2], xw - US_UH, yb - NU, 0);
+    if (n_begin < n_end) issue(0, 0);
+  }
+  __syncwarp();
+  bool ok = mbar_wait_bounded(&bar[2], 0);
+  float2 phi[USR];
+#pragma unroll
+  for (int k = 0; k < USR; ++k) phi[k] = make_float2(0.f, 0.f);
+  uint32_t parity = 0;  // bit b: parity of buffer b's next completion
+  for (int i = 0; ok && i < n_end - n_begin; ++i) {
+    const int b = i & 1;
+    __syncwarp();  // every lane is done with the other buffer (the previous direction)
+    if (lane == 0 && i + 1 < n_end - n_begin) {
+      fence_proxy_async();
+      issue(i + 1, b ^ 1);
+    }
+    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[b], (parity >> b) & 1u));
+    parity ^= 1u << b;
+    if (!ok) {  // copy engine stalled: drain the other copy, then flag and leave
+      if (lane == 0 && i + 1 < n_end - n_begin) mbar_wait_bounded(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u);
+      break;
+    }
+    const Dir<float> dr = sdir[i];
+    const int n = n_begin + i;
+    const int x0 = xw - (dr.mu > 0.f ? US_UH : 0), r0 = dr.nu > 0.f ? yb - NU : yb;
+    const int cx0 = (x0 >> 1) & ~3, cy0 = r0 >> shy;
+    const float* buf = bufs + b * B::BUF;
+    const bool sxp = dr.mu > 0.f, syp = dr.nu > 0.f;
+    if (sxp && syp) upstream_tile<NU, true, true>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
+    else if (sxp) upstream_tile<NU, true, false>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
+    else if (syp) upstream_tile<NU, false, true>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
+    else upstream_tile<NU, false, false>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
+  }
+  if (!ok) {
+    if (lane == 0) atomicExch(a.err, 1);
+    return;
+  }
+  const int col = xw + 2 * lane;
+  if (2 * lane < OUTW && col < a.nx) {
+    float* ph = a.phi_part + (size_t)chunk * a.nx * a.ny;
+#pragma unroll
+    for (int k = 0; k < USR; ++k)
+      if (yb + k < a.ny) *reinterpret_cast<float2*>(ph + (size_t)(yb + k) * a.nx + col) = phi[k];
+  }
+}
+
 template <typename C>
 __global__ void k_restrict(const C* __restrict__ fine, C* __restrict__ coarse, const C* __restrict__ rcoef,
                            int nx, int ny, int nr, int nc, int nxc, int nyc, int nrc, int ncc, int fx, int fy,
@@ -412,10 +616,63 @@ cudaError_t launch_up_mode(const UpArgs<T, C>& a, int nchunk, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+template <int NU>
+cudaError_t launch_up_stream(const UpArgs<float, float>& a, const UsMaps& maps, int nchunk, cudaStream_t s) {
+  constexpr int OUTW = US_W - US_UH;
+  constexpr size_t smem = (size_t)US_WARPS * UsBuf<NU>::WARP * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_upwind_stream<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int ncg = (a.nx + OUTW - 1) / OUTW, nbands = (a.ny + USR - 1) / USR;
+  const int warps = ncg * nbands;
+  dim3 grid((warps + US_WARPS - 1) / US_WARPS, nchunk);
+  k_upwind_stream<NU><<<grid, US_WARPS * 32, smem, s>>>(a, ncg, nbands, maps);
+  return cudaGetLastError();
+}
+
+// Tensor maps of the streaming kernel's windows, or false when the layout
+// does not allow them (rows not 16-byte multiples, unaligned bases, x not
+// coarsened by 2, more than US_DMAX directions per chunk).
+inline bool up_stream_maps(const UpArgs<float, float>& a, UsMaps* m) {
+  const int rows = USR + a.nu;
+  if (a.src_stride != (size_t)a.nx * a.ny || !a.err || a.dpc > US_DMAX || a.nx % 4) return false;
+  if (!encode_tmap_3d(&m->src, a.src, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.nx, a.ny, a.nd, US_W, rows)) return false;
+  if (!encode_tmap_3d(&m->sig, a.sig, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.nx, a.ny, 1, US_W + US_UH, USR + 2 * a.nu))
+    return false;
+  if (!encode_tmap_3d(&m->psi, a.psi_in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.nx, a.ny, a.nd, US_W, USR)) return false;
+  if (a.init_mode == INIT_UPSAMPLE) {
+    if (a.fx != 2) return false;
+    const int ndc = 8 * a.nrc * a.ncc;
+    if (!encode_tmap_3d(&m->crs, a.init, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.nxc, a.nyc, ndc, US_CW, rows))
+      return false;
+  } else if (a.init_mode != INIT_ZERO) {
+    return false;
+  }
+  return true;
+}
+
 }  // namespace
 
+// The finest level's sweeps with the update run in the streaming kernel
+// (FP32 storage, rows of a multiple of 4 nodes, 16-byte aligned buffers);
+// the correction levels and other layouts in the tiled one.
 template <typename T, typename C>
 cudaError_t launch_upwind(const UpArgs<T, C>& a, int mode, int nchunk, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<C, float>::value) {
+    UsMaps maps;
+    memset(&maps, 0, sizeof(maps));
+    if (mode == UP_UPDATE && a.nu <= 4 && up_stream_maps(a, &maps)) {
+      switch (a.nu) {
+        case 1: return launch_up_stream<1>(a, maps, nchunk, s);
+        case 2: return launch_up_stream<2>(a, maps, nchunk, s);
+        case 3: return launch_up_stream<3>(a, maps, nchunk, s);
+        case 4: return launch_up_stream<4>(a, maps, nchunk, s);
+      }
+    }
+  }
   return mode == UP_CORR ? launch_up_mode<T, C, UP_CORR>(a, nchunk, s) : launch_up_mode<T, C, UP_UPDATE>(a, nchunk, s);
 }
 
