@@ -248,16 +248,16 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
 }
 
 // Finest-level upwind Jacobi with the update (UP_UPDATE) in streaming form,
-// FP32: no barriers after the set-up.  A warp owns 64 consecutive columns
+// FP32 compute, psi stored in FP32, BF16 or FP16: no barriers after the set-up.  A warp owns 64 consecutive columns
 // (two per lane) and walks a band of USR rows in the sweep order of the
 // direction, all nu sweep levels at once: level k of a node needs level k-1
 // of its x-upstream neighbour (the lane's other column, or the adjacent
 // lane's by shuffle) and of its y-upstream neighbour (the previous row, kept
-// in registers).  The UH = 4 columns on the x-upwind side (nu <= 4; every
-// window starts on a 16-byte boundary, as TMA needs) and the nu rows before
-// the band are halo: a value there is exact only up to the level of its
-// distance from the window's upwind edge, so the 60 downwind columns and the
-// band's rows are exact after nu levels.
+// in registers).  The UH columns on the x-upwind side (4 for FP32 storage, 8
+// for BF16/FP16, nu <= 4: every window starts on a 16-byte boundary, as TMA
+// needs) and the nu rows before the band are halo: a value there is exact
+// only up to the level of its distance from the window's upwind edge, so the
+// 64 - UH downwind columns and the band's rows are exact after nu levels.
 // Each warp stages by TMA, into two buffers of its own with one mbarrier
 // each, the source over the nu + USR rows, psi over the band and the rows of
 // the coarser correction (UpSamp parents, x coarsened by 2), and sigma_t
@@ -272,44 +272,58 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
 constexpr int USR = 8;       // output rows per warp band
 constexpr int US_WARPS = 4;  // warps per CTA
 constexpr int US_W = 64;     // columns of a warp's window
-constexpr int US_UH = 4;     // halo columns
+template <typename T> constexpr int us_uh() { return sizeof(T) == 2 ? 8 : 4; }  // halo columns
 constexpr int US_CW = US_W / 2 + 4;  // coarse window columns (x coarsened by 2, start rounded down to 4)
 constexpr int US_DMAX = 64;  // directions per chunk (at most 64 chunks of the direction count)
 // staging per warp (floats, each part 128-byte aligned): sigma_t over
 // [USR + 2 nu][64 + UH], then two buffers of source [ROWS][64], psi
-// [USR][64] and coarse correction [ROWS][US_CW]
-template <int NU> struct UsBuf {
-  static constexpr int ROWS = USR + NU;
+// [USR][64] (storage type) and coarse correction [ROWS][US_CW]
+template <typename T, int NU> struct UsBuf {
+  static constexpr int ROWS = USR + NU, UH = us_uh<T>();
   static constexpr int rnd(int v) { return (v + 31) / 32 * 32; }
-  static constexpr int SIGW = US_W + US_UH, SIGH = USR + 2 * NU;
+  static constexpr int SIGW = US_W + UH, SIGH = USR + 2 * NU;
   static constexpr int SIG = 0, B0 = rnd(SIGH * SIGW);
-  static constexpr int SRC = 0, PSI = rnd(ROWS * US_W), CRS = PSI + rnd(USR * US_W), BUF = CRS + rnd(ROWS * US_CW);
-  static constexpr int WARP = B0 + 2 * BUF;
+  static constexpr int SRC = 0, PSI = rnd(ROWS * US_W), CRS = PSI + rnd(USR * US_W * (int)sizeof(T) / 4);
+  static constexpr int BUF = CRS + rnd(ROWS * US_CW), WARP = B0 + 2 * BUF;
 };
+template <typename T> __device__ __forceinline__ float2 ld_pair(const T* p) {
+  if constexpr (sizeof(T) == 4) return *reinterpret_cast<const float2*>(p);
+  else return make_float2(Conv<T>::ld(p), Conv<T>::ld(p + 1));
+}
+template <typename T> __device__ __forceinline__ void st_pair(T* p, float2 v) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float2*>(p) = v;
+  } else {
+    T t[2];
+    Conv<T>::st(&t[0], v.x);
+    Conv<T>::st(&t[1], v.y);
+    *reinterpret_cast<uint32_t*>(p) = *reinterpret_cast<const uint32_t*>(t);
+  }
+}
 struct UsMaps {
   CUtensorMap src, sig, psi, crs;
 };
 
-template <int NU, bool SXP, bool SYP>
-__device__ __forceinline__ void upstream_tile(const UpArgs<float, float>& a, const Dir<float>& dr, int n, int xw,
+template <typename T, int NU, bool SXP, bool SYP>
+__device__ __forceinline__ void upstream_tile(const UpArgs<T, float>& a, const Dir<float>& dr, int n, int xw,
                                               int yb, int lane, const float* sigw, const float* buf, int cx0,
                                               int cy0, float2 (&phi)[USR]) {
-  constexpr int ROWS = USR + NU;
-  using B = UsBuf<NU>;
+  constexpr int ROWS = USR + NU, UH = us_uh<T>();
+  using B = UsBuf<T, NU>;
   const int nx = a.nx, ny = a.ny;
   const size_t npix = (size_t)nx * ny;
-  const int x0 = xw - (SXP ? US_UH : 0), r0 = SYP ? yb - NU : yb;  // window origin
+  const int x0 = xw - (SXP ? UH : 0), r0 = SYP ? yb - NU : yb;  // window origin
   const int c0 = x0 + 2 * lane;                                     // this lane's columns c0, c0 + 1
   const bool cin = c0 >= 0 && c0 < nx;                              // nx even: both or neither
-  float* pout = a.psi_out + (size_t)n * npix;
+  T* pout = a.psi_out + (size_t)n * npix;
   const int shy = a.fy >> 1;
   const bool rx = SXP ? (a.bc.xlo == BC_REFLECTIVE && c0 == 0) : (a.bc.xhi == BC_REFLECTIVE && c0 + 1 == nx - 1);
   const int ybnd = SYP ? 0 : ny - 1;
   const bool ry = SYP ? a.bc.ylo == BC_REFLECTIVE : a.bc.yhi == BC_REFLECTIVE;
-  const bool outl = SXP ? 2 * lane >= US_UH : 2 * lane < US_W - US_UH;
+  const bool outl = SXP ? 2 * lane >= UH : 2 * lane < US_W - UH;
   const bool crs = a.init_mode == INIT_UPSAMPLE;
   const int cxl = (c0 >> 1) - cx0;                         // both columns' coarse column
-  const int sgc = c0 - (xw - US_UH);                       // column in the sigma window
+  const int sgc = c0 - (xw - UH);                          // column in the sigma window
   const float2 ax = make_float2(dr.ax, dr.ax), ay = make_float2(dr.ay, dr.ay);
   const float axy = dr.ax + dr.ay;
   float2 prev[NU];
@@ -340,20 +354,20 @@ __device__ __forceinline__ void upstream_tile(const UpArgs<float, float>& a, con
       }
       const float2 uy = ryb ? d : prev[k];
       prev[k] = d;
-      d = __fmul2_rn(__ffma2_rn(ay, uy, __ffma2_rn(ax, ux, src)), inv);
+      d = __fmul2_rn(__ffma2_rn(ax, ux, __ffma2_rn(ay, uy, src)), inv);  // the shuffle's value last
     }
     if (it >= NU) {
       const int orow = SYP ? it - NU : USR - 1 + NU - it;
       float2 pv = make_float2(0.f, 0.f);
       if (in && outl) {
-        const float2 p = *reinterpret_cast<const float2*>(buf + B::PSI + orow * US_W + 2 * lane);
+        const float2 p = ld_pair(reinterpret_cast<const T*>(buf + B::PSI) + orow * US_W + 2 * lane);
         const float2 pn = make_float2(p.x + d.x, p.y + d.y);
-        *reinterpret_cast<float2*>(pout + (size_t)y * nx + c0) = pn;
-        pv = make_float2(dr.w * pn.x, dr.w * pn.y);
+        st_pair(pout + (size_t)y * nx + c0, pn);
+        pv = make_float2(dr.w * stored<T, float>(pn.x), dr.w * stored<T, float>(pn.y));
       }
       if (SXP) {  // lane j: columns xw + 2j, xw + 2j + 1
-        pv.x = __shfl_down_sync(0xffffffffu, pv.x, US_UH / 2);
-        pv.y = __shfl_down_sync(0xffffffffu, pv.y, US_UH / 2);
+        pv.x = __shfl_down_sync(0xffffffffu, pv.x, UH / 2);
+        pv.y = __shfl_down_sync(0xffffffffu, pv.y, UH / 2);
       }
       phi[orow].x += pv.x;
       phi[orow].y += pv.y;
@@ -361,11 +375,11 @@ __device__ __forceinline__ void upstream_tile(const UpArgs<float, float>& a, con
   }
 }
 
-template <int NU>
-__global__ void __launch_bounds__(US_WARPS * 32, 3) k_upwind_stream(const UpArgs<float, float> a, int ncg, int nbands,
+template <typename T, int NU>
+__global__ void __launch_bounds__(US_WARPS * 32, 3) k_upwind_stream(const UpArgs<T, float> a, int ncg, int nbands,
                                                                     const __grid_constant__ UsMaps maps) {
-  constexpr int OUTW = US_W - US_UH, ROWS = USR + NU;
-  using B = UsBuf<NU>;
+  constexpr int UH = us_uh<T>(), OUTW = US_W - UH, ROWS = USR + NU;
+  using B = UsBuf<T, NU>;
   extern __shared__ __align__(128) unsigned char us_smem[];
   __shared__ Dir<float> sdir[US_DMAX];
   __shared__ int spar[US_DMAX];
@@ -387,10 +401,11 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_upwind_stream(const UpArgs
   float* bufs = wbase + B::B0;
   uint64_t* bar = sbar[wl];
   const int shy = a.fy >> 1;
-  const uint32_t bytes = (uint32_t)((ROWS + USR) * US_W * sizeof(float) + (crs ? ROWS * US_CW * sizeof(float) : 0));
+  const uint32_t bytes =
+      (uint32_t)(ROWS * US_W * sizeof(float) + USR * US_W * sizeof(T) + (crs ? ROWS * US_CW * sizeof(float) : 0));
   auto issue = [&](int i, int b) {  // lane 0: direction n_begin + i into buffer b
     const Dir<float>& dr = sdir[i];
-    const int x0 = xw - (dr.mu > 0.f ? US_UH : 0), r0 = dr.nu > 0.f ? yb - NU : yb;
+    const int x0 = xw - (dr.mu > 0.f ? UH : 0), r0 = dr.nu > 0.f ? yb - NU : yb;
     float* dst = bufs + b * B::BUF;
     mbar_expect_tx(&bar[b], bytes);
     tma_load_3d(dst + B::SRC, &maps.src, &bar[b], x0, r0, n_begin + i);
@@ -401,7 +416,7 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_upwind_stream(const UpArgs
     for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
     mbar_fence_init();
     mbar_expect_tx(&bar[2], (uint32_t)(B::SIGH * B::SIGW * sizeof(float)));
-    tma_load_3d(wbase + B::SIG, &maps.sig, &bar[2], xw - US_UH, yb - NU, 0);
+    tma_load_3d(wbase + B::SIG, &maps.sig, &bar[2], xw - UH, yb - NU, 0);
     if (n_begin < n_end) issue(0, 0);
   }
   __syncwarp();
@@ -425,14 +440,14 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_upwind_stream(const UpArgs
     }
     const Dir<float> dr = sdir[i];
     const int n = n_begin + i;
-    const int x0 = xw - (dr.mu > 0.f ? US_UH : 0), r0 = dr.nu > 0.f ? yb - NU : yb;
+    const int x0 = xw - (dr.mu > 0.f ? UH : 0), r0 = dr.nu > 0.f ? yb - NU : yb;
     const int cx0 = (x0 >> 1) & ~3, cy0 = r0 >> shy;
     const float* buf = bufs + b * B::BUF;
     const bool sxp = dr.mu > 0.f, syp = dr.nu > 0.f;
-    if (sxp && syp) upstream_tile<NU, true, true>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
-    else if (sxp) upstream_tile<NU, true, false>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
-    else if (syp) upstream_tile<NU, false, true>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
-    else upstream_tile<NU, false, false>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
+    if (sxp && syp) upstream_tile<T, NU, true, true>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
+    else if (sxp) upstream_tile<T, NU, true, false>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
+    else if (syp) upstream_tile<T, NU, false, true>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
+    else upstream_tile<T, NU, false, false>(a, dr, n, xw, yb, lane, sigw, buf, cx0, cy0, phi);
   }
   if (!ok) {
     if (lane == 0) atomicExch(a.err, 1);
@@ -616,33 +631,37 @@ cudaError_t launch_up_mode(const UpArgs<T, C>& a, int nchunk, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-template <int NU>
-cudaError_t launch_up_stream(const UpArgs<float, float>& a, const UsMaps& maps, int nchunk, cudaStream_t s) {
-  constexpr int OUTW = US_W - US_UH;
-  constexpr size_t smem = (size_t)US_WARPS * UsBuf<NU>::WARP * sizeof(float);
+template <typename T, int NU>
+cudaError_t launch_up_stream(const UpArgs<T, float>& a, const UsMaps& maps, int nchunk, cudaStream_t s) {
+  constexpr int OUTW = US_W - us_uh<T>();
+  constexpr size_t smem = (size_t)US_WARPS * UsBuf<T, NU>::WARP * sizeof(float);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_upwind_stream<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_upwind_stream<T, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int ncg = (a.nx + OUTW - 1) / OUTW, nbands = (a.ny + USR - 1) / USR;
   const int warps = ncg * nbands;
   dim3 grid((warps + US_WARPS - 1) / US_WARPS, nchunk);
-  k_upwind_stream<NU><<<grid, US_WARPS * 32, smem, s>>>(a, ncg, nbands, maps);
+  k_upwind_stream<T, NU><<<grid, US_WARPS * 32, smem, s>>>(a, ncg, nbands, maps);
   return cudaGetLastError();
 }
 
 // Tensor maps of the streaming kernel's windows, or false when the layout
 // does not allow them (rows not 16-byte multiples, unaligned bases, x not
 // coarsened by 2, more than US_DMAX directions per chunk).
-inline bool up_stream_maps(const UpArgs<float, float>& a, UsMaps* m) {
-  const int rows = USR + a.nu;
+template <typename T> bool up_stream_maps(const UpArgs<T, float>& a, UsMaps* m) {
+  const int rows = USR + a.nu, uh = us_uh<T>();
   if (a.src_stride != (size_t)a.nx * a.ny || !a.err || a.dpc > US_DMAX || a.nx % 4) return false;
+  const CUtensorMapDataType pt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                  : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   if (!encode_tmap_3d(&m->src, a.src, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.nx, a.ny, a.nd, US_W, rows)) return false;
-  if (!encode_tmap_3d(&m->sig, a.sig, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.nx, a.ny, 1, US_W + US_UH, USR + 2 * a.nu))
+  if (!encode_tmap_3d(&m->sig, a.sig, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.nx, a.ny, 1, US_W + uh, USR + 2 * a.nu))
     return false;
-  if (!encode_tmap_3d(&m->psi, a.psi_in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.nx, a.ny, a.nd, US_W, USR)) return false;
+  if (!encode_tmap_3d(&m->psi, a.psi_in, pt, sizeof(T), a.nx, a.ny, a.nd, US_W, USR)) return false;
   if (a.init_mode == INIT_UPSAMPLE) {
     if (a.fx != 2) return false;
     const int ndc = 8 * a.nrc * a.ncc;
@@ -657,19 +676,19 @@ inline bool up_stream_maps(const UpArgs<float, float>& a, UsMaps* m) {
 }  // namespace
 
 // The finest level's sweeps with the update run in the streaming kernel
-// (FP32 storage, rows of a multiple of 4 nodes, 16-byte aligned buffers);
+// (FP32 compute, rows of 16-byte multiples, 16-byte aligned buffers);
 // the correction levels and other layouts in the tiled one.
 template <typename T, typename C>
 cudaError_t launch_upwind(const UpArgs<T, C>& a, int mode, int nchunk, cudaStream_t s) {
-  if constexpr (std::is_same<T, float>::value && std::is_same<C, float>::value) {
+  if constexpr (std::is_same<C, float>::value) {
     UsMaps maps;
     memset(&maps, 0, sizeof(maps));
-    if (mode == UP_UPDATE && a.nu <= 4 && up_stream_maps(a, &maps)) {
+    if (mode == UP_UPDATE && a.nu <= 4 && up_stream_maps<T>(a, &maps)) {
       switch (a.nu) {
-        case 1: return launch_up_stream<1>(a, maps, nchunk, s);
-        case 2: return launch_up_stream<2>(a, maps, nchunk, s);
-        case 3: return launch_up_stream<3>(a, maps, nchunk, s);
-        case 4: return launch_up_stream<4>(a, maps, nchunk, s);
+        case 1: return launch_up_stream<T, 1>(a, maps, nchunk, s);
+        case 2: return launch_up_stream<T, 2>(a, maps, nchunk, s);
+        case 3: return launch_up_stream<T, 3>(a, maps, nchunk, s);
+        case 4: return launch_up_stream<T, 4>(a, maps, nchunk, s);
       }
     }
   }
