@@ -333,13 +333,23 @@ int btmg_wait_selftest(int32_t polls, void* stream);
  *
  * btmg_solve_batch solves every problem i from its caller-owned device
  * psi[i] (layout of btmg_get_layout; initial guess in, solution out): one
- * eager cycle per problem, then each problem's whole cycle (all groups) is
- * captured once as a CUDA graph and one parent graph holds the cycles of all
- * unconverged problems as independent branches (plus the copies of their
- * residual norms to the host), so one graph launch advances every problem by
- * a cycle and small problems run side by side.  Every check_every launches
- * the residuals are read; converged, failed or exhausted problems leave the
- * parent graph, which is then rebuilt.  infos[i] (nullable array, history
+ * eager cycle per problem, then one CUDA graph advances every unconverged
+ * problem by a cycle.  When every problem has one group, FP32 compute
+ * (FP32/BF16/FP16 storage), no scattering smoother and the same nu <= 4, the
+ * graph holds each problem's fine residual (with its source and norm), then
+ * ONE persistent launch that does the coarse correction of all of them (the
+ * restrictions down every level and the nu upwind Jacobi sweeps from the
+ * coarsest level up to level 1, Sec. 2.5): its CTAs drain a device queue of
+ * (problem, level, block) tasks, each waiting, bounded by about a second, for
+ * the previous level of its problem to complete (a wait that gives up makes
+ * the call return BTMG_ERR_TIMEOUT), then each problem's finest sweeps and
+ * PG Jacobi.  With autotune = 1 the persistent launch's sweep tile width (16
+ * or 32 nodes) and grid (1, 2 or 4 CTAs per SM) are chosen by timing 5
+ * launches of each on the first cycle's residuals (CUDA events).  Other
+ * batches hold each problem's whole cycle as an independent branch.  The
+ * graph also copies the residual norms to the host.  Every check_every
+ * launches the residuals are read; converged, failed or exhausted problems
+ * leave the graph, which is then rebuilt.  infos[i] (nullable array, history
  * ignored) receives cycles, status and the FP64 relative residual of the
  * returned psi as btmg_solve.  Returns BTMG_OK when every problem
  * converged, else BTMG_ERR_NOT_CONVERGED (or the first hard error).  Learned
@@ -354,6 +364,10 @@ int btmg_batch_problem(btmg_batch* b, int32_t i, btmg_problem** p);
 /* Chunk count of problem i, the automatic choice for its shape, and the
  * tuned time of one eager cycle in ms (0 when not tuned).                  */
 int btmg_batch_chunks(const btmg_batch* b, int32_t i, int32_t* chunks, int32_t* auto_chunks, double* ms);
+/* Whether the batch's coarse corrections run in the persistent launch, its
+ * sweep tile width, CTAs per SM, and the tuned time of one launch in ms (0
+ * before tuning or without autotune).  Any output may be NULL.            */
+int btmg_batch_coarse(const btmg_batch* b, int32_t* persistent, int32_t* tile, int32_t* ctas, double* ms);
 int btmg_solve_batch(btmg_batch* b, void* const* psi, double rtol, int32_t max_cycles, int32_t check_every,
                      btmg_solve_info* infos, void* stream);
 

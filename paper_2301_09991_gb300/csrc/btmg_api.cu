@@ -513,10 +513,14 @@ template <typename T, typename C> struct Impl {
   // With `homog`, the cycle of the learned correction c (in P->d_lc, its
   // residual in d_s[0]): zero external source, no inner-refinement source,
   // scalar-flux partials in d_lphi, result back in d_lc.
-  static cudaError_t cycle_part_b(btmg_problem* P, T* psi_g, int g, cudaStream_t s, bool homog = false) {
+  // coarse_external: the restrictions and the coarse sweeps (steps 2-4) ran
+  // elsewhere (the persistent batched launch) and d_delta[1] holds their result
+  static cudaError_t cycle_part_b(btmg_problem* P, T* psi_g, int g, cudaStream_t s, bool homog = false,
+                                  bool coarse_external = false) {
     cudaError_t e;
     const int L = P->L;
     const LevelH& L0 = P->lev[0];
+    if (!coarse_external) {
     // the smallest levels run in one single-CTA launch (restrictions and
     // sweeps): the smoother's levels while it is active, else the
     // published cycle's when the smoother is off
@@ -586,6 +590,7 @@ template <typename T, typename C> struct Impl {
           cudaSuccess)
         return e;
     }
+    }  // !coarse_external
     // 4./5. finest level: nu sweeps from UpSamp(delta_2), psi_tmp = psi + delta
     if (P->scat_on[0] && !P->scat_off) {
       C* ph = homog ? dptr<C>(P->d_lphi) : dptr<C>(P->d_phi_part) + (size_t)g * P->nchunk * L0.npix();
@@ -1489,6 +1494,32 @@ template <typename T, typename C> struct RunCapture {
   }
 };
 // relative residual of psi (all groups), FP64 norms
+// The two parts of a one-group cycle around its coarse correction: A = the
+// scalar-flux partials, source, fine residual and its norm; B = the finest
+// level's sweeps from d_delta[1], source and fine PG Jacobi (the batched
+// persistent launch does the levels in between).
+template <typename T, typename C> struct RunCapturePart {
+  static int run(btmg_problem* P, void* psi, int part, cudaStream_t s, cudaGraph_t* g) {
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    T* ps = reinterpret_cast<T*>(psi);
+    cudaError_t e = cudaSuccess;
+    if (part == 0) {
+      e = Impl<T, C>::phi_partials(P, ps, s);
+      if (e == cudaSuccess) e = Impl<T, C>::cycle_part_a(P, ps, 0, s);
+    } else {
+      e = Impl<T, C>::cycle_part_b(P, ps, 0, s, false, true);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      CK(e != cudaSuccess ? e : ee);
+    }
+    *g = graph;
+    return BTMG_OK;
+  }
+};
+
 template <typename T, typename C> struct RunResidual {
   static int run(btmg_problem* P, const void* psi, double* rel, cudaStream_t s) {
     CK(Impl<T, C>::residual_all(P, reinterpret_cast<const T*>(psi), nullptr, s));
@@ -1634,6 +1665,21 @@ struct btmg_batch {
   double* h_res = nullptr;  // pinned: per problem rn2[G], qn2[G]
   int* h_err = nullptr;     // pinned: per problem bounded-wait flag
   std::vector<size_t> res_off;
+  // persistent coarse correction (one-group problems with FP32 compute): the
+  // cycle of every active problem is part A (fine residual), one persistent
+  // launch of every problem's restrictions and coarse sweeps, part B (finest
+  // sweeps and PG Jacobi)
+  bool persist = false;
+  bool autotune = false, tuned = false;
+  int tu = 32, ctas = 2;           // sweep tile width and CTAs per SM of the launch
+  double coarse_ms = 0.0;          // tuned time of one persistent launch
+  std::vector<cudaGraph_t> cycA, cycB;
+  cudaGraph_t coarse = nullptr;    // counter reset + persistent launch, active set
+  void* d_plan = nullptr;          // segments, tasks and arguments of the active set
+  unsigned* d_cnt = nullptr;       // head + done per segment
+  int* d_cerr = nullptr;           // bounded-wait flag of the persistent launch
+  int* h_cerr = nullptr;           // pinned copy
+  size_t cnt_cap = 0, plan_cap = 0;
 };
 
 namespace {
@@ -1642,12 +1688,240 @@ void batch_free(btmg_batch* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   for (cudaGraph_t g : B->cyc)
     if (g) cudaGraphDestroy(g);
+  for (cudaGraph_t g : B->cycA)
+    if (g) cudaGraphDestroy(g);
+  for (cudaGraph_t g : B->cycB)
+    if (g) cudaGraphDestroy(g);
+  if (B->coarse) cudaGraphDestroy(B->coarse);
+  if (B->d_plan) cudaFree(B->d_plan);
+  if (B->d_cnt) cudaFree(B->d_cnt);
+  if (B->d_cerr) cudaFree(B->d_cerr);
+  if (B->h_cerr) cudaFreeHost(B->h_cerr);
   for (btmg_problem* P : B->probs) destroy(P);
   if (B->h_res) cudaFreeHost(B->h_res);
   if (B->h_err) cudaFreeHost(B->h_err);
   if (B->order) cudaEventDestroy(B->order);
   if (B->bs) cudaStreamDestroy(B->bs);
   delete B;
+}
+
+// The coarse correction of a one-group problem as segments of the persistent
+// batched launch, in the order of cycle_part_b: the restrictions down every
+// level (Sec. 2.5), then the nu upwind Jacobi sweeps from the coarsest level
+// up to level 1 (Eq. matrix_full, beta = 1; UpSamp of the coarser level's
+// correction), each segment waiting for the one before it.  FP32 compute.
+void coarse_plan(btmg_problem* P, int tu, std::vector<CoarseSeg>& segs, std::vector<CoarseRestrict>& ra,
+                 std::vector<UpArgs<float, float>>& ua) {
+  const int L = P->L;
+  int prev = -1;
+  for (int l = 0; l + 1 < L; ++l) {
+    const LevelH &A = P->lev[l], &B = P->lev[l + 1];
+    ra.push_back(CoarseRestrict{dptr<float>(P->d_s[l]), dptr<float>(P->d_s[l + 1]), dptr<float>(P->d_rcoef[l]), A.nx,
+                                A.ny, A.nr, A.nc, B.nx, B.ny, B.nr, B.nc, A.fx, A.fy, A.fr, A.fc});
+    segs.push_back(CoarseSeg{0, (int)ra.size() - 1, (int)((B.n() + kCoarseCells - 1) / kCoarseCells), prev, 0});
+    prev = (int)segs.size() - 1;
+  }
+  for (int l = L - 1; l >= 1; --l) {
+    const LevelH& A = P->lev[l];
+    UpArgs<float, float> u{};
+    u.sig = dptr<float>(P->d_sig[l]);
+    u.dir = reinterpret_cast<const Dir<float>*>(P->d_dir[l]);
+    u.nx = A.nx;
+    u.ny = A.ny;
+    u.nr = A.nr;
+    u.nc = A.nc;
+    u.nd = A.nd;
+    u.nu = P->d.nu_jacobi;
+    u.src_stride = A.npix();
+    u.tiles_x = (A.nx + tu - 1) / tu;
+    u.bc = Bc{P->d.bc[0], P->d.bc[1], P->d.bc[2], P->d.bc[3]};
+    u.dpc = 1;
+    u.err = P->d_err;
+    u.src = dptr<float>(P->d_s[l]);
+    u.delta_out = dptr<float>(P->d_delta[l]);
+    u.init_mode = l == L - 1 ? INIT_ZERO : INIT_UPSAMPLE;
+    if (l + 1 < L) {
+      const LevelH& B = P->lev[l + 1];
+      u.init = dptr<float>(P->d_delta[l + 1]);
+      u.nxc = B.nx;
+      u.nyc = B.ny;
+      u.nrc = B.nr;
+      u.ncc = B.nc;
+      u.fx = A.fx;
+      u.fy = A.fy;
+      u.fr = A.fr;
+      u.fc = A.fc;
+      u.parent = reinterpret_cast<const int*>(P->d_parent[l]);
+    }
+    ua.push_back(u);
+    const int tiles = u.tiles_x * ((A.ny + tu - 1) / tu);
+    segs.push_back(CoarseSeg{1, (int)ua.size() - 1, tiles * A.nd, prev, tiles});
+    prev = (int)segs.size() - 1;
+  }
+}
+
+// Builds (on B->bs, by stream capture) the graph of one persistent coarse
+// launch over the active problems with tile width tu and ctas CTAs per SM:
+// the task plan is uploaded, the counters and the error word are zeroed,
+// then the kernel drains the queue.  Tasks are ordered by the index of their
+// segment inside its problem's chain, then by problem and block, so every
+// prerequisite precedes its dependents.
+int coarse_graph(btmg_batch* B, const std::vector<int>& active, int tu, int ctas, cudaGraph_t* out) {
+  std::vector<CoarseSeg> segs;
+  std::vector<CoarseRestrict> ra;
+  std::vector<UpArgs<float, float>> ua;
+  std::vector<int> first(active.size() + 1, 0);
+  for (size_t k = 0; k < active.size(); ++k) {
+    first[k] = (int)segs.size();
+    coarse_plan(B->probs[active[k]], tu, segs, ra, ua);
+  }
+  first[active.size()] = (int)segs.size();
+  std::vector<int2> tasks;
+  for (int stage = 0;; ++stage) {
+    bool any = false;
+    for (size_t k = 0; k < active.size(); ++k) {
+      const int sg = first[k] + stage;
+      if (sg >= first[k + 1]) continue;
+      any = true;
+      for (int b = 0; b < segs[sg].blocks; ++b) tasks.push_back(make_int2(sg, b));
+    }
+    if (!any) break;
+  }
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t o_task = al(segs.size() * sizeof(CoarseSeg)), o_ra = o_task + al(tasks.size() * sizeof(int2));
+  const size_t o_ua = o_ra + al(ra.size() * sizeof(CoarseRestrict)), bytes = o_ua + al(ua.size() * sizeof(UpArgs<float, float>));
+  if (bytes > B->plan_cap) {
+    if (B->d_plan) cudaFree(B->d_plan);
+    B->d_plan = nullptr;
+    B->plan_cap = 0;
+    if (cudaMalloc(&B->d_plan, bytes) != cudaSuccess) return fail(BTMG_ERR_OOM, "batch plan");
+    B->plan_cap = bytes;
+  }
+  if (1 + segs.size() > B->cnt_cap) {
+    if (B->d_cnt) cudaFree(B->d_cnt);
+    B->d_cnt = nullptr;
+    B->cnt_cap = 0;
+    if (cudaMalloc(&B->d_cnt, (1 + segs.size()) * sizeof(unsigned)) != cudaSuccess)
+      return fail(BTMG_ERR_OOM, "batch counters");
+    B->cnt_cap = 1 + segs.size();
+  }
+  char* base = static_cast<char*>(B->d_plan);
+  std::vector<char> host(bytes, 0);
+  memcpy(host.data(), segs.data(), segs.size() * sizeof(CoarseSeg));
+  memcpy(host.data() + o_task, tasks.data(), tasks.size() * sizeof(int2));
+  memcpy(host.data() + o_ra, ra.data(), ra.size() * sizeof(CoarseRestrict));
+  memcpy(host.data() + o_ua, ua.data(), ua.size() * sizeof(UpArgs<float, float>));
+  CK(cudaMemcpyAsync(B->d_plan, host.data(), bytes, cudaMemcpyHostToDevice, B->bs));
+  CK(cudaStreamSynchronize(B->bs));
+  CoarseBatch cb{};
+  cb.seg = reinterpret_cast<const CoarseSeg*>(base);
+  cb.task = reinterpret_cast<const int2*>(base + o_task);
+  cb.ntasks = (int)tasks.size();
+  cb.ra = reinterpret_cast<const CoarseRestrict*>(base + o_ra);
+  cb.ua = reinterpret_cast<const UpArgs<float, float>*>(base + o_ua);
+  cb.head = B->d_cnt;
+  cb.done = B->d_cnt + 1;
+  cb.err = B->d_cerr;
+  const int nu = B->probs[active[0]]->d.nu_jacobi;
+  CK(cudaStreamBeginCapture(B->bs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(B->d_cnt, 0, (1 + segs.size()) * sizeof(unsigned), B->bs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_cerr, 0, sizeof(int), B->bs);
+  if (e == cudaSuccess && cb.ntasks > 0) e = launch_coarse_batch(cb, nu, tu, ctas, B->bs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(B->bs, &g);
+  if (e != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    CK(e != cudaSuccess ? e : ee);
+  }
+  *out = g;
+  return BTMG_OK;
+}
+
+// The tile width and grid of the persistent launch, timed: each candidate's
+// graph runs 2 warm-up and 5 timed times (CUDA events on B->bs) on the
+// current restricted residuals (the launch only rewrites the coarse levels,
+// which the next cycle recomputes); the fastest is kept.
+int coarse_tune(btmg_batch* B, const std::vector<int>& active) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int best_tu = B->tu, best_ctas = B->ctas;
+  for (int tu : {16, 32})
+    for (int ctas : {1, 2, 4}) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t x = nullptr;
+      if (int rc = coarse_graph(B, active, tu, ctas, &g)) return rc;
+      cudaError_t e = cudaGraphInstantiate(&x, g, 0);
+      cudaGraphDestroy(g);
+      CK(e);
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaGraphLaunch(x, B->bs);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, B->bs);
+      for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaGraphLaunch(x, B->bs);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, B->bs);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      cudaGraphExecDestroy(x);
+      CK(e);
+      if (ms / 5 < best) {
+        best = ms / 5;
+        best_tu = tu;
+        best_ctas = ctas;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B->tu = best_tu;
+  B->ctas = best_ctas;
+  B->coarse_ms = best;
+  B->tuned = true;
+  return BTMG_OK;
+}
+
+// persistent form of the parent graph: every active problem's part A, then
+// the persistent coarse launch of all of them, then every problem's part B
+// followed by the copies of its residual norms and error flag
+int batch_build_persistent(btmg_batch* B, const std::vector<int>& active) {
+  if (B->coarse) cudaGraphDestroy(B->coarse);
+  B->coarse = nullptr;
+  if (int rc = coarse_graph(B, active, B->tu, B->ctas, &B->coarse)) return rc;
+  cudaGraph_t parent = nullptr;
+  CK(cudaGraphCreate(&parent, 0));
+  std::vector<cudaGraphNode_t> as;
+  cudaError_t e = cudaSuccess;
+  for (int i : active) {
+    cudaGraphNode_t a;
+    if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&a, parent, nullptr, 0, B->cycA[i]);
+    as.push_back(a);
+  }
+  cudaGraphNode_t cn, cm;
+  if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&cn, parent, as.data(), as.size(), B->coarse);
+  if (e == cudaSuccess)
+    e = cudaGraphAddMemcpyNode1D(&cm, parent, &cn, 1, B->h_cerr, B->d_cerr, sizeof(int), cudaMemcpyDeviceToHost);
+  for (int i : active) {
+    btmg_problem* P = B->probs[i];
+    cudaGraphNode_t child, m0, m1, m2;
+    if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, parent, &cn, 1, B->cycB[i]);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&m0, parent, &child, 1, B->h_res + B->res_off[i], P->d_rn2,
+                                   sizeof(double) * P->G, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&m1, parent, &child, 1, B->h_res + B->res_off[i] + P->G, P->d_qn2,
+                                   sizeof(double) * P->G, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&m2, parent, &child, 1, B->h_err + i, P->d_err, sizeof(int),
+                                   cudaMemcpyDeviceToHost);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(parent);
+    CK(e);
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&B->exec, parent, 0);
+  cudaGraphDestroy(parent);
+  CK(ei);
+  B->exec_set = active;
+  return BTMG_OK;
 }
 
 // parent graph: one child-graph branch per active problem, each followed by
@@ -1711,6 +1985,26 @@ int solve_batch(btmg_batch* B, void* const* psi, double rtol, int max_cycles, in
     cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
   }
+  if (B->persist) {  // the two parts of every cycle, and the launch's tuning
+    for (int i = 0; i < n; ++i) {
+      btmg_problem* P = B->probs[i];
+      if (!B->cycA[i] || recaptured) {
+        for (cudaGraph_t* gp : {&B->cycA[i], &B->cycB[i]}) {
+          if (*gp) cudaGraphDestroy(*gp);
+          *gp = nullptr;
+        }
+        if (int rc = dispatch<RunCapturePart>(P->dtype, P, psi[i], 0, B->bs, &B->cycA[i])) return rc;
+        if (int rc = dispatch<RunCapturePart>(P->dtype, P, psi[i], 1, B->bs, &B->cycB[i])) return rc;
+      }
+    }
+    if (B->autotune && !B->tuned) {
+      std::vector<int> all(n);
+      for (int i = 0; i < n; ++i) all[i] = i;
+      if (int rc = coarse_tune(B, all)) return rc;
+      if (B->exec) cudaGraphExecDestroy(B->exec);
+      B->exec = nullptr;
+    }
+  }
   const double pi4 = 4.0 * kPi;
   for (;;) {
     std::vector<int> active;
@@ -1722,10 +2016,13 @@ int solve_batch(btmg_batch* B, void* const* psi, double rtol, int max_cycles, in
       }
     if (active.empty()) break;
     if (!B->exec || active != B->exec_set) {
-      if (int rc = batch_build(B, active)) return rc;
+      if (B->exec) cudaGraphExecDestroy(B->exec);
+      B->exec = nullptr;
+      if (int rc = B->persist ? batch_build_persistent(B, active) : batch_build(B, active)) return rc;
     }
     for (int j = 0; j < k; ++j) CK(cudaGraphLaunch(B->exec, B->bs));
     CK(cudaStreamSynchronize(B->bs));
+    if (B->persist && *B->h_cerr) return fail(BTMG_ERR_TIMEOUT, "a bounded device wait gave up (persistent launch)");
     for (int i : active) {
       btmg_problem* P = B->probs[i];
       cycles[i] += k;
@@ -2177,12 +2474,28 @@ int btmg_create_batch(const btmg_problem_desc* descs, int32_t n, int32_t autotun
     }
     B->cyc.assign(n, nullptr);
     B->cyc_psi.assign(n, nullptr);
+    B->cycA.assign(n, nullptr);
+    B->cycB.assign(n, nullptr);
     if (cudaMallocHost(&B->h_res, sizeof(double) * off) != cudaSuccess ||
         cudaMallocHost(&B->h_err, sizeof(int) * n) != cudaSuccess) {
       batch_free(B);
       return fail(BTMG_ERR_OOM, "batch pinned buffers");
     }
     std::memset(B->h_err, 0, sizeof(int) * n);
+    // the persistent coarse launch: one-group problems with FP32 compute and
+    // the published correction sweeps, the same sweep count throughout
+    B->persist = true;
+    B->autotune = autotune != 0;
+    for (btmg_problem* P : B->probs)
+      if (P->f64 || P->G != 1 || P->d.scat_levels != 0 || P->d.nu_jacobi != B->probs[0]->d.nu_jacobi ||
+          !coarse_batch_supported(P->d.nu_jacobi, 32))
+        B->persist = false;
+    if (B->persist && (cudaMalloc(&B->d_cerr, sizeof(int)) != cudaSuccess ||
+                       cudaMallocHost(&B->h_cerr, sizeof(int)) != cudaSuccess)) {
+      batch_free(B);
+      return fail(BTMG_ERR_OOM, "batch error word");
+    }
+    if (B->persist) *B->h_cerr = 0;
   } catch (...) {
     batch_free(B);
     return fail(BTMG_ERR_OOM, "host allocation failed");
@@ -2200,6 +2513,15 @@ int btmg_destroy_batch(btmg_batch* b) {
 int btmg_batch_problem(btmg_batch* b, int32_t i, btmg_problem** p) {
   if (!b || !p || i < 0 || i >= (int)b->probs.size()) return fail(BTMG_ERR_INVALID_ARG, "bad batch index");
   *p = b->probs[i];
+  return BTMG_OK;
+}
+
+int btmg_batch_coarse(const btmg_batch* b, int32_t* persistent, int32_t* tile, int32_t* ctas, double* ms) {
+  if (!b) return fail(BTMG_ERR_INVALID_ARG, "null batch");
+  if (persistent) *persistent = b->persist ? 1 : 0;
+  if (tile) *tile = b->tu;
+  if (ctas) *ctas = b->ctas;
+  if (ms) *ms = b->coarse_ms;
   return BTMG_OK;
 }
 

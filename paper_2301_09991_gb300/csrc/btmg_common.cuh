@@ -192,6 +192,39 @@ template <typename C> struct ScatTail {
 };
 template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStream_t s);
 
+// Batched coarse correction in one persistent launch (k_mg_impl.cuh): the
+// restrictions and the upwind Jacobi sweeps of every level below the finest
+// of every problem of a batch, as a queue of (segment, block) tasks.  A
+// segment is one level's restriction or sweep of one problem; a task waits
+// (bounded) until the previous segment of its problem is complete.  FP32.
+struct CoarseRestrict {
+  const float* fine;
+  float* coarse;
+  const float* rcoef;
+  int nx, ny, nr, nc, nxc, nyc, nrc, ncc, fx, fy, fr, fc;
+};
+struct CoarseSeg {
+  int type;    // 0 restriction, 1 upwind sweeps (UP_CORR)
+  int arg;     // index into the restriction or sweep arguments
+  int blocks;  // tasks of the segment
+  int prev;    // segment of the same problem that must be complete first (-1: none)
+  int tiles;   // sweeps: tiles of the level (task = tile + tiles * direction)
+};
+struct CoarseBatch {
+  const CoarseSeg* seg;
+  const int2* task;  // (segment, block) in an order where every prerequisite comes first
+  int ntasks;
+  const CoarseRestrict* ra;
+  const UpArgs<float, float>* ua;
+  unsigned* head;  // next task to take (zero before each launch)
+  unsigned* done;  // finished tasks per segment (zero before each launch)
+  int* err;        // set to nonzero when a bounded wait gave up
+};
+constexpr int kCoarseCells = 2048;  // coarse cells per restriction task
+// sweeps per level nu (1..4) and tile width tu (16 or 32); ctas: CTAs per SM
+bool coarse_batch_supported(int nu, int tu);
+cudaError_t launch_coarse_batch(const CoarseBatch& cb, int nu, int tu, int ctas, cudaStream_t s);
+
 // particle balance of one group of an upwind-scheme solution (k_balance.cu):
 // per-block FP64 partials (production, removal) and (x leakage, y leakage)
 template <typename C>

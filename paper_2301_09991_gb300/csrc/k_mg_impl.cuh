@@ -39,13 +39,23 @@ constexpr int UT = 32, UNT = 256, NUMAX = 8;
 // FP32: the fast reciprocal (2 ulp, the Jacobi diagonal tolerates it); FP64: exact
 __device__ __forceinline__ float rcp_(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ double rcp_(double v) { return 1.0 / v; }
-template <typename T, typename C, int MODE, int NU>
-__global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
-  constexpr int W = UT + NU;        // loaded region (tile + NU upwind nodes)
+// shared bytes of one tile of width TU with NU sweeps (two sweep buffers
+// with their zero ring and spare cell, and the sigma region)
+template <typename C, int NU, int TU> constexpr size_t upwind_smem() {
+  return (2 * ((size_t)(TU + NU + 2) * (TU + NU + 2) + 1) + (size_t)(TU + 2 * NU) * (TU + 2 * NU)) * sizeof(C);
+}
+// One TU x TU tile (tile index `tile` of a grid tiles_x wide) and direction
+// chunk `chunk` of the nu-sweep upwind Jacobi, by the 256 threads of a CTA;
+// smem_raw holds upwind_smem<C, NU, TU>() bytes.
+template <typename T, typename C, int MODE, int NU, int TU>
+__device__ __forceinline__ void upwind_tile(const UpArgs<T, C>& a, const int tile, const int chunk,
+                                            unsigned char* smem_raw) {
+  static_assert(TU * TU % UNT == 0 && UNT % TU == 0, "tile rows per thread");
+  constexpr int RPT = TU * TU / UNT, RSTEP = UNT / TU;  // tile rows per thread, row step
+  constexpr int W = TU + NU;        // loaded region (tile + NU upwind nodes)
   constexpr int WP = W + 2;         // stride with the zero ring
-  constexpr int WS = UT + 2 * NU;   // sigma region covering both upwind sides
+  constexpr int WS = TU + 2 * NU;   // sigma region covering both upwind sides
   constexpr int NS = (W * W + UNT - 1) / UNT;  // region cells per thread
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   // two sweep buffers, each followed by one spare cell that the unused
   // slots of the last thread row read and write (no per-cell tests)
   constexpr int DB = WP * WP + 1;
@@ -53,9 +63,8 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
   C* D1 = D0 + DB;
   C* SG = D1 + DB;
 
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int tile = blockIdx.x, chunk = blockIdx.y;
-  const int x0 = (tile % a.tiles_x) * UT, y0 = (tile / a.tiles_x) * UT;
+  const int tid = threadIdx.x, tx = tid % TU, ty = tid / TU;
+  const int x0 = (tile % a.tiles_x) * TU, y0 = (tile / a.tiles_x) * TU;
   const int nx = a.nx, ny = a.ny;
   const size_t npix = (size_t)nx * ny;
 
@@ -99,22 +108,22 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
     combo = cmb;
   };
 
-  C phi_acc[4];
+  C phi_acc[RPT];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) phi_acc[k] = C(0);
+  for (int k = 0; k < RPT; ++k) phi_acc[k] = C(0);
 
   const int n_begin = chunk * a.dpc;
   const int n_end = min(n_begin + a.dpc, a.nd);
 
   // registers holding the next direction's inputs
-  C rs[NS], rd[NS], rp[4];
-  // this thread's tile nodes (column tx, rows ty + 8k): offset of row 0 and
-  // the rows inside the domain
+  C rs[NS], rd[NS], rp[RPT];
+  // this thread's tile nodes (column tx, rows ty + RSTEP k): offset of row 0
+  // and the rows inside the domain
   const int pofs = (y0 + ty) * nx + x0 + tx;
   int pmask = 0;
 #pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (x0 + tx < nx && y0 + ty + 8 * k < ny) pmask |= 1 << k;
+  for (int k = 0; k < RPT; ++k)
+    if (x0 + tx < nx && y0 + ty + RSTEP * k < ny) pmask |= 1 << k;
   auto fetch = [&](int n) {
     const Dir<C> dr = a.dir[n];
     const int cmb = (dr.mu > C(0) ? 1 : 0) | (dr.nu > C(0) ? 2 : 0);
@@ -138,7 +147,7 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
     if (MODE == UP_UPDATE) {
       const T* pin_n = a.psi_in + (size_t)n * npix + pofs;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) rp[k] = (pmask >> k) & 1 ? (C)Conv<T>::ld(pin_n + 8 * k * nx) : C(0);
+      for (int k = 0; k < RPT; ++k) rp[k] = (pmask >> k) & 1 ? (C)Conv<T>::ld(pin_n + RSTEP * k * nx) : C(0);
     }
   };
 
@@ -182,9 +191,9 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
       ireg[s] = gofs[s] >= 0 ? rcp_(axy + sgv[s]) : C(0);
       at(Dinit, cb[s]) = rd[s];
     }
-    C pin[4];
+    C pin[RPT];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) pin[k] = rp[k];
+    for (int k = 0; k < RPT; ++k) pin[k] = rp[k];
     if (n + 1 < n_end) fetch(n + 1);  // in flight during the sweeps
     __syncthreads();
     C* Dold = Dinit;
@@ -214,16 +223,16 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
       Dold = Dnew;
       Dnew = t;
     }
-    // store the tile: column tx, rows ty + 8k (pofs and pmask give the
+    // store the tile: column tx, rows ty + RSTEP k (pofs and pmask give the
     // global offset of row 0 and the rows inside the domain; the region's
-    // cell of row 0 moves by a constant 8 WP per row block)
+    // cell of row 0 moves by a constant RSTEP WP per row block)
     const unsigned db = (unsigned)((ty + (syp ? NU : 0) + 1) * WP + tx + (sxp ? NU : 0) + 1) * sizeof(C);
     const size_t nbase = (size_t)n * npix + pofs;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < RPT; ++k) {
       if (!((pmask >> k) & 1)) continue;
-      const C d = at(Dold, db + (unsigned)(8 * k * WP * sizeof(C)));
-      const size_t gi = nbase + (size_t)(8 * k) * nx;
+      const C d = at(Dold, db + (unsigned)(RSTEP * k * WP * sizeof(C)));
+      const size_t gi = nbase + (size_t)(RSTEP * k) * nx;
       if (MODE == UP_CORR) {
         a.delta_out[gi] = d;
       } else {
@@ -240,11 +249,17 @@ __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
   if (MODE == UP_UPDATE) {
     C* ph = a.phi_part + (size_t)chunk * npix;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int gx = x0 + tx, gy = y0 + ty + 8 * k;
+    for (int k = 0; k < RPT; ++k) {
+      const int gx = x0 + tx, gy = y0 + ty + RSTEP * k;
       if (gx < nx && gy < ny) ph[(size_t)gy * nx + gx] = phi_acc[k];
     }
   }
+}
+
+template <typename T, typename C, int MODE, int NU>
+__global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  upwind_tile<T, C, MODE, NU, UT>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // Finest-level upwind Jacobi with the update (UP_UPDATE) in streaming form,
@@ -462,12 +477,14 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_upwind_stream(const UpArgs
   }
 }
 
+// Coarse cells [id0, id1) of the restriction fine -> coarse (Sec. 2.5),
+// strided over the CTA's threads starting at `first` with step `stride`.
 template <typename C>
-__global__ void k_restrict(const C* __restrict__ fine, C* __restrict__ coarse, const C* __restrict__ rcoef,
-                           int nx, int ny, int nr, int nc, int nxc, int nyc, int nrc, int ncc, int fx, int fy,
-                           int fr, int fc) {
-  const size_t total = (size_t)8 * nrc * ncc * nyc * nxc;
-  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void restrict_cells(const C* __restrict__ fine, C* __restrict__ coarse,
+                                               const C* __restrict__ rcoef, int nx, int ny, int nr, int nc, int nxc,
+                                               int nyc, int nrc, int ncc, int fx, int fy, int fr, int fc,
+                                               size_t first, size_t stride, size_t id1) {
+  for (size_t id = first; id < id1; id += stride) {
     const int X = id % nxc;
     const int Y = (id / nxc) % nyc;
     const int N = id / ((size_t)nxc * nyc);
@@ -494,6 +511,78 @@ __global__ void k_restrict(const C* __restrict__ fine, C* __restrict__ coarse, c
     }
     coarse[id] = acc;
   }
+}
+
+// Persistent batched coarse correction: each CTA takes (segment, block)
+// tasks from a global counter until the queue is empty; before a task, its
+// thread 0 waits (bounded, about a second) until the previous segment of the
+// same problem has all its blocks finished, and after the task it publishes
+// the block (fence, then counter).  The queue lists every prerequisite
+// before its dependents, so the tasks a CTA waits on were taken earlier by
+// running CTAs: no deadlock whatever the grid.  A wait that gives up sets
+// the error word and ends the CTA.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+template <int NU, int TU>
+__global__ void __launch_bounds__(UNT) k_coarse_batch(const CoarseBatch cb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task, s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int t = (int)atomicAdd(cb.head, 1u);
+      int ok = 1;
+      if (t < cb.ntasks) {
+        const int prev = cb.seg[cb.task[t].x].prev;
+        if (prev >= 0) {
+          const unsigned need = (unsigned)cb.seg[prev].blocks;
+          for (int it = 0; ld_acquire(cb.done + prev) < need; ++it) {
+            if (it >= (1 << 22)) {
+              ok = 0;
+              break;
+            }
+            __nanosleep(256);
+          }
+        }
+      }
+      s_task = t;
+      s_ok = ok;
+    }
+    __syncthreads();
+    const int t = s_task;
+    if (t >= cb.ntasks) return;
+    if (!s_ok) {
+      if (threadIdx.x == 0) atomicExch(cb.err, 1);
+      return;
+    }
+    const int2 tk = cb.task[t];
+    const CoarseSeg sg = cb.seg[tk.x];
+    if (sg.type == 0) {
+      const CoarseRestrict& r = cb.ra[sg.arg];
+      const size_t total = (size_t)8 * r.nrc * r.ncc * r.nyc * r.nxc;
+      const size_t id0 = (size_t)tk.y * kCoarseCells, id1 = min(total, id0 + (size_t)kCoarseCells);
+      restrict_cells<float>(r.fine, r.coarse, r.rcoef, r.nx, r.ny, r.nr, r.nc, r.nxc, r.nyc, r.nrc, r.ncc, r.fx, r.fy,
+                            r.fr, r.fc, id0 + threadIdx.x, blockDim.x, id1);
+    } else {
+      upwind_tile<float, float, UP_CORR, NU, TU>(cb.ua[sg.arg], tk.y % sg.tiles, tk.y / sg.tiles, smem_raw);
+    }
+    __syncthreads();  // the block's writes precede its publication
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(cb.done + tk.x, 1u);
+    }
+  }
+}
+
+template <typename C>
+__global__ void k_restrict(const C* __restrict__ fine, C* __restrict__ coarse, const C* __restrict__ rcoef,
+                           int nx, int ny, int nr, int nc, int nxc, int nyc, int nrc, int ncc, int fx, int fy,
+                           int fr, int fc) {
+  const size_t total = (size_t)8 * nrc * ncc * nyc * nxc;
+  restrict_cells<C>(fine, coarse, rcoef, nx, ny, nr, nc, nxc, nyc, nrc, ncc, fx, fy, fr, fc,
+                    blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x, total);
 }
 
 template <typename C>
@@ -1001,6 +1090,28 @@ cudaError_t launch_refine_update(double* psi64, const T* delta, double inv_alpha
 }
 
 #ifdef BTMG_MG_DEFINE_COMMON
+namespace {
+template <int NU, int TU>
+cudaError_t launch_cb(const CoarseBatch& cb, int ctas, cudaStream_t s) {
+  constexpr size_t smem = upwind_smem<float, NU, TU>();
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_coarse_batch<NU, TU><<<sms * ctas, UNT, smem, s>>>(cb);
+  return cudaGetLastError();
+}
+}  // namespace
+bool coarse_batch_supported(int nu, int tu) { return nu >= 1 && nu <= 4 && (tu == 16 || tu == 32); }
+cudaError_t launch_coarse_batch(const CoarseBatch& cb, int nu, int tu, int ctas, cudaStream_t s) {
+  const bool t32 = tu == 32;
+  switch (nu) {
+    case 1: return t32 ? launch_cb<1, 32>(cb, ctas, s) : launch_cb<1, 16>(cb, ctas, s);
+    case 2: return t32 ? launch_cb<2, 32>(cb, ctas, s) : launch_cb<2, 16>(cb, ctas, s);
+    case 3: return t32 ? launch_cb<3, 32>(cb, ctas, s) : launch_cb<3, 16>(cb, ctas, s);
+    case 4: return t32 ? launch_cb<4, 32>(cb, ctas, s) : launch_cb<4, 16>(cb, ctas, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s) {
   k_sum<<<1, 1024, 0, s>>>(part, n, out);
   return cudaGetLastError();
