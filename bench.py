@@ -445,14 +445,15 @@ def multigroup_pg(btmg, torch, prob, cycles):
             "kernel_share": {k: round(v[0] / tot, 4) for k, v in prof.items()}}
 
 
-def batched(btmg, torch, cycles=4):
+def batched(btmg, torch, cycles=4, probs=None, label=None):
     """Batched workload: 64 independent one-group Voronoi problems (seed 4),
     N uniform over the multiples of 16 in [64, 512], direction grids uniform
     over {8x16, 16x16, 16x32, 32x32}, PG on, FP32.  Throughput of `cycles`
-    cycles of btmg_solve_batch (autotuned chunks; one eager cycle, graph
-    cycles, final residuals) against the same cycles run problem by problem
-    (btmg_solve, graph path)."""
-    probs = I.batch()
+    cycles of btmg_solve_batch (autotuned chunks, the coarse corrections of
+    all problems in one persistent launch with an autotuned tile width and
+    grid; one eager cycle, graph cycles, final residuals) against the same
+    cycles run problem by problem (btmg_solve, graph path)."""
+    probs = I.batch() if probs is None else probs
     N = sum(p["nx"] * p["ny"] * p["n_polar"] * p["n_azim"] for p in probs)
     t0 = time.perf_counter()
     b = btmg.Batch(probs, dtype=btmg.F32, pg=1, autotune=True)
@@ -466,6 +467,7 @@ def batched(btmg, torch, cycles=4):
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     chunks = [b.chunks(i) for i in range(len(probs))]
+    persistent, tile, ctas, coarse_ms = b.coarse()
     b.close()
     del psis, b
     torch.cuda.empty_cache()
@@ -481,8 +483,10 @@ def batched(btmg, torch, cycles=4):
     t_seq = time.perf_counter() - t0
     del gps, xs
     torch.cuda.empty_cache()
-    return {"workload": "64 Voronoi problems, N in 64..512 (step 16), dirs in {8x16,16x16,16x32,32x32}, "
-                        "seed 4, PG on, FP32",
+    return {"workload": label or ("64 Voronoi problems, N in 64..512 (step 16), dirs in {8x16,16x16,16x32,32x32}, "
+                                  "seed 4, PG on, FP32"),
+            "problems": len(probs), "persistent_coarse": {"used": persistent, "tile": tile, "ctas_per_sm": ctas,
+                                                          "ms_per_launch": round(coarse_ms, 4)},
             "unknowns": N, "cycles": cycles, "value": N * cycles / t_batch, "unit": UNIT,
             "seconds": round(t_batch, 4), "sequential_value": N * cycles / t_seq,
             "sequential_seconds": round(t_seq, 4), "autotune_seconds": round(t_tune, 2),
@@ -626,6 +630,11 @@ def main():
         del psi, gp, hpsi
         torch.cuda.empty_cache()
         line["batched"] = batched(btmg, torch)
+        # many small problems: the coarse levels are latency-bound
+        small = I.batch(count=256, seed=44, n_lo=32, n_hi=128, step=16, grids=((4, 8), (8, 8), (8, 16)))
+        line["batched_small"] = batched(btmg, torch, cycles=8, probs=small,
+                                        label="256 Voronoi problems, N in 32..128 (step 16), dirs in {4x8,8x8,8x16}, "
+                                              "seed 44, PG on, FP32")
         line["multigroup"] = multigroup(btmg, torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)

@@ -368,6 +368,11 @@ int btmg_batch_chunks(const btmg_batch* b, int32_t i, int32_t* chunks, int32_t* 
  * sweep tile width, CTAs per SM, and the tuned time of one launch in ms (0
  * before tuning or without autotune).  Any output may be NULL.            */
 int btmg_batch_coarse(const btmg_batch* b, int32_t* persistent, int32_t* tile, int32_t* ctas, double* ms);
+/* Failure-path self-test of the persistent launch (no counterpart in the
+ * paper): a queue of one task whose prerequisite never completes; its wait
+ * gives up after about a second, sets the launch's error word and the CTA
+ * ends.  Returns BTMG_ERR_TIMEOUT (the expected outcome), OOM or CUDA.    */
+int btmg_batch_wait_selftest(void* stream);
 int btmg_solve_batch(btmg_batch* b, void* const* psi, double rtol, int32_t max_cycles, int32_t check_every,
                      btmg_solve_info* infos, void* stream);
 

@@ -33,7 +33,7 @@ EXPORTS = (
     "btmg_unet_set_params", "btmg_unet_get_grads", "btmg_unet_forward", "btmg_unet_train_step",
     "btmg_unet_last_error", "btmg_set_learned", "btmg_learn_stats", "btmg_scatter_fallbacks", "btmg_convfem_stencils", "btmg_particle_balance", "btmg_learn_canvas",
     "btmg_learn_features", "btmg_create_batch", "btmg_destroy_batch", "btmg_batch_problem",
-    "btmg_batch_chunks", "btmg_batch_coarse", "btmg_solve_batch", "btmg_wait_selftest", "btmg_fp32_fma_rate",
+    "btmg_batch_chunks", "btmg_batch_coarse", "btmg_batch_wait_selftest", "btmg_solve_batch", "btmg_wait_selftest", "btmg_fp32_fma_rate",
 )
 LEARN_FEATURES = 4  # input channels of the learned correction
 PROF_CLASSES = ("pg_residual", "pg_jacobi", "upwind_fine", "upwind_coarse", "restrict", "misc")
@@ -132,6 +132,7 @@ def load(build_if_missing: bool = True):
     L.btmg_batch_problem.argtypes = [vp, i32, C.POINTER(vp)]
     L.btmg_batch_chunks.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), dp]
     L.btmg_batch_coarse.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), dp]
+    L.btmg_batch_wait_selftest.argtypes = [vp]
     L.btmg_solve_batch.argtypes = [vp, C.POINTER(vp), C.c_double, i32, i32, C.POINTER(SolveInfo), vp]
     L.btmg_unet_create.argtypes = [i32, C.c_uint64, C.POINTER(vp)]
     L.btmg_unet_destroy.argtypes = [vp]

@@ -2516,6 +2516,24 @@ int btmg_batch_problem(btmg_batch* b, int32_t i, btmg_problem** p) {
   return BTMG_OK;
 }
 
+int btmg_batch_wait_selftest(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws = nullptr;
+  int* err = nullptr;
+  if (cudaMalloc(&ws, kCoarseWaitTestBytes) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    if (ws) cudaFree(ws);
+    return fail(BTMG_ERR_OOM, "self-test workspace");
+  }
+  int h = 0;
+  cudaError_t e = launch_coarse_wait_selftest(ws, err, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(ws);
+  cudaFree(err);
+  CK(e);
+  return h ? fail(BTMG_ERR_TIMEOUT, "bounded wait of the persistent launch gave up (self-test)") : BTMG_OK;
+}
+
 int btmg_batch_coarse(const btmg_batch* b, int32_t* persistent, int32_t* tile, int32_t* ctas, double* ms) {
   if (!b) return fail(BTMG_ERR_INVALID_ARG, "null batch");
   if (persistent) *persistent = b->persist ? 1 : 0;

@@ -224,6 +224,8 @@ constexpr int kCoarseCells = 2048;  // coarse cells per restriction task
 // sweeps per level nu (1..4) and tile width tu (16 or 32); ctas: CTAs per SM
 bool coarse_batch_supported(int nu, int tu);
 cudaError_t launch_coarse_batch(const CoarseBatch& cb, int nu, int tu, int ctas, cudaStream_t s);
+constexpr size_t kCoarseWaitTestBytes = 1024;
+cudaError_t launch_coarse_wait_selftest(void* ws, int* err, cudaStream_t s);
 
 // particle balance of one group of an upwind-scheme solution (k_balance.cu):
 // per-block FP64 partials (production, removal) and (x leakage, y leakage)

@@ -1101,6 +1101,31 @@ cudaError_t launch_cb(const CoarseBatch& cb, int ctas, cudaStream_t s) {
 }
 }  // namespace
 bool coarse_batch_supported(int nu, int tu) { return nu >= 1 && nu <= 4 && (tu == 16 || tu == 32); }
+// The persistent launch's bounded wait on purpose: one task whose
+// prerequisite segment has no task in the queue, so its counter never
+// reaches the segment's block count; the wait gives up and sets *cb.err.
+// ws: device workspace of kCoarseWaitTestBytes bytes.
+cudaError_t launch_coarse_wait_selftest(void* ws, int* err, cudaStream_t s) {
+  char* b = static_cast<char*>(ws);
+  CoarseSeg segs[2] = {{0, 0, 1, -1, 0}, {0, 0, 1, 0, 0}};
+  const int2 task = make_int2(1, 0);
+  cudaError_t e = cudaMemcpyAsync(b, segs, sizeof(segs), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b + 256, &task, sizeof(task), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b + 512, 0, 3 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  CoarseBatch cb{};
+  cb.seg = reinterpret_cast<const CoarseSeg*>(b);
+  cb.task = reinterpret_cast<const int2*>(b + 256);
+  cb.ntasks = 1;
+  cb.ra = nullptr;  // never reached: the only task gives up before its body
+  cb.ua = nullptr;
+  cb.head = reinterpret_cast<unsigned*>(b + 512);
+  cb.done = cb.head + 1;
+  cb.err = err;
+  k_coarse_batch<3, 32><<<1, UNT, upwind_smem<float, 3, 32>(), s>>>(cb);
+  return cudaGetLastError();
+}
 cudaError_t launch_coarse_batch(const CoarseBatch& cb, int nu, int tu, int ctas, cudaStream_t s) {
   const bool t32 = tu == 32;
   switch (nu) {

@@ -62,6 +62,30 @@ def test_batch_matches_individual_cycles_bitwise(pg):
         assert abs(info["rel_resid"] - r) <= 1e-5 * max(r, 1e-30), (info, r)
 
 
+def test_persistent_coarse_launch_is_used_and_matches_single_cycles_bf16():
+    """Batches of one-group FP32-compute problems run their coarse
+    corrections in the persistent launch; with BF16 storage every member
+    still equals its own cycles bit for bit; autotuning picks a tile width
+    of 16 or 32 and 1, 2 or 4 CTAs per SM."""
+    probs = _mixed(seed=6, count=6)
+    b = btmg.Batch(probs, dtype=btmg.BF16, pg=0, autotune=True)
+    psis = b.zeros()
+    rc, infos = b.solve(psis, rtol=0.0, max_cycles=5, check_every=5)
+    persistent, tile, ctas, ms = b.coarse()
+    assert persistent and tile in (16, 32) and ctas in (1, 2, 4) and ms > 0, (persistent, tile, ctas, ms)
+    for i, (prob, info) in enumerate(zip(probs, infos)):
+        gp = btmg.Problem(prob, dtype=btmg.BF16, pg=0, chunks=b.chunks(i)[0])
+        psi = gp.zeros()
+        for _ in range(info["cycles"]):
+            gp.mg_cycle(psi, want_residual=False)
+        torch.cuda.synchronize()
+        assert torch.equal(psi, psis[i]), (i, info)
+    # FP64 and multigroup batches keep a whole cycle per graph branch
+    assert not btmg.Batch(probs[:2], dtype=btmg.F64, pg=0).coarse()[0]
+    assert not btmg.Batch([I.multigroup(n=24, n_polar=4, n_azim=8, G=2, blocks=3, seed=7)],
+                          dtype=btmg.F32, pg=0).coarse()[0]
+
+
 def test_batch_f64_member_matches_oracle_solve():
     probs = [I.voronoi(24, 4, 8, 77), I.voronoi(40, 8, 8, 78), I.two_region(nx=20, ny=28)]
     b = btmg.Batch(probs, dtype=btmg.F64, pg=0)
