@@ -192,9 +192,42 @@ def load_net(path):
     return net
 
 
+# multiply-adds per canvas pixel of one U-net forward: the 3x3 convolutions
+# cin x cout at full (1), 1/4, 1/16 and 1/64 of the pixels (encoder 16-16,
+# 16-32 | 32-32, 32-48 | 48-48, 48-64 | 64-64; decoder 112-48 at 1/16, 80-32
+# at 1/4, 48-16 at 1) and the 1x1 output layer 16-16
+UNET_MACS_PER_PIXEL = (9 * (16 * 16 + 16 * 16) + 9 * (16 * 32 + 32 * 32) // 4 + 9 * (32 * 48 + 48 * 48) // 16
+                       + 9 * (48 * 64 + 64 * 64) // 64 + 9 * 112 * 48 // 16 + 9 * 80 * 32 // 4 + 9 * 48 * 16
+                       + 16 * 16)
+
+
+def forward_timing(net, reps=20):
+    """CUDA-event time of U-net forwards (BF16 tensor-core convolutions) for
+    the learned step's canvas (one 64 x 64 image) and for batches of 32
+    images of 64 x 64 and 256 x 256, with the achieved tensor rate."""
+    import torch
+    out = []
+    for n, hw in ((1, 64), (32, 64), (32, 256)):
+        x = torch.randn((n, hw, hw, btmg.LEARN_FEATURES), dtype=torch.float32, device="cuda")
+        net.forward(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            net.forward(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        flops = 2.0 * UNET_MACS_PER_PIXEL * n * hw * hw
+        out.append(dict(images=n, canvas=hw, ms=round(ms, 4), gflop=round(flops / 1e9, 3),
+                        tflops=round(flops / ms / 1e9, 2)))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["train", "eval"])
+    ap.add_argument("cmd", choices=["train", "eval", "timing"])
+    ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--out", default="learned_unet.npy")
     ap.add_argument("--weights", default=None)
     ap.add_argument("--mix", default="64:200,128:60,256:30",
@@ -202,7 +235,11 @@ def main():
     ap.add_argument("--steps", type=int, default=4000)
     args = ap.parse_args()
     log = lambda m: print(m, flush=True)
-    if args.cmd == "train":
+    if args.cmd == "timing":
+        net = load_net(args.weights) if args.weights else btmg.UNet(in_channels=btmg.LEARN_FEATURES, seed=1)
+        for row in forward_timing(net, args.reps):
+            print(json.dumps(row), flush=True)
+    elif args.cmd == "train":
         t0 = time.time()
         plan, seed = [], 1000
         for item in args.mix.split(","):
