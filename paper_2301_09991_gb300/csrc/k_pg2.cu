@@ -368,9 +368,9 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
       });
       __syncthreads();
     }
-    // ---- stage 3a: T = m1_y Psi (rows -2..33) -------------------------------
+    // ---- stage 3a: T = m1_y Psi (rows -2..33), three-row items -------------
     {
-      constexpr int NT3 = (HT / 2) * (WP / 4);  // per array
+      constexpr int NT3 = (HT / 3) * (WP / 4);  // per array
       constexpr int NT3P = (NT3 + 7) / 8 * 8;
 #pragma unroll 1
       for (int it = tid; it < 2 * NT3P; it += NT) {
@@ -378,23 +378,25 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
         const int j = isx ? it : it - NT3P;
         if (j >= NT3) continue;
         int rb, q;
-        split_item<WP / 4 - 8>(j, HT / 2, rb, q);
-        const int r = rb * 2;  // T rows r, r+1 from Psi rows r .. r+5
+        split_item<WP / 4 - 8>(j, HT / 3, rb, q);
+        const int r = rb * 3;  // T rows r .. r+2 from Psi rows r .. r+6
         const float* src = isx ? Px : Py;
         float* dst = isx ? Tx : Ty;
-        float2 s0[4], s1[4];
+        float2 s0[4], s1[4], s2[4];
 #pragma unroll
-        for (int v = 0; v < 6; ++v) {
+        for (int v = 0; v < 7; ++v) {
           float2 p[4];
           ld_run<WP, 2>(src, r + v, 2 * q, p);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if (v < 5) s0[k] = v == 0 ? mul2(f2(M1(0)), p[k]) : fma2(f2(M1(v)), p[k], s0[k]);
-            if (v > 0) s1[k] = v == 1 ? mul2(f2(M1(0)), p[k]) : fma2(f2(M1(v - 1)), p[k], s1[k]);
+            if (v > 0 && v < 6) s1[k] = v == 1 ? mul2(f2(M1(0)), p[k]) : fma2(f2(M1(v - 1)), p[k], s1[k]);
+            if (v > 1) s2[k] = v == 2 ? mul2(f2(M1(0)), p[k]) : fma2(f2(M1(v - 2)), p[k], s2[k]);
           }
         }
         st_quad<WP>(dst, r, q, s0);
         st_quad<WP>(dst, r + 1, q, s1);
+        st_quad<WP>(dst, r + 2, q, s2);
       }
     }
     __syncthreads();
@@ -453,13 +455,13 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
     // on tile rows 0..31, columns -2..33; items of two rows and four nodes
     // (six K and Pk rows in)
     {
-      constexpr int N4 = (HU / 2) * (WK / 4);  // per group
-#pragma unroll 1
-      for (int it = tid; it < 2 * N4; it += NT) {
-        const bool xg = it < N4;
-        int rb, q;
-        split_item<WK / 4 - 8>(xg ? it : it - N4, HU / 2, rb, q);
-        const int r = rb * 2;
+      // two-row items over quads 0..7 of both groups: exactly one per thread
+      static_assert((HU / 2) * 8 * 2 == NT && WK / 4 == 9, "stage-4 item mapping");
+      {
+        const int it = tid;
+        const bool xg = it < 128;
+        const int j = it & 127;
+        const int r = (j >> 3) * 2, q = j & 7;
         const float* K = xg ? Kx : Ky;
         float2 a0[4], a1[4], b0[4], b1[4];  // rows r and r+1 of the two sums
 #pragma unroll
@@ -488,6 +490,25 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
         st_quad<WK>(dA, r + 1, q, a1);
         st_quad<WK>(dB, r, q, b0);
         st_quad<WK>(dB, r + 1, q, b1);
+      }
+      // the ninth quad (nodes 32..35) of every row and group: one node each
+      {
+        const int it = tid;
+        const bool xg = it < 128;
+        const int r = (it & 127) >> 2, x = 32 + (it & 3);
+        const float* K = xg ? Kx : Ky;
+        float2 a = f2(0.f), bsum = f2(0.f);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const float2 kk = *reinterpret_cast<const float2*>(K + elem<WK>(r + v, x));
+          const float2 pp = *reinterpret_cast<const float2*>(Pk + elem<WK>(r + v, x));
+          const float2 kp = mul2(kk, sub2(pp, c0));
+          const float2 w = f2(xg ? M1(v) : S1(v));
+          a = v == 0 ? mul2(w, kp) : fma2(w, kp, a);
+          bsum = v == 0 ? mul2(w, kk) : fma2(w, kk, bsum);
+        }
+        *reinterpret_cast<float2*>((xg ? U0 : U2) + elem<WK>(r, x)) = a;
+        *reinterpret_cast<float2*>((xg ? U1 : U3) + elem<WK>(r, x)) = bsum;
       }
     }
     __syncthreads();
