@@ -144,10 +144,12 @@ template <int E> __device__ __forceinline__ void split_item(int it, int rows, in
 // cell (r, c) is node (x0 + c - HALO, y0 + r - HALO): the columns left and
 // right of the domain over every row, then the rows above and below it
 // between those columns (four strips; empty for an interior tile).
+// `skip` drops whole strips (bit 0 left, 1 right, 2 top, 3 bottom).
 template <int H, int W, int HALO, typename F>
-__device__ __forceinline__ void for_outside(int x0, int y0, int nx, int ny, int tid, int copies, F f) {
-  const int cl = max(0, HALO - x0), ch = min(W, nx - x0 + HALO);
-  const int rl = max(0, HALO - y0), rh = min(H, ny - y0 + HALO);
+__device__ __forceinline__ void for_outside(int x0, int y0, int nx, int ny, int tid, int copies, F f,
+                                            unsigned skip = 0u) {
+  const int cl = (skip & 1u) ? 0 : max(0, HALO - x0), ch = (skip & 2u) ? W : min(W, nx - x0 + HALO);
+  const int rl = (skip & 4u) ? 0 : max(0, HALO - y0), rh = (skip & 8u) ? H : min(H, ny - y0 + HALO);
   const int mid = ch - cl, wr = W - ch;
   const int nL = H * cl, nR = H * wr, nT = rl * mid, nB = (H - rh) * mid;
   const int tot = nL + nR + nT + nB;
@@ -245,13 +247,25 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
     // out-of-domain cells arrive as 0 (the vacuum incoming halo of Sec. 2.3);
     // the others take the nearest interior node, per direction
     if (edge6) {
-      for_outside<H6, W6, 6>(x0, y0, nx, ny, tid, 2, [&](int pl, int r, int c) {
-        const int gx = x0 + c - 6, gy = y0 + r - 6;
+      // a strip on an incoming vacuum side is all zero (the copy's fill):
+      // skipped whole; the other cells take the nearest interior node
+      // unless incoming in the other axis
+#pragma unroll
+      for (int pl = 0; pl < 2; ++pl) {
         const Dir<float>& dd = pl ? d1 : d0;
+        const bool sxp = dd.mu > 0.f, syp = dd.nu > 0.f;
+        const unsigned skip = (a.bc.xlo == BC_VACUUM && sxp ? 1u : 0u) | (a.bc.xhi == BC_VACUUM && !sxp ? 2u : 0u) |
+                              (a.bc.ylo == BC_VACUUM && syp ? 4u : 0u) | (a.bc.yhi == BC_VACUUM && !syp ? 8u : 0u);
         float* Pp = pl ? P1 : P0;
-        if (!halo_is_zero(a.bc, gx, gy, nx, ny, dd.mu > 0.f, dd.nu > 0.f))
-          Pp[r * PS + c + 2] = Pp[(clampi(gy, 0, ny - 1) - y0 + 6) * PS + clampi(gx, 0, nx - 1) - x0 + 8];
-      });
+        for_outside<H6, W6, 6>(
+            x0, y0, nx, ny, tid, 1,
+            [&](int, int r, int c) {
+              const int gx = x0 + c - 6, gy = y0 + r - 6;
+              if (!halo_is_zero(a.bc, gx, gy, nx, ny, sxp, syp))
+                Pp[r * PS + c + 2] = Pp[(clampi(gy, 0, ny - 1) - y0 + 6) * PS + clampi(gx, 0, nx - 1) - x0 + 8];
+            },
+            skip);
+      }
       __syncthreads();
     }
     // psi at the tile origin, per direction: the product terms use psi - c0
