@@ -34,6 +34,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "btmg_common.cuh"
 #include "tma.cuh"
@@ -53,31 +54,49 @@ constexpr int WP = 40;  // Px, Py, Tx, Ty: columns x0-4 ..
 constexpr int WK = 36;  // Kx, Ky, Pk, U, V: columns x0-2 ..
 constexpr int HA = H6, HB = TY + 8, HPX = TY + 8, HT = TY + 4, HK = TY + 4, HU = TY;
 
+// Row pitch (floats) of each pair array: 2W, plus padding on the arrays
+// whose ragged quads (columns 32 and beyond, read by items that span
+// several rows) would otherwise put rows two or four apart on the same
+// banks; quads 0..7 of a row are 128 contiguous bytes in any case.
+template <int W, int RP> struct Lay {
+  static_assert(RP >= 2 * W && RP % 4 == 0, "row pitch");
+  static constexpr int w = W, rp = RP;
+};
+using LA = Lay<WA, 2 * WA + 4>;  // A
+using LB = Lay<WB, 2 * WB + 8>;  // B
+using LP = Lay<WP, 2 * WP + 8>;  // Px, Py
+using LT = Lay<WP, 2 * WP + 8>;  // Tx, Ty
+using LK = Lay<WK, 2 * WK>;      // Kx, Ky, Pk
+using LU = Lay<WK, 2 * WK>;      // U0 .. U3
+
 // float offsets of the arrays (each a multiple of 4 floats)
 constexpr int OFF_P = 0;                     // 2 planes, TMA destination
 constexpr int OFF_AB = OFF_P + 2 * PLANE;    // A and B, later Tx/Ty, later U0..U3
-constexpr int SZ_U = HU * 2 * WK;
-constexpr int SZ_AB = (HA * 2 * WA + HB * 2 * WB) > 4 * SZ_U ? (HA * 2 * WA + HB * 2 * WB) : 4 * SZ_U;
-constexpr int OFF_A = OFF_AB, OFF_B = OFF_AB + HA * 2 * WA;
-constexpr int OFF_TX = OFF_AB, OFF_TY = OFF_AB + HT * 2 * WP;
-constexpr int OFF_PX = OFF_AB + SZ_AB, OFF_PY = OFF_PX + HPX * 2 * WP;
-constexpr int OFF_KX = OFF_PY + HPX * 2 * WP, OFF_KY = OFF_KX + HK * 2 * WK;
-constexpr int OFF_PK = OFF_KY + HK * 2 * WK;
-constexpr int ELEMS = OFF_PK + HK * 2 * WK;
-static_assert(OFF_TY + HT * 2 * WP <= OFF_AB + SZ_AB, "T arrays inside the A/B region");
-static_assert(4 * SZ_U <= SZ_AB && HA * 2 * WA + HB * 2 * WB <= SZ_AB, "A/B region");
+constexpr int SZ_U = HU * LU::rp;
+constexpr int SZ_A = HA * LA::rp, SZ_B = HB * LB::rp, SZ_T = HT * LT::rp;
+constexpr int SZ_AB = (SZ_A + SZ_B) > 4 * SZ_U ? (SZ_A + SZ_B) : 4 * SZ_U;
+constexpr int OFF_A = OFF_AB, OFF_B = OFF_AB + SZ_A;
+constexpr int OFF_TX = OFF_AB, OFF_TY = OFF_AB + SZ_T;
+constexpr int OFF_PX = OFF_AB + SZ_AB, OFF_PY = OFF_PX + HPX * LP::rp;
+constexpr int OFF_KX = OFF_PY + HPX * LP::rp, OFF_KY = OFF_KX + HK * LK::rp;
+constexpr int OFF_PK = OFF_KY + HK * LK::rp;
+constexpr int ELEMS = OFF_PK + HK * LK::rp;
+static_assert(2 * SZ_T <= SZ_AB, "T arrays inside the A/B region");
+static_assert(4 * SZ_U <= SZ_AB && SZ_A + SZ_B <= SZ_AB, "A/B region");
 static_assert((PLANE * 4) % 128 == 0, "second staged plane 128-byte aligned");
 static_assert(OFF_AB % 4 == 0 && OFF_B % 4 == 0 && OFF_TY % 4 == 0 && OFF_PX % 4 == 0 && OFF_PY % 4 == 0 &&
                   OFF_KX % 4 == 0 && OFF_KY % 4 == 0 && OFF_PK % 4 == 0 && SZ_U % 4 == 0,
               "16-byte alignment of the shared arrays");
+// two CTAs per SM: 2 x (dynamic + static shared memory + 1 KB reserved) <= 228 KB
+static_assert(2 * (ELEMS * 4 + 128 + 1024) <= 228 * 1024, "two CTAs per SM");
 
 // float offset of pair-chunk p (nodes 2p, 2p+1, both directions) of a row of
-// an array W nodes wide
-template <int W> __device__ __forceinline__ int chunk(int row, int p) {
-  return row * (2 * W) + (p & 1) * W + (p >> 1) * 4;
+// an array with layout L
+template <class L> __device__ __forceinline__ int chunk(int row, int p) {
+  return row * L::rp + (p & 1) * L::w + (p >> 1) * 4;
 }
 // float offset of node x (lane 0) of a row
-template <int W> __device__ __forceinline__ int elem(int row, int x) { return chunk<W>(row, x >> 1) + (x & 1) * 2; }
+template <class L> __device__ __forceinline__ int elem(int row, int x) { return chunk<L>(row, x >> 1) + (x & 1) * 2; }
 
 __device__ __forceinline__ void ld_chunk(const float* p, float2& a, float2& b) {
   const float4 v = *reinterpret_cast<const float4*>(p);
@@ -88,13 +107,13 @@ __device__ __forceinline__ void st_chunk(float* p, float2 a, float2 b) {
   *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
 }
 // nodes 2p .. 2p+2n-1 of a row (n chunks)
-template <int W, int N> __device__ __forceinline__ void ld_run(const float* base, int row, int p, float2 (&o)[2 * N]) {
+template <class L, int N> __device__ __forceinline__ void ld_run(const float* base, int row, int p, float2 (&o)[2 * N]) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) ld_chunk(base + chunk<W>(row, p + i), o[2 * i], o[2 * i + 1]);
+  for (int i = 0; i < N; ++i) ld_chunk(base + chunk<L>(row, p + i), o[2 * i], o[2 * i + 1]);
 }
-template <int W> __device__ __forceinline__ void st_quad(float* base, int row, int q, const float2 (&o)[4]) {
-  st_chunk(base + chunk<W>(row, 2 * q), o[0], o[1]);
-  st_chunk(base + chunk<W>(row, 2 * q + 1), o[2], o[3]);
+template <class L> __device__ __forceinline__ void st_quad(float* base, int row, int q, const float2 (&o)[4]) {
+  st_chunk(base + chunk<L>(row, 2 * q), o[0], o[1]);
+  st_chunk(base + chunk<L>(row, 2 * q + 1), o[2], o[3]);
 }
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
@@ -115,10 +134,10 @@ __device__ __forceinline__ float S1(int k) {
 __device__ __forceinline__ float D1(float p0, float p1, float p3, float p4) {
   return (8.0f / 12.0f) * (p3 - p1) - (1.0f / 12.0f) * (p4 - p0);
 }
-// 5-tap correlation of 8 consecutive pairs: out[k] = sum_u w_u in[k + u]
-template <bool S> __device__ __forceinline__ void xpass(const float2 (&in)[8], float2 (&o)[4]) {
+// 5-tap correlation of NO + 4 consecutive pairs: out[k] = sum_u w_u in[k + u]
+template <bool S, int NO> __device__ __forceinline__ void xpass(const float2 (&in)[NO + 4], float2 (&o)[NO]) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NO; ++k) {
     float2 acc = mul2(f2(S ? S1(0) : M1(0)), in[k]);
 #pragma unroll
     for (int u = 1; u < 5; ++u) acc = fma2(f2(S ? S1(u) : M1(u)), in[k + u], acc);
@@ -297,10 +316,10 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
               else o[k].x = od[k], raw[k].x = p[k];
             }
           }
-          st_quad<WA>(A, r, q, o);
+          st_quad<LA>(A, r, q, o);
           // Pk: tile rows -2..33, columns -2..33 (A row r = tile row r - 6,
           // the raw inputs p[0..3] are tile columns c - 6 .. c - 3)
-          if (r >= 4 && r < 4 + HK && c >= 4 && c <= WK) st_quad<WK>(Pk, r - 4, q - 1, raw);
+          if (r >= 4 && r < 4 + HK && c >= 4 && c <= WK) st_quad<LK>(Pk, r - 4, q - 1, raw);
         } else {
           int rb, q;
           split_item<WB / 4 - 8>(it - NA, HB / 2, rb, q);
@@ -323,8 +342,8 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
               else o0[k].x = e0, o1[k].x = e1;
             }
           }
-          st_quad<WB>(B, r, q, o0);
-          st_quad<WB>(B, r + 1, q, o1);
+          st_quad<LB>(B, r, q, o0);
+          st_quad<LB>(B, r + 1, q, o1);
         }
       }
     }
@@ -349,7 +368,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
 #pragma unroll
           for (int v = 0; v < 6; ++v) {
             float2 p[4];
-            ld_run<WA, 2>(A, r + v, 2 * q, p);
+            ld_run<LA, 2>(A, r + v, 2 * q, p);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               if (v < 5) s0[k] = v == 0 ? mul2(f2(M1(0)), p[k]) : fma2(f2(M1(v)), p[k], s0[k]);
@@ -358,18 +377,18 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
           }
 #pragma unroll
           for (int k = 0; k < 4; ++k) s0[k] = mul2(s0[k], idx), s1[k] = mul2(s1[k], idx);
-          st_quad<WP>(Px, r, q, s0);
-          st_quad<WP>(Px, r + 1, q, s1);
+          st_quad<LP>(Px, r, q, s0);
+          st_quad<LP>(Px, r + 1, q, s1);
         } else {
           int r, q;
           split_item<WP / 4 - 8>(it - NX, HPX, r, q);
           // Py node c = tile column c - 4 needs B nodes c + 2 .. c + 6
           float2 p[8], o[4];
-          ld_run<WB, 4>(B, r, 2 * q + 1, p);
+          ld_run<LB, 4>(B, r, 2 * q + 1, p);
           xpass<false>(p, o);
 #pragma unroll
           for (int k = 0; k < 4; ++k) o[k] = mul2(o[k], idy);
-          st_quad<WP>(Py, r, q, o);
+          st_quad<LP>(Py, r, q, o);
         }
       }
     }
@@ -377,8 +396,8 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
     if (edge4) {  // derived-field halo: nearest interior node
       for_outside<HPX, WP, 4>(x0, y0, nx, ny, tid, 1, [&](int, int r, int c) {
         const int sr = clampi(y0 + r - 4, 0, ny - 1) - y0 + 4, sc = clampi(x0 + c - 4, 0, nx - 1) - x0 + 4;
-        *reinterpret_cast<float2*>(Px + elem<WP>(r, c)) = *reinterpret_cast<const float2*>(Px + elem<WP>(sr, sc));
-        *reinterpret_cast<float2*>(Py + elem<WP>(r, c)) = *reinterpret_cast<const float2*>(Py + elem<WP>(sr, sc));
+        *reinterpret_cast<float2*>(Px + elem<LP>(r, c)) = *reinterpret_cast<const float2*>(Px + elem<LP>(sr, sc));
+        *reinterpret_cast<float2*>(Py + elem<LP>(r, c)) = *reinterpret_cast<const float2*>(Py + elem<LP>(sr, sc));
       });
       __syncthreads();
     }
@@ -400,7 +419,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
 #pragma unroll
         for (int v = 0; v < 7; ++v) {
           float2 p[4];
-          ld_run<WP, 2>(src, r + v, 2 * q, p);
+          ld_run<LP, 2>(src, r + v, 2 * q, p);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if (v < 5) s0[k] = v == 0 ? mul2(f2(M1(0)), p[k]) : fma2(f2(M1(v)), p[k], s0[k]);
@@ -408,9 +427,9 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
             if (v > 1) s2[k] = v == 2 ? mul2(f2(M1(0)), p[k]) : fma2(f2(M1(v - 2)), p[k], s2[k]);
           }
         }
-        st_quad<WP>(dst, r, q, s0);
-        st_quad<WP>(dst, r + 1, q, s1);
-        st_quad<WP>(dst, r + 2, q, s2);
+        st_quad<LT>(dst, r, q, s0);
+        st_quad<LT>(dst, r + 1, q, s1);
+        st_quad<LT>(dst, r + 2, q, s2);
       }
     }
     __syncthreads();
@@ -419,22 +438,20 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
       const float2 cx = make_float2(a.a_r * d0.mu, a.a_r * d1.mu), cy = make_float2(a.a_r * d0.nu, a.a_r * d1.nu);
       const float amu[2] = {fabsf(d0.mu), fabsf(d1.mu)}, anu[2] = {fabsf(d0.nu), fabsf(d1.nu)};
       const float kxmax[2] = {a.dx * amu[0], a.dx * amu[1]}, kymax[2] = {a.dy * anu[0], a.dy * anu[1]};
-      constexpr int NK = HK * (WK / 4);
-#pragma unroll 1
-      for (int it = tid; it < NK; it += NT) {
-        int r, q;
-        split_item<WK / 4 - 8>(it, HK, r, q);
-        // K node c = tile column c - 2: T nodes c .. c + 4, Psi node c + 2 of row r + 2
-        float2 tx[8], ty[8], pxv[4], pyv[4], mx[4], my[4];
-        ld_run<WP, 4>(Tx, r, 2 * q, tx);
-        ld_run<WP, 4>(Ty, r, 2 * q, ty);
-        ld_run<WP, 2>(Px, r + 2, 2 * q + 1, pxv);
-        ld_run<WP, 2>(Py, r + 2, 2 * q + 1, pyv);
+      // K nodes 2p .. 2p + 2NC - 1 of row r (K node c = tile column c - 2):
+      // T nodes c .. c + 4 and the Psi node c + 2 of row r + 2
+      auto k_nodes = [&](auto nc_tag, int r, int p) {
+        constexpr int NC = decltype(nc_tag)::value, NN = 2 * NC;
+        float2 tx[NN + 4], ty[NN + 4], pxv[NN], pyv[NN], mx[NN], my[NN];
+        ld_run<LT, NC + 2>(Tx, r, p, tx);
+        ld_run<LT, NC + 2>(Ty, r, p, ty);
+        ld_run<LP, NC>(Px, r + 2, p + 1, pxv);
+        ld_run<LP, NC>(Py, r + 2, p + 1, pyv);
         xpass<false>(tx, mx);
         xpass<false>(ty, my);
-        float2 kxo[4], kyo[4];
+        float2 kxo[NN], kyo[NN];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < NN; ++k) {
           const float2 Rx = mul2(cx, sub2(mx[k], pxv[k])), Ry = mul2(cy, sub2(my[k], pyv[k]));
           const float rx[2] = {Rx.x, Rx.y}, ry[2] = {Ry.x, Ry.y};
           const float px[2] = {pxv[k].x, pxv[k].y}, py[2] = {pyv[k].x, pyv[k].y};
@@ -451,16 +468,36 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
           kxo[k] = make_float2(kx[0], kx[1]);
           kyo[k] = make_float2(ky[0], ky[1]);
         }
-        st_quad<WK>(Kx, r, q, kxo);
-        st_quad<WK>(Ky, r, q, kyo);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          st_chunk(Kx + chunk<LK>(r, p + i), kxo[2 * i], kxo[2 * i + 1]);
+          st_chunk(Ky + chunk<LK>(r, p + i), kyo[2 * i], kyo[2 * i + 1]);
+        }
+      };
+      // 36 x 36 K nodes = 324 quads: one quad per thread (rows 0..31, quads
+      // 0..7), then the other 68 quads as 136 two-node items: rows 32..35,
+      // chunks 0..15 (eight even chunks of a row, then its eight odd ones),
+      // and chunks 16, 17 of every row
+      static_assert(HK == 36 && WK == 36 && NT == 256, "stage-3b item mapping");
+      k_nodes(std::integral_constant<int, 2>{}, tid >> 3, 2 * (tid & 7));
+      if (tid < 136) {
+        int r, p;
+        if (tid < 64) {
+          r = 32 + (tid >> 4);
+          p = ((tid & 7) << 1) | ((tid >> 3) & 1);
+        } else {
+          r = (tid - 64) >> 1;
+          p = 16 + (tid & 1);
+        }
+        k_nodes(std::integral_constant<int, 1>{}, r, p);
       }
     }
     __syncthreads();
     if (edge4) {
       for_outside<HK, WK, 2>(x0, y0, nx, ny, tid, 1, [&](int, int r, int c) {
         const int sr = clampi(y0 + r - 2, 0, ny - 1) - y0 + 2, sc = clampi(x0 + c - 2, 0, nx - 1) - x0 + 2;
-        *reinterpret_cast<float2*>(Kx + elem<WK>(r, c)) = *reinterpret_cast<const float2*>(Kx + elem<WK>(sr, sc));
-        *reinterpret_cast<float2*>(Ky + elem<WK>(r, c)) = *reinterpret_cast<const float2*>(Ky + elem<WK>(sr, sc));
+        *reinterpret_cast<float2*>(Kx + elem<LK>(r, c)) = *reinterpret_cast<const float2*>(Kx + elem<LK>(sr, sc));
+        *reinterpret_cast<float2*>(Ky + elem<LK>(r, c)) = *reinterpret_cast<const float2*>(Ky + elem<LK>(sr, sc));
       });
       __syncthreads();
     }
@@ -481,8 +518,8 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
 #pragma unroll
         for (int v = 0; v < 6; ++v) {
           float2 kk[4], pp[4];
-          ld_run<WK, 2>(K, r + v, 2 * q, kk);
-          ld_run<WK, 2>(Pk, r + v, 2 * q, pp);
+          ld_run<LK, 2>(K, r + v, 2 * q, kk);
+          ld_run<LK, 2>(Pk, r + v, 2 * q, pp);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const float2 kp = mul2(kk[k], sub2(pp[k], c0));
@@ -500,10 +537,10 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
         }
         float* dA = xg ? U0 : U2;
         float* dB = xg ? U1 : U3;
-        st_quad<WK>(dA, r, q, a0);
-        st_quad<WK>(dA, r + 1, q, a1);
-        st_quad<WK>(dB, r, q, b0);
-        st_quad<WK>(dB, r + 1, q, b1);
+        st_quad<LU>(dA, r, q, a0);
+        st_quad<LU>(dA, r + 1, q, a1);
+        st_quad<LU>(dB, r, q, b0);
+        st_quad<LU>(dB, r + 1, q, b1);
       }
       // the ninth quad (nodes 32..35) of every row and group: one node each
       {
@@ -514,15 +551,15 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
         float2 a = f2(0.f), bsum = f2(0.f);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          const float2 kk = *reinterpret_cast<const float2*>(K + elem<WK>(r + v, x));
-          const float2 pp = *reinterpret_cast<const float2*>(Pk + elem<WK>(r + v, x));
+          const float2 kk = *reinterpret_cast<const float2*>(K + elem<LK>(r + v, x));
+          const float2 pp = *reinterpret_cast<const float2*>(Pk + elem<LK>(r + v, x));
           const float2 kp = mul2(kk, sub2(pp, c0));
           const float2 w = f2(xg ? M1(v) : S1(v));
           a = v == 0 ? mul2(w, kp) : fma2(w, kp, a);
           bsum = v == 0 ? mul2(w, kk) : fma2(w, kk, bsum);
         }
-        *reinterpret_cast<float2*>((xg ? U0 : U2) + elem<WK>(r, x)) = a;
-        *reinterpret_cast<float2*>((xg ? U1 : U3) + elem<WK>(r, x)) = bsum;
+        *reinterpret_cast<float2*>((xg ? U0 : U2) + elem<LU>(r, x)) = a;
+        *reinterpret_cast<float2*>((xg ? U1 : U3) + elem<LU>(r, x)) = bsum;
       }
     }
     __syncthreads();
@@ -534,7 +571,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         float2 pp[8];
-        ld_run<WK, 4>(Pk, r5 + v, c5 / 2, pp);
+        ld_run<LK, 4>(Pk, r5 + v, c5 / 2, pp);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float2 pk = sub2(pp[j], c0);
@@ -546,21 +583,21 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
       xpass<true>(my, fp);
       xpass<false>(sy, gp);
       float2 u[8], fkp[4], fk[4], gkp[4], gk[4];
-      ld_run<WK, 4>(U0, r5, c5 / 2, u);
+      ld_run<LU, 4>(U0, r5, c5 / 2, u);
       xpass<true>(u, fkp);
-      ld_run<WK, 4>(U1, r5, c5 / 2, u);
+      ld_run<LU, 4>(U1, r5, c5 / 2, u);
       xpass<true>(u, fk);
-      ld_run<WK, 4>(U2, r5, c5 / 2, u);
+      ld_run<LU, 4>(U2, r5, c5 / 2, u);
       xpass<false>(u, gkp);
-      ld_run<WK, 4>(U3, r5, c5 / 2, u);
+      ld_run<LU, 4>(U3, r5, c5 / 2, u);
       xpass<false>(u, gk);
       // this thread's psi, k and Psi (tile row r5, columns c5 .. c5+3)
       float2 praw[4], kxv[4], kyv[4], pxv[4], pyv[4];
-      ld_run<WK, 2>(Pk, r5 + 2, c5 / 2 + 1, praw);
-      ld_run<WK, 2>(Kx, r5 + 2, c5 / 2 + 1, kxv);
-      ld_run<WK, 2>(Ky, r5 + 2, c5 / 2 + 1, kyv);
-      ld_run<WP, 2>(Px, r5 + 4, c5 / 2 + 2, pxv);
-      ld_run<WP, 2>(Py, r5 + 4, c5 / 2 + 2, pyv);
+      ld_run<LK, 2>(Pk, r5 + 2, c5 / 2 + 1, praw);
+      ld_run<LK, 2>(Kx, r5 + 2, c5 / 2 + 1, kxv);
+      ld_run<LK, 2>(Ky, r5 + 2, c5 / 2 + 1, kyv);
+      ld_run<LP, 2>(Px, r5 + 4, c5 / 2 + 2, pxv);
+      ld_run<LP, 2>(Py, r5 + 4, c5 / 2 + 2, pyv);
       const float2 i2x = f2(a.inv_dx2), i2y = f2(a.inv_dy2), mu = make_float2(d0.mu, d1.mu),
                    nu = make_float2(d0.nu, d1.nu);
       const float2 half = f2(a.half), w = make_float2(d0.w, d1.w);
