@@ -12,7 +12,7 @@
 // order of every sum, are those of k_pg.cu.
 //
 // One CTA owns a 32x32 tile and loops over the direction pairs of a chunk.
-// The pair's two psi planes arrive by one TMA copy (a 48 x 44 x 2 box) into a
+// The pair's two psi planes arrive by one TMA copy (a 56 x 44 x 2 box) into a
 // single staging buffer, which is free again after the first pass, so the
 // next pair's copy is issued there and lands during the rest of the passes.
 // Passes (D = d1, M = m1, S = s1 of Sec. 2.7 / the Appendix, h = 1):
@@ -44,7 +44,9 @@ namespace {
 
 constexpr int TX = 32, TY = 32, NT = 256;
 constexpr int H6 = TY + 12, W6 = TX + 12;  // psi with its 6-node halo
-constexpr int PS = 48;                     // staged row: columns x0-8 .. x0+39
+// staged row: columns x0-8 .. x0+47 (x0+40 .. x0+47 are not used: the
+// wider box staggers the banks of staged rows two apart)
+constexpr int PS = 56;
 constexpr int PLANE = H6 * PS;             // floats of one staged direction plane
 
 // widths (nodes per row) of the pair arrays
@@ -64,7 +66,7 @@ template <int W, int RP> struct Lay {
 };
 using LA = Lay<WA, 2 * WA + 4>;  // A
 using LB = Lay<WB, 2 * WB + 8>;  // B
-using LP = Lay<WP, 2 * WP + 8>;  // Px, Py
+using LP = Lay<WP, 2 * WP + 4>;  // Px, Py
 using LT = Lay<WP, 2 * WP + 8>;  // Tx, Ty
 using LK = Lay<WK, 2 * WK>;      // Kx, Ky, Pk
 using LU = Lay<WK, 2 * WK>;      // U0 .. U3
@@ -82,6 +84,7 @@ constexpr int OFF_KX = OFF_PY + HPX * LP::rp, OFF_KY = OFF_KX + HK * LK::rp;
 constexpr int OFF_PK = OFF_KY + HK * LK::rp;
 constexpr int ELEMS = OFF_PK + HK * LK::rp;
 static_assert(2 * SZ_T <= SZ_AB, "T arrays inside the A/B region");
+static_assert(2 * SZ_U <= 2 * HPX * LP::rp, "U4, U5 inside the Px/Py region");
 static_assert(4 * SZ_U <= SZ_AB && SZ_A + SZ_B <= SZ_AB, "A/B region");
 static_assert((PLANE * 4) % 128 == 0, "second staged plane 128-byte aligned");
 static_assert(OFF_AB % 4 == 0 && OFF_B % 4 == 0 && OFF_TY % 4 == 0 && OFF_PX % 4 == 0 && OFF_PY % 4 == 0 &&
@@ -207,6 +210,8 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
   float* const U1 = U0 + SZ_U;
   float* const U2 = U1 + SZ_U;
   float* const U3 = U2 + SZ_U;
+  float* const U4 = sm + OFF_PX;  // stage 4 on, in place of Px and Py
+  float* const U5 = U4 + SZ_U;
   __shared__ double red[NT / 32];
   __shared__ __align__(8) uint64_t bar;
 
@@ -289,6 +294,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
     }
     // psi at the tile origin, per direction: the product terms use psi - c0
     const float2 c0 = make_float2(P0[6 * PS + 8], P1[6 * PS + 8]);
+    float2 adv5[4];  // mu Psi_x + nu Psi_y at this thread's stage-5 nodes
     // ---- stage 1: A = d1_x P, B = d1_y P (difference form), Pk = P ---------
     {
       constexpr int NA = HA * (WA / 4), NB = (HB / 2) * (WB / 4);
@@ -438,9 +444,11 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
       const float2 cx = make_float2(a.a_r * d0.mu, a.a_r * d1.mu), cy = make_float2(a.a_r * d0.nu, a.a_r * d1.nu);
       const float amu[2] = {fabsf(d0.mu), fabsf(d1.mu)}, anu[2] = {fabsf(d0.nu), fabsf(d1.nu)};
       const float kxmax[2] = {a.dx * amu[0], a.dx * amu[1]}, kymax[2] = {a.dy * anu[0], a.dy * anu[1]};
+      const float2 mu = make_float2(d0.mu, d1.mu), nu = make_float2(d0.nu, d1.nu);
       // K nodes 2p .. 2p + 2NC - 1 of row r (K node c = tile column c - 2):
-      // T nodes c .. c + 4 and the Psi node c + 2 of row r + 2
-      auto k_nodes = [&](auto nc_tag, int r, int p) {
+      // T nodes c .. c + 4 and the Psi node c + 2 of row r + 2; adv = the
+      // streaming term mu Psi_x + nu Psi_y of the same nodes
+      auto k_nodes = [&](auto nc_tag, int r, int p, auto& adv) {
         constexpr int NC = decltype(nc_tag)::value, NN = 2 * NC;
         float2 tx[NN + 4], ty[NN + 4], pxv[NN], pyv[NN], mx[NN], my[NN];
         ld_run<LT, NC + 2>(Tx, r, p, tx);
@@ -467,6 +475,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
           }
           kxo[k] = make_float2(kx[0], kx[1]);
           kyo[k] = make_float2(ky[0], ky[1]);
+          adv[k] = fma2(nu, pyv[k], mul2(mu, pxv[k]));
         }
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
@@ -474,22 +483,25 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
           st_chunk(Ky + chunk<LK>(r, p + i), kyo[2 * i], kyo[2 * i + 1]);
         }
       };
-      // 36 x 36 K nodes = 324 quads: one quad per thread (rows 0..31, quads
-      // 0..7), then the other 68 quads as 136 two-node items: rows 32..35,
-      // chunks 0..15 (eight even chunks of a row, then its eight odd ones),
-      // and chunks 16, 17 of every row
+      // 36 x 36 K nodes: first the stage-5 nodes of this thread (tile row
+      // r5, columns c5 .. c5+3: K row r5 + 2, chunks c5/2 + 1, + 2), whose
+      // streaming term stays in registers until stage 5; then the other 136
+      // chunks as two-node items: K rows 0, 1, 34, 35 (even chunks of a row,
+      // then its odd ones) and chunks 0 and 17 of rows 2..33
       static_assert(HK == 36 && WK == 36 && NT == 256, "stage-3b item mapping");
-      k_nodes(std::integral_constant<int, 2>{}, tid >> 3, 2 * (tid & 7));
+      k_nodes(std::integral_constant<int, 2>{}, r5 + 2, c5 / 2 + 1, adv5);
       if (tid < 136) {
         int r, p;
-        if (tid < 64) {
-          r = 32 + (tid >> 4);
-          p = ((tid & 7) << 1) | ((tid >> 3) & 1);
+        if (tid < 72) {
+          const int rr = tid / 18, c = tid - rr * 18;
+          r = rr < 2 ? rr : rr + 32;
+          p = c < 9 ? 2 * c : 2 * (c - 9) + 1;
         } else {
-          r = (tid - 64) >> 1;
-          p = 16 + (tid & 1);
+          r = 2 + ((tid - 72) >> 1);
+          p = (tid & 1) ? 17 : 0;
         }
-        k_nodes(std::integral_constant<int, 1>{}, r, p);
+        float2 adv_unused[2];
+        k_nodes(std::integral_constant<int, 1>{}, r, p, adv_unused);
       }
     }
     __syncthreads();
@@ -501,10 +513,12 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
       });
       __syncthreads();
     }
-    // ---- stage 4: the k-dependent y passes of both groups --------------------
-    //   U0 = m1_y (k_x pc), U1 = m1_y k_x, U2 = s1_y (k_y pc), U3 = s1_y k_y
+    // ---- stage 4: the y passes of both groups -------------------------------
+    //   U0 = m1_y (k_x pc), U1 = m1_y k_x, U4 = m1_y pc,
+    //   U2 = s1_y (k_y pc), U3 = s1_y k_y, U5 = s1_y pc
     // on tile rows 0..31, columns -2..33; items of two rows and four nodes
-    // (six K and Pk rows in)
+    // (six K and Pk rows in).  U4 and U5 take the place of Px and Py, whose
+    // last reads were in stage 3b.
     {
       // two-row items over quads 0..7 of both groups: exactly one per thread
       static_assert((HU / 2) * 8 * 2 == NT && WK / 4 == 9, "stage-4 item mapping");
@@ -514,7 +528,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
         const int j = it & 127;
         const int r = (j >> 3) * 2, q = j & 7;
         const float* K = xg ? Kx : Ky;
-        float2 a0[4], a1[4], b0[4], b1[4];  // rows r and r+1 of the two sums
+        float2 a0[4], a1[4], b0[4], b1[4], e0[4], e1[4];  // rows r and r+1 of the three sums
 #pragma unroll
         for (int v = 0; v < 6; ++v) {
           float2 kk[4], pp[4];
@@ -522,25 +536,31 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
           ld_run<LK, 2>(Pk, r + v, 2 * q, pp);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const float2 kp = mul2(kk[k], sub2(pp[k], c0));
+            const float2 pc = sub2(pp[k], c0);
+            const float2 kp = mul2(kk[k], pc);
             if (v < 5) {
               const float2 w = f2(xg ? M1(v) : S1(v));
               a0[k] = v == 0 ? mul2(w, kp) : fma2(w, kp, a0[k]);
               b0[k] = v == 0 ? mul2(w, kk[k]) : fma2(w, kk[k], b0[k]);
+              e0[k] = v == 0 ? mul2(w, pc) : fma2(w, pc, e0[k]);
             }
             if (v > 0) {
               const float2 w = f2(xg ? M1(v - 1) : S1(v - 1));
               a1[k] = v == 1 ? mul2(w, kp) : fma2(w, kp, a1[k]);
               b1[k] = v == 1 ? mul2(w, kk[k]) : fma2(w, kk[k], b1[k]);
+              e1[k] = v == 1 ? mul2(w, pc) : fma2(w, pc, e1[k]);
             }
           }
         }
         float* dA = xg ? U0 : U2;
         float* dB = xg ? U1 : U3;
+        float* dE = xg ? U4 : U5;
         st_quad<LU>(dA, r, q, a0);
         st_quad<LU>(dA, r + 1, q, a1);
         st_quad<LU>(dB, r, q, b0);
         st_quad<LU>(dB, r + 1, q, b1);
+        st_quad<LU>(dE, r, q, e0);
+        st_quad<LU>(dE, r + 1, q, e1);
       }
       // the ninth quad (nodes 32..35) of every row and group: one node each
       {
@@ -548,41 +568,33 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
         const bool xg = it < 128;
         const int r = (it & 127) >> 2, x = 32 + (it & 3);
         const float* K = xg ? Kx : Ky;
-        float2 a = f2(0.f), bsum = f2(0.f);
+        float2 a = f2(0.f), bsum = f2(0.f), e = f2(0.f);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           const float2 kk = *reinterpret_cast<const float2*>(K + elem<LK>(r + v, x));
           const float2 pp = *reinterpret_cast<const float2*>(Pk + elem<LK>(r + v, x));
-          const float2 kp = mul2(kk, sub2(pp, c0));
+          const float2 pc = sub2(pp, c0);
+          const float2 kp = mul2(kk, pc);
           const float2 w = f2(xg ? M1(v) : S1(v));
           a = v == 0 ? mul2(w, kp) : fma2(w, kp, a);
           bsum = v == 0 ? mul2(w, kk) : fma2(w, kk, bsum);
+          e = v == 0 ? mul2(w, pc) : fma2(w, pc, e);
         }
         *reinterpret_cast<float2*>((xg ? U0 : U2) + elem<LU>(r, x)) = a;
         *reinterpret_cast<float2*>((xg ? U1 : U3) + elem<LU>(r, x)) = bsum;
+        *reinterpret_cast<float2*>((xg ? U4 : U5) + elem<LU>(r, x)) = e;
       }
     }
     __syncthreads();
     // ---- stage 5: x passes and assembly on this thread's four nodes ----------
     {
-      // the k-free terms straight from Pk: s1_x m1_y pc and m1_x s1_y pc
-      // (tile rows r5-2 .. r5+2 = Pk rows r5 .. r5+4, columns c5-2 .. c5+5)
-      float2 my[8], sy[8];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        float2 pp[8];
-        ld_run<LK, 4>(Pk, r5 + v, c5 / 2, pp);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float2 pk = sub2(pp[j], c0);
-          my[j] = v == 0 ? mul2(f2(M1(0)), pk) : fma2(f2(M1(v)), pk, my[j]);
-          sy[j] = v == 0 ? mul2(f2(S1(0)), pk) : fma2(f2(S1(v)), pk, sy[j]);
-        }
-      }
-      float2 fp[4], gp[4];
-      xpass<true>(my, fp);
-      xpass<false>(sy, gp);
-      float2 u[8], fkp[4], fk[4], gkp[4], gk[4];
+      // the k-free terms s1_x m1_y pc and m1_x s1_y pc
+      float2 u[8], fp[4], gp[4];
+      ld_run<LU, 4>(U4, r5, c5 / 2, u);
+      xpass<true>(u, fp);
+      ld_run<LU, 4>(U5, r5, c5 / 2, u);
+      xpass<false>(u, gp);
+      float2 fkp[4], fk[4], gkp[4], gk[4];
       ld_run<LU, 4>(U0, r5, c5 / 2, u);
       xpass<true>(u, fkp);
       ld_run<LU, 4>(U1, r5, c5 / 2, u);
@@ -591,15 +603,12 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
       xpass<false>(u, gkp);
       ld_run<LU, 4>(U3, r5, c5 / 2, u);
       xpass<false>(u, gk);
-      // this thread's psi, k and Psi (tile row r5, columns c5 .. c5+3)
-      float2 praw[4], kxv[4], kyv[4], pxv[4], pyv[4];
+      // this thread's psi and k (tile row r5, columns c5 .. c5+3)
+      float2 praw[4], kxv[4], kyv[4];
       ld_run<LK, 2>(Pk, r5 + 2, c5 / 2 + 1, praw);
       ld_run<LK, 2>(Kx, r5 + 2, c5 / 2 + 1, kxv);
       ld_run<LK, 2>(Ky, r5 + 2, c5 / 2 + 1, kyv);
-      ld_run<LP, 2>(Px, r5 + 4, c5 / 2 + 2, pxv);
-      ld_run<LP, 2>(Py, r5 + 4, c5 / 2 + 2, pyv);
-      const float2 i2x = f2(a.inv_dx2), i2y = f2(a.inv_dy2), mu = make_float2(d0.mu, d1.mu),
-                   nu = make_float2(d0.nu, d1.nu);
+      const float2 i2x = f2(a.inv_dx2), i2y = f2(a.inv_dy2);
       const float2 half = f2(a.half), w = make_float2(d0.w, d1.w);
       float2 res[4];
 #pragma unroll
@@ -607,9 +616,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
         const float2 npc = sub2(c0, praw[k]);  // -(psi - c0)
         const float2 Dx = mul2(fma2(npc, fk[k], fma2(kxv[k], fp[k], fkp[k])), i2x);
         const float2 Dy = mul2(fma2(npc, gk[k], fma2(kyv[k], gp[k], gkp[k])), i2y);
-        float2 Ap = mul2(mu, pxv[k]);
-        Ap = fma2(nu, pyv[k], Ap);
-        Ap = fma2(half, add2(Dx, Dy), Ap);
+        float2 Ap = fma2(half, add2(Dx, Dy), adv5[k]);
         Ap = fma2(f2(sig[k]), praw[k], Ap);
         res[k] = Ap;
       }
