@@ -6,7 +6,43 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
+#include <utility>
+
 namespace btmg {
+
+// ------------------------------------------- programmatic dependent launch -
+// The kernels of a cycle are launched with programmatic stream
+// serialisation: a kernel may be scheduled while its predecessor in the
+// stream drains, so its launch overlaps the predecessor's last wave.
+// pdl_wait() (first statement of such a kernel) blocks until the
+// predecessor has completed and its writes are visible; pdl_launch() then
+// lets the successor be scheduled.  Both are no-ops for a plain launch.
+// BTMG_PDL=0 in the environment launches plainly.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("BTMG_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+template <typename... KP, typename... A>
+inline cudaError_t launch_pdl(void (*kern)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 // ---------------------------------------------------------------- types ---
 template <typename T> struct Conv;

@@ -259,6 +259,8 @@ __device__ __forceinline__ void upwind_tile(const UpArgs<T, C>& a, const int til
 template <typename T, typename C, int MODE, int NU>
 __global__ void __launch_bounds__(UNT, 3) k_upwind(const UpArgs<T, C> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
+  pdl_launch();
   upwind_tile<T, C, MODE, NU, UT>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
@@ -398,6 +400,8 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_upwind_stream(const UpArgs
   extern __shared__ __align__(128) unsigned char us_smem[];
   __shared__ Dir<float> sdir[US_DMAX];
   __shared__ int spar[US_DMAX];
+  pdl_wait();
+  pdl_launch();
   __shared__ __align__(8) uint64_t sbar[US_WARPS][3];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int chunk = blockIdx.y;
@@ -580,6 +584,8 @@ template <typename C>
 __global__ void k_restrict(const C* __restrict__ fine, C* __restrict__ coarse, const C* __restrict__ rcoef,
                            int nx, int ny, int nr, int nc, int nxc, int nyc, int nrc, int ncc, int fx, int fy,
                            int fr, int fc) {
+  pdl_wait();
+  pdl_launch();
   const size_t total = (size_t)8 * nrc * ncc * nyc * nxc;
   restrict_cells<C>(fine, coarse, rcoef, nx, ny, nr, nc, nxc, nyc, nrc, ncc, fx, fy, fr, fc,
                     blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x, total);
@@ -602,6 +608,8 @@ __global__ void k_prolong(const C* __restrict__ coarse, C* __restrict__ fine, in
 template <typename T, typename C>
 __global__ void k_phi_partial(const T* __restrict__ psi, C* __restrict__ part, const Dir<C>* __restrict__ dir,
                               int npix, int nd, int dpc, int nchunk) {
+  pdl_wait();
+  pdl_launch();
   const size_t total = (size_t)nchunk * npix;
   for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
     const int pix = id % npix;
@@ -617,6 +625,8 @@ template <typename C>
 __global__ void k_source(const C* __restrict__ src_g, const C* __restrict__ sigs_g, const C* __restrict__ phi_part,
                          int G, int g, int nchunk, int npix, C* __restrict__ b, C* __restrict__ qfix,
                          double* __restrict__ qn2_part) {
+  pdl_wait();
+  pdl_launch();
   __shared__ double red[8];
   double acc = 0.0;
   const C inv4pi = C(0.07957747154594767);  // 1 / (4 pi)
@@ -646,6 +656,8 @@ __global__ void k_source(const C* __restrict__ src_g, const C* __restrict__ sigs
 
 template <typename C>
 __global__ void k_phi_sum(const C* __restrict__ part, int nchunk, int npix, C* __restrict__ phi) {
+  pdl_wait();
+  pdl_launch();
   for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < npix; pix += gridDim.x * blockDim.x) {
     C acc = C(0);
     for (int c = 0; c < nchunk; ++c) acc += part[(size_t)c * npix + pix];
@@ -654,6 +666,8 @@ __global__ void k_phi_sum(const C* __restrict__ part, int nchunk, int npix, C* _
 }
 
 __global__ void k_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+  pdl_wait();
+  pdl_launch();
   __shared__ double red[32];
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
@@ -701,8 +715,7 @@ cudaError_t launch_up_nu(const UpArgs<T, C>& a, int nchunk, cudaStream_t s) {
   }
   const int tiles_y = (a.ny + UT - 1) / UT;
   dim3 grid(a.tiles_x * tiles_y, nchunk);
-  k_upwind<T, C, MODE, NU><<<grid, UNT, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_upwind<T, C, MODE, NU>, grid, dim3(UNT), smem, s, a);
 }
 
 template <typename T, typename C, int MODE>
@@ -734,8 +747,7 @@ cudaError_t launch_up_stream(const UpArgs<T, float>& a, const UsMaps& maps, int 
   const int ncg = (a.nx + OUTW - 1) / OUTW, nbands = (a.ny + USR - 1) / USR;
   const int warps = ncg * nbands;
   dim3 grid((warps + US_WARPS - 1) / US_WARPS, nchunk);
-  k_upwind_stream<T, NU><<<grid, US_WARPS * 32, smem, s>>>(a, ncg, nbands, maps);
-  return cudaGetLastError();
+  return launch_pdl(k_upwind_stream<T, NU>, grid, dim3(US_WARPS * 32), smem, s, a, ncg, nbands, maps);
 }
 
 // Tensor maps of the streaming kernel's windows, or false when the layout
@@ -788,9 +800,8 @@ template <typename C>
 cudaError_t launch_restrict(const C* fine, C* coarse, const C* rcoef, int nx, int ny, int nr, int nc, int nxc,
                             int nyc, int nrc, int ncc, int fx, int fy, int fr, int fc, cudaStream_t s) {
   const size_t total = (size_t)8 * nrc * ncc * nyc * nxc;
-  k_restrict<C><<<grid_for(total, 256), 256, 0, s>>>(fine, coarse, rcoef, nx, ny, nr, nc, nxc, nyc, nrc, ncc, fx,
-                                                      fy, fr, fc);
-  return cudaGetLastError();
+  return launch_pdl(k_restrict<C>, dim3(grid_for(total, 256)), dim3(256), 0, s, fine, coarse, rcoef, nx, ny, nr, nc,
+                    nxc, nyc, nrc, ncc, fx, fy, fr, fc);
 }
 
 template <typename C>
@@ -806,21 +817,20 @@ template <typename T, typename C>
 cudaError_t launch_phi_partial(const T* psi, C* part, const Dir<C>* dir, int nx, int ny, int nd, int dpc,
                                int nchunk, cudaStream_t s) {
   const int npix = nx * ny;
-  k_phi_partial<T, C><<<grid_for((size_t)nchunk * npix, 256), 256, 0, s>>>(psi, part, dir, npix, nd, dpc, nchunk);
-  return cudaGetLastError();
+  return launch_pdl(k_phi_partial<T, C>, dim3(grid_for((size_t)nchunk * npix, 256)), dim3(256), 0, s, psi, part, dir,
+                    npix, nd, dpc, nchunk);
 }
 
 template <typename C>
 cudaError_t launch_source(const C* src_g, const C* sigs_g, const C* phi_part, int G, int g, int nchunk, int npix,
                           C* b, C* qfix, double* qn2_part, int nblocks, cudaStream_t s) {
-  k_source<C><<<nblocks, 256, 0, s>>>(src_g, sigs_g, phi_part, G, g, nchunk, npix, b, qfix, qn2_part);
-  return cudaGetLastError();
+  return launch_pdl(k_source<C>, dim3(nblocks), dim3(256), 0, s, src_g, sigs_g, phi_part, G, g, nchunk, npix, b, qfix,
+                    qn2_part);
 }
 
 template <typename C>
 cudaError_t launch_phi_sum(const C* part, int nchunk, int npix, C* phi, cudaStream_t s) {
-  k_phi_sum<C><<<grid_for(npix, 256), 256, 0, s>>>(part, nchunk, npix, phi);
-  return cudaGetLastError();
+  return launch_pdl(k_phi_sum<C>, dim3(grid_for(npix, 256)), dim3(256), 0, s, part, nchunk, npix, phi);
 }
 
 namespace {
@@ -1138,8 +1148,7 @@ cudaError_t launch_coarse_batch(const CoarseBatch& cb, int nu, int tu, int ctas,
 }
 
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s) {
-  k_sum<<<1, 1024, 0, s>>>(part, n, out);
-  return cudaGetLastError();
+  return launch_pdl(k_sum, dim3(1), dim3(1024), 0, s, part, n, out);
 }
 #endif
 

@@ -157,6 +157,8 @@ template <typename T, typename C, int MODE, bool PGON, bool TMA, int ORD>
 __global__ void __launch_bounds__(NT, sizeof(C) == 4 ? 3 : 1)
     k_pg(const PgArgs<T, C> a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  pdl_wait();
+  pdl_launch();
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* P = sm + OFF_P + 2;  // current staged tile (+2: origin -6 in x)
   C* A = sm + OFF_A;
@@ -637,8 +639,7 @@ cudaError_t launch_variant(const PgArgs<T, C>& a, const CUtensorMap& tm, int nch
   }
   const int tiles_y = (a.ny + TY - 1) / TY;
   dim3 grid(a.tiles_x * tiles_y, nchunk);
-  k_pg<T, C, MODE, PGON, TMA, ORD><<<grid, NT, smem, s>>>(a, tm);
-  return cudaGetLastError();
+  return launch_pdl(k_pg<T, C, MODE, PGON, TMA, ORD>, grid, dim3(NT), smem, s, a, tm);
 }
 
 template <typename T, typename C, int MODE, bool PGON, int ORD>

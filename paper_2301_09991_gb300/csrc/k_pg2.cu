@@ -194,6 +194,8 @@ __device__ __forceinline__ void for_outside(int x0, int y0, int nx, int ny, int 
 __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, const int mode,
                                                 const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  pdl_wait();
+  pdl_launch();
   float* sm = reinterpret_cast<float*>(smem_raw);
   float* const P0 = sm + OFF_P;  // staged plane of direction n (tile base: column x0-8, row y0-6)
   float* const P1 = P0 + PLANE;  // direction n+1
@@ -721,8 +723,7 @@ cudaError_t launch_pg2(const PgArgs<float, float>& a, int mode, int nchunk, cuda
     return cudaErrorInvalidValue;
   const int tiles_y = (a.ny + TY - 1) / TY;
   dim3 grid(a.tiles_x * tiles_y, nchunk);
-  k_pg2<<<grid, NT, smem, s>>>(a, mode, tm);
-  return cudaGetLastError();
+  return launch_pdl(k_pg2, grid, dim3(NT), smem, s, a, mode, tm);
 }
 
 }  // namespace btmg

@@ -360,6 +360,8 @@ __global__ void k_scat_gain(const C* __restrict__ sig, const C* __restrict__ cra
 // smoother, its scalar flux summed over all directions at once.
 template <typename C, int TMAX, bool SCAT> __global__ void __launch_bounds__(1024) k_tail(const ScatTail<C> t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
+  pdl_launch();
   C* Ja = reinterpret_cast<C*>(smem_raw);
   C* Jb = Ja + TMAX;
   C* Dc = Jb + TMAX;  // the coarser level's delta, then this level's
@@ -536,8 +538,7 @@ template <typename C, bool SCAT> cudaError_t launch_tail_mode(const ScatTail<C>&
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_tail<C, TMAX, SCAT><<<1, 1024, smem, s>>>(t);
-  return cudaGetLastError();
+  return launch_pdl(k_tail<C, TMAX, SCAT>, dim3(1), dim3(1024), smem, s, t);
 }
 template <typename C> cudaError_t launch_scat_tail(const ScatTail<C>& t, cudaStream_t s) {
   return t.scat ? launch_tail_mode<C, true>(t, s) : launch_tail_mode<C, false>(t, s);

@@ -116,6 +116,8 @@ template <> struct Quad<__half, float, true> : Quad16<__half> {};
 template <typename T, typename C, int MODE, bool VEC>
 __global__ void __launch_bounds__(RNT, 4) k_upres(const PgArgs<T, C> a) {
   __shared__ double red[RNT / 32];
+  pdl_wait();
+  pdl_launch();
   const int tid = threadIdx.x;
   const int tile = blockIdx.x, chunk = blockIdx.y;
   const int tiles_sx = (a.nx + RTX - 1) / RTX;
@@ -240,6 +242,8 @@ __global__ void __launch_bounds__(RNT, 4) k_upres_tma(const PgArgs<T, C> a, cons
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[KS];
   __shared__ double red[RNT / 32];
+  pdl_wait();
+  pdl_launch();
   const int tid = threadIdx.x;
   const int tile = blockIdx.x, chunk = blockIdx.y;
   const int tiles_sx = (a.nx + RTX - 1) / RTX;
@@ -381,8 +385,7 @@ cudaError_t launch_tma(const PgArgs<T, C>& a, const CUtensorMap& tm, int nchunk,
     attr_set = true;
   }
   dim3 grid(((a.nx + RTX - 1) / RTX) * ((a.ny + RTY - 1) / RTY), nchunk);
-  k_upres_tma<T, C, MODE><<<grid, RNT, smem, s>>>(a, tm);
-  return cudaGetLastError();
+  return launch_pdl(k_upres_tma<T, C, MODE>, grid, dim3(RNT), smem, s, a, tm);
 }
 
 bool aligned(const void* p, size_t b) { return ((uintptr_t)p % b) == 0; }
@@ -390,8 +393,7 @@ bool aligned(const void* p, size_t b) { return ((uintptr_t)p % b) == 0; }
 template <typename T, typename C, int MODE, bool VEC>
 cudaError_t launch_v(const PgArgs<T, C>& a, int nchunk, cudaStream_t s) {
   dim3 grid(((a.nx + RTX - 1) / RTX) * ((a.ny + RTY - 1) / RTY), nchunk);
-  k_upres<T, C, MODE, VEC><<<grid, RNT, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_upres<T, C, MODE, VEC>, grid, dim3(RNT), 0, s, a);
 }
 
 }  // namespace
