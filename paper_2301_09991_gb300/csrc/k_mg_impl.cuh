@@ -591,6 +591,42 @@ __global__ void k_restrict(const C* __restrict__ fine, C* __restrict__ coarse, c
                     blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x, total);
 }
 
+// The restriction of a level whose coarse cells all have their 2 x 2 node
+// and 2 x 2 direction children, with coarse rows of a multiple of 4 nodes:
+// thread (q, Y, N) forms coarse nodes 4q .. 4q+3 of coarse row Y and
+// direction N from 16-byte row loads, each cell summed in restrict_cells'
+// order (children (j, i), then fine rows, then fine columns), so the two
+// kernels agree bit for bit.
+__global__ void k_restrict4(const float* __restrict__ fine, float* __restrict__ coarse,
+                            const float* __restrict__ rcoef, int nx, int ny, int nr, int nc, int nxc, int nyc,
+                            int nrc, int ncc) {
+  pdl_wait();
+  pdl_launch();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y * blockDim.y + threadIdx.y, N = blockIdx.z;
+  if (4 * q >= nxc || Y >= nyc) return;
+  const int f = N / (nrc * ncc), J = (N % (nrc * ncc)) / ncc, I = N % ncc;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int aa = 0; aa < 2; ++aa)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+      const int n = f * nr * nc + (2 * J + aa) * nc + 2 * I + bb;
+      const float w = rcoef[n];
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy) {
+        const float* row = fine + ((size_t)n * ny + 2 * Y + yy) * nx + 8 * q;
+        const float4 u = *reinterpret_cast<const float4*>(row), v = *reinterpret_cast<const float4*>(row + 4);
+        const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc[k] += w * x[2 * k];
+          acc[k] += w * x[2 * k + 1];
+        }
+      }
+    }
+  *reinterpret_cast<float4*>(coarse + ((size_t)N * nyc + Y) * nxc + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+
 template <typename C>
 __global__ void k_prolong(const C* __restrict__ coarse, C* __restrict__ fine, int nx, int ny, int nr, int nc,
                           int nxc, int nyc, int nrc, int ncc, int fx, int fy, int fr, int fc) {
@@ -800,6 +836,14 @@ template <typename C>
 cudaError_t launch_restrict(const C* fine, C* coarse, const C* rcoef, int nx, int ny, int nr, int nc, int nxc,
                             int nyc, int nrc, int ncc, int fx, int fy, int fr, int fc, cudaStream_t s) {
   const size_t total = (size_t)8 * nrc * ncc * nyc * nxc;
+  if constexpr (std::is_same<C, float>::value) {
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) % 16) == 0; };
+    if (fx == 2 && fy == 2 && fr == 2 && fc == 2 && nx == 2 * nxc && ny == 2 * nyc && nr == 2 * nrc &&
+        nc == 2 * ncc && nxc % 4 == 0 && nyc <= 65535 * 8 && 8 * nrc * ncc <= 65535 && al(fine) && al(coarse)) {
+      const dim3 block(32, 8), grid((nxc / 4 + 31) / 32, (nyc + 7) / 8, 8 * nrc * ncc);
+      return launch_pdl(k_restrict4, grid, block, 0, s, fine, coarse, rcoef, nx, ny, nr, nc, nxc, nyc, nrc, ncc);
+    }
+  }
   return launch_pdl(k_restrict<C>, dim3(grid_for(total, 256)), dim3(256), 0, s, fine, coarse, rcoef, nx, ny, nr, nc,
                     nxc, nyc, nrc, ncc, fx, fy, fr, fc);
 }

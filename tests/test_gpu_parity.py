@@ -109,6 +109,23 @@ def test_restrict_prolong(name, mk):
         assert np.array_equal(f, op.prolong(l, coarse))
 
 
+@pytest.mark.parametrize("nx,ny", [(64, 48), (72, 40), (36, 20)])
+def test_restrict_fp32_every_level(nx, ny):
+    """FP32 restriction on every level against the FP64 oracle: the 16-byte
+    row kernel where every coarse cell has all its 2 x 2 node and 2 x 2
+    direction children and coarse rows hold a multiple of 4 nodes (64 x 48:
+    levels 0..3; 72 x 40: level 0), the general kernel elsewhere (36 x 20:
+    coarse rows of 18 nodes)."""
+    prob = I.checkerboard(n=nx, ny=ny, n_polar=8, n_azim=16, blocks=4, seed=51)
+    gp = btmg.Problem(prob, dtype=btmg.F32)
+    op = O.OracleProblem(prob)
+    rng = np.random.default_rng(2)
+    for l in range(gp.L - 1):
+        fine = rng.standard_normal(gp.level_shape(l)).astype(np.float32)
+        c = host(gp.restrict(l, dev(fine, torch.float32)))
+        assert rel(c, op.restrict(l, fine.astype(np.float64))) < 1e-6, l
+
+
 @pytest.mark.parametrize("name,mk", SMALL)
 @pytest.mark.parametrize("sweeps", [1, 3, 11])
 def test_upwind_jacobi_every_level(name, mk, sweeps):
