@@ -350,6 +350,17 @@ __global__ void k_scat_gain(const C* __restrict__ sig, const C* __restrict__ cra
   w[i] = (C)(kappa / (1.0 - kappa * S));
 }
 
+// Division by a run-time divisor d in [1, 2^16) of a numerator x in
+// [0, 2^16) as one multiply-high: with m = ceil(2^32 / d) the error
+// x (m - 2^32/d) / 2^32 < 2^-16 <= 1/d never carries past the next integer,
+// so the quotient is exact.
+struct FDiv {
+  uint32_t m;
+  int d;
+  __device__ __forceinline__ explicit FDiv(int dd) : m(dd > 1 ? 0xFFFFFFFFu / (uint32_t)dd + 1u : 0u), d(dd) {}
+  __device__ __forceinline__ int div(int x) const { return d == 1 ? x : (int)__umulhi((uint32_t)x, m); }
+};
+
 // The small coarsest levels in one CTA (as separate kernels they are
 // launch-bound): the restrictions down these levels (the restriction of
 // Sec. 2.5 as k_restrict computes it), then for each level from the
@@ -369,10 +380,12 @@ template <typename C, int TMAX, bool SCAT> __global__ void __launch_bounds__(102
   for (int li = 0; li + 1 < t.count; ++li) {
     const ScatTailLevel<C> F = t.lev[li], Q = t.lev[li + 1];
     const int total = Q.nd * Q.ny * Q.nx;
+    const FDiv dnx(Q.nx), dny(Q.ny), dnrc(Q.nr * Q.nc), dnc(Q.nc);
 #pragma unroll 4
     for (int id = threadIdx.x; id < total; id += blockDim.x) {
-      const int X = id % Q.nx, Y = (id / Q.nx) % Q.ny, N = id / (Q.nx * Q.ny);
-      const int f = N / (Q.nr * Q.nc), J = (N % (Q.nr * Q.nc)) / Q.nc, I = N % Q.nc;
+      const int idy = dnx.div(id), N = dny.div(idy);
+      const int X = id - idy * Q.nx, Y = idy - N * Q.ny;
+      const int f = dnrc.div(N), Jn = N - f * Q.nr * Q.nc, J = dnc.div(Jn), I = Jn - J * Q.nc;
       C acc = C(0);
       for (int aa = 0; aa < F.fr; ++aa) {
         const int j = J * F.fr + aa;
@@ -404,13 +417,14 @@ template <typename C, int TMAX, bool SCAT> __global__ void __launch_bounds__(102
     const int npix = L.nx * L.ny, n_all = npix * L.nd;
     const bool has_coarse = li + 1 < t.count;
     const int nxc = has_coarse ? t.lev[li + 1].nx : 1, npixc = has_coarse ? nxc * t.lev[li + 1].ny : 1;
+    const FDiv dpix(npix), dx(L.nx), dfy(L.fy), dfx(L.fx);
     C* Jprev = nullptr;
     C* Jcur = Ja;
     for (int k = 1; k <= t.nu; ++k) {
 #pragma unroll 4
       for (int idx = threadIdx.x; idx < n_all; idx += blockDim.x) {
-        const int dn = idx / npix, i = idx - dn * npix;
-        const int x = i % L.nx, y = i / L.nx;
+        const int dn = dpix.div(idx), i = idx - dn * npix;
+        const int y = dx.div(i), x = i - y * L.nx;
         const Dir<C> dr = L.dir[dn];
         const bool sxp = dr.mu > C(0), syp = dr.nu > C(0);
         int xu = sxp ? x - 1 : x + 1, yu = syp ? y - 1 : y + 1;
@@ -430,8 +444,8 @@ template <typename C, int TMAX, bool SCAT> __global__ void __launch_bounds__(102
           }
         } else if (has_coarse) {
           const C* cn = Dc + L.parent[dn] * npixc;
-          if (!zx) ux = cn[(y / L.fy) * nxc + xu / L.fx];
-          if (!zy) uy = cn[(yu / L.fy) * nxc + x / L.fx];
+          if (!zx) ux = cn[dfy.div(y) * nxc + dfx.div(xu)];
+          if (!zy) uy = cn[dfy.div(yu) * nxc + dfx.div(x)];
         }
         Jcur[idx] = (ls[idx] + dr.ax * ux + dr.ay * uy) * srcp(dr.ax + dr.ay + lsig[i]);
       }
@@ -451,7 +465,7 @@ template <typename C, int TMAX, bool SCAT> __global__ void __launch_bounds__(102
     for (int idx = threadIdx.x; idx < n_all; idx += blockDim.x) {
       C d = Jprev[idx];
       if (SCAT) {
-        const int dn = idx / npix, i = idx - dn * npix;
+        const int dn = dpix.div(idx), i = idx - dn * npix;
         const Dir<C> dr = L.dir[dn];
         d += cf[i] * srcp(dr.ax + dr.ay + L.sig[i]);
       }
