@@ -38,6 +38,12 @@ int fail(int code, const std::string& msg) {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTile = 32;  // tile edge of the PG and upwind kernels
+// multiprocessors of the current device (152 on GB300 if the query fails)
+int device_sms() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
 constexpr int kDotBlocks = 4 * 152;  // blocks of the learned-step dot product (4 per SM)
 
 // ------------------------------------------------- quadrature (Sec. 2.2) --
@@ -586,7 +592,13 @@ template <typename T, typename C> struct Impl {
       u.init_mode = (l == L - 1) ? INIT_ZERO : INIT_UPSAMPLE;
       u.init = (l == L - 1) ? nullptr : dptr<C>(P->d_delta[l + 1]);
       u.delta_out = dptr<C>(P->d_delta[l]);
-      if ((e = timed(P, PC_UP_COARSE, s, [&] { return launch_upwind<T, C>(u, UP_CORR, P->lev[l].nd, s); })) !=
+      // directions per CTA: as many (up to 8) as still leave two waves of
+      // CTAs, so that each CTA's next direction is fetched during its sweeps
+      const int nd_l = P->lev[l].nd, tiles_l = u.tiles_x * ((P->lev[l].ny + kTile - 1) / kTile);
+      int dpc_l = 1;
+      while (dpc_l < 8 && nd_l % (2 * dpc_l) == 0 && (long)tiles_l * (nd_l / (2 * dpc_l)) >= 2L * 3 * device_sms()) dpc_l *= 2;
+      u.dpc = dpc_l;
+      if ((e = timed(P, PC_UP_COARSE, s, [&] { return launch_upwind<T, C>(u, UP_CORR, nd_l / dpc_l, s); })) !=
           cudaSuccess)
         return e;
     }
