@@ -358,7 +358,9 @@ template <typename T, typename C> struct Impl {
   // b for group g from the scalar-flux partials of every group; with
   // want_norm the squared norm of its fixed part (external source and the
   // other groups' scattering) lands in d_qn2[g] for the relative residual.
-  static cudaError_t source(btmg_problem* P, int g, cudaStream_t s, bool want_norm = true) {
+  // want_norm: q's norm partials; sum_norm: also their sum into d_qn2 (else
+  // the caller sums them with another reduction)
+  static cudaError_t source(btmg_problem* P, int g, cudaStream_t s, bool want_norm = true, bool sum_norm = true) {
     const size_t npix = P->lev[0].npix();
     cudaError_t e = timed(P, PC_MISC, s, [&] {
       const C* src = P->zero_src ? dptr<C>(P->d_zero_src) : dptr<C>(P->d_src);
@@ -366,7 +368,7 @@ template <typename T, typename C> struct Impl {
                               dptr<C>(P->d_phi_part), P->G, g, P->nchunk, (int)npix, dptr<C>(P->d_b), nullptr,
                               want_norm ? P->d_qn2_part : nullptr, P->n_q_blocks, s);
     });
-    if (e != cudaSuccess || !want_norm) return e;
+    if (e != cudaSuccess || !want_norm || !sum_norm) return e;
     return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_qn2_part, P->n_q_blocks, P->d_qn2 + g, s); });
   }
 
@@ -504,8 +506,9 @@ template <typename T, typename C> struct Impl {
   static cudaError_t cycle_part_a(btmg_problem* P, T* psi_g, int g, cudaStream_t s) {
     cudaError_t e;
     const LevelH& L0 = P->lev[0];
-    // 1. r_1 = b - A psi  (Eq. Petrov), weighted norm
-    if ((e = source(P, g, s)) != cudaSuccess) return e;
+    // 1. r_1 = b - A psi  (Eq. Petrov), weighted norm; the source norm is
+    // summed with the residual norm in one launch
+    if ((e = source(P, g, s, true, false)) != cudaSuccess) return e;
     PgArgs<T, C> a = pg_args(P, g, psi_g);
     a.r_out = dptr<C>(P->d_s[0]);
     a.norm_part = P->d_norm_part;
@@ -513,7 +516,9 @@ template <typename T, typename C> struct Impl {
     if ((e = timed(P, PC_PG_RESID, s, [&] { return launch_pg<T, C>(a, PG_RESID, P->d.pg != 0, P->nchunk, s); })) !=
         cudaSuccess)
       return e;
-    return timed(P, PC_MISC, s, [&] { return launch_sum(P->d_norm_part, P->n_norm_sum, P->d_rn2 + g, s); });
+    return timed(P, PC_MISC, s, [&] {
+      return launch_sum2(P->d_norm_part, P->n_norm_sum, P->d_rn2 + g, P->d_qn2_part, P->n_q_blocks, P->d_qn2 + g, s);
+    });
   }
 
   // With `homog`, the cycle of the learned correction c (in P->d_lc, its

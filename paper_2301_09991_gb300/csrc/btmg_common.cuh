@@ -291,6 +291,9 @@ template <typename C>
 cudaError_t launch_phi_sum(const C* phi_part, int nchunk, int npix, C* phi, cudaStream_t s);
 // out[0] = sum(part[0..n)) (deterministic, one block)
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s);
+// two such sums in one launch (each in launch_sum's order, so the same bits)
+cudaError_t launch_sum2(const double* part_a, int na, double* out_a, const double* part_b, int nb, double* out_b,
+                        cudaStream_t s);
 // iterative refinement helpers: extra = alpha * r64 (to the compute type);
 // psi64 += delta / alpha (delta in the storage type)
 // learned correction: features [H8][W8][3] = (rho / rms(rho), log optical

@@ -701,10 +701,9 @@ __global__ void k_phi_sum(const C* __restrict__ part, int nchunk, int npix, C* _
   }
 }
 
-__global__ void k_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
-  pdl_wait();
-  pdl_launch();
-  __shared__ double red[32];
+// one block: the deterministic sum of part[0..n) into out[0]
+__device__ __forceinline__ void block_sum(const double* __restrict__ part, int n, double* __restrict__ out,
+                                          double* red) {
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -715,6 +714,22 @@ __global__ void k_sum(const double* __restrict__ part, int n, double* __restrict
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
     out[0] = s;
   }
+}
+
+__global__ void k_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+  pdl_wait();
+  pdl_launch();
+  __shared__ double red[32];
+  block_sum(part, n, out, red);
+}
+
+__global__ void k_sum2(const double* __restrict__ part_a, int na, double* __restrict__ out_a,
+                       const double* __restrict__ part_b, int nb, double* __restrict__ out_b) {
+  pdl_wait();
+  pdl_launch();
+  __shared__ double red[2][32];
+  block_sum(part_a, na, out_a, red[0]);
+  block_sum(part_b, nb, out_b, red[1]);
 }
 
 // one-block deterministic sum (the same reduction as launch_sum, local to each TU)
@@ -1193,6 +1208,10 @@ cudaError_t launch_coarse_batch(const CoarseBatch& cb, int nu, int tu, int ctas,
 
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s) {
   return launch_pdl(k_sum, dim3(1), dim3(1024), 0, s, part, n, out);
+}
+cudaError_t launch_sum2(const double* part_a, int na, double* out_a, const double* part_b, int nb, double* out_b,
+                        cudaStream_t s) {
+  return launch_pdl(k_sum2, dim3(1), dim3(1024), 0, s, part_a, na, out_a, part_b, nb, out_b);
 }
 #endif
 
