@@ -176,6 +176,22 @@ int btmg_prolong(btmg_problem* p, int32_t level, const void* coarse, void* fine,
  * (FP64 reduction); if non-NULL the call synchronises the stream.          */
 int btmg_mg_cycle(btmg_problem* p, void* psi, double* rel_resid, void* stream);
 
+/* The same cycle (Fig. multi_grid_it) on psi in HOST memory: psi_in
+ * ([G][nd][ny][nx], storage type, the btmg_get_layout order) is copied to a
+ * device buffer that the problem owns (allocated by the first call, freed
+ * with the problem), the cycle runs, and the result is written to psi_out
+ * (host, same layout; may be psi_in).  With page-locked host buffers the
+ * copy back overlaps the cycle's last kernel: each group's final PG Jacobi
+ * (FP32 paired kernel, direction chunks a multiple of 4) runs as four
+ * launches over consecutive direction ranges on side streams, and every
+ * range is copied as soon as its launch is done; other kernels copy a
+ * group while the next group cycles.  rel_resid as in btmg_mg_cycle; with
+ * it the call returns when psi_out is complete, without it psi_out is
+ * complete once `stream` is.  The result equals btmg_mg_cycle's bit for
+ * bit.  Errors as btmg_mg_cycle; BTMG_ERR_CUDA if the device buffer cannot
+ * be allocated.                                                            */
+int btmg_mg_cycle_host(btmg_problem* p, const void* psi_in, void* psi_out, double* rel_resid, void* stream);
+
 /* Fixed-source solve from the caller's psi: groups in order, each cycled
  * until its relative residual is below rtol or max_cycles; repeated over
  * groups while upscatter makes the all-group residual exceed rtol.  Cycles

@@ -26,7 +26,7 @@ ERR_NOALLOC_TOO_LARGE = -9
 EXPORTS = (
     "btmg_create_problem", "btmg_destroy_problem", "btmg_num_unknowns", "btmg_get_layout",
     "btmg_num_levels", "btmg_level_info", "btmg_level_quadrature", "btmg_scalar_flux",
-    "btmg_apply_operator", "btmg_smooth", "btmg_restrict", "btmg_prolong", "btmg_mg_cycle",
+    "btmg_apply_operator", "btmg_smooth", "btmg_restrict", "btmg_prolong", "btmg_mg_cycle", "btmg_mg_cycle_host",
     "btmg_solve", "btmg_error_string", "btmg_last_error", "btmg_profile", "btmg_profile_read",
     "btmg_launch_count", "btmg_apply_operator_noalloc", "btmg_solve_refined",
     "btmg_unet_create", "btmg_unet_destroy", "btmg_unet_num_params", "btmg_unet_get_params",
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
     L.btmg_restrict.argtypes = [vp, i32, vp, vp, vp]
     L.btmg_prolong.argtypes = [vp, i32, vp, vp, vp]
     L.btmg_mg_cycle.argtypes = [vp, vp, dp, vp]
+    L.btmg_mg_cycle_host.argtypes = [vp, vp, vp, dp, vp]
     L.btmg_solve.argtypes = [vp, vp, C.c_double, i32, C.POINTER(SolveInfo), vp]
     L.btmg_profile.argtypes = [vp, i32]
     L.btmg_profile_read.argtypes = [vp, dp, i64p, i32]
@@ -448,6 +449,21 @@ class Problem:
         rel = C.c_double(0.0)
         _check(load().btmg_mg_cycle(self.h, _ptr(psi), C.byref(rel) if want_residual else None,
                                     _stream_ptr(stream)))
+        return rel.value if want_residual else None
+
+    def mg_cycle_host(self, psi_in, psi_out=None, want_residual=True, stream=None):
+        """One cycle on host tensors (btmg_mg_cycle_host): psi_in, psi_out
+        contiguous CPU tensors of the problem's shape and storage type
+        (psi_out defaults to psi_in; page-locked memory lets the copy back
+        overlap the last kernel).  Returns the relative residual of the
+        input, or None."""
+        psi_out = psi_in if psi_out is None else psi_out
+        for t in (psi_in, psi_out):
+            if t.is_cuda or t.dtype != self.torch_dtype or not t.is_contiguous() or tuple(t.shape) != self.shape:
+                raise ValueError("psi_in/psi_out must be contiguous CPU tensors %s of %s" % (self.shape, self.torch_dtype))
+        rel = C.c_double(0.0)
+        _check(load().btmg_mg_cycle_host(self.h, _ptr(psi_in), _ptr(psi_out),
+                                         C.byref(rel) if want_residual else None, _stream_ptr(stream)))
         return rel.value if want_residual else None
 
     def solve(self, psi, rtol=1e-6, max_cycles=1000, check_every=1, max_outer=0, history=True,

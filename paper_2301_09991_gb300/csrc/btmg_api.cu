@@ -38,6 +38,7 @@ int fail(int code, const std::string& msg) {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTile = 32;  // tile edge of the PG and upwind kernels
+constexpr int kOutParts = 4;  // direction ranges of the host-buffer cycle's final launch
 // multiprocessors of the current device (152 on GB300 if the query fails)
 int device_sms() {
   int dev = 0, sms = 152;
@@ -259,6 +260,13 @@ struct btmg_problem {
   int64_t learn_count = 0;      // mg_cycle calls since the net was attached
   bool learn_off = false;       // solve-time fallback to plain cycles (reset by each solve)
   int32_t learn_fallbacks = 0;  // solves that fell back since the net was attached
+  // host-buffer cycle (btmg_mg_cycle_host): device copy of psi, and while a
+  // call runs the host destination of every group's final PG Jacobi, which
+  // is streamed out in direction ranges on the side streams
+  void* d_hpsi = nullptr;  // [G][nd][ny][nx] storage type
+  void* out_host = nullptr;
+  cudaStream_t out_s[kOutParts] = {};
+  cudaEvent_t out_ev[kOutParts + 1] = {};
   // per-kernel-class CUDA-event timing (btmg_profile) and launch counting
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_pool;
@@ -637,7 +645,75 @@ template <typename T, typename C> struct Impl {
       j.extra = nullptr;
       j.phi_part = dptr<C>(P->d_lphi);
     }
-    return timed(P, PC_PG_JACOBI, s, [&] { return launch_pg<T, C>(j, PG_JACOBI, P->d.pg != 0, P->nchunk, s); });
+    if (homog || !P->out_host)
+      return timed(P, PC_PG_JACOBI, s, [&] { return launch_pg<T, C>(j, PG_JACOBI, P->d.pg != 0, P->nchunk, s); });
+    return jacobi_to_host(P, j, g, s);
+  }
+
+  // The final PG Jacobi of group g with its result copied to P->out_host.
+  // The paired FP32 kernel runs as kOutParts launches over consecutive
+  // direction-chunk ranges, each on its own side stream and followed there
+  // by the copy of its directions, so the copies of the first ranges overlap
+  // the kernels of the later ones (the ranges share no data: each writes its
+  // own directions and chunk partials).  Otherwise one launch, then the
+  // group's copy on a side stream (it overlaps the next group's cycle).
+  // The side streams fork from and join back into s through events.
+  static cudaError_t jacobi_to_host(btmg_problem* P, PgArgs<T, C>& j, int g, cudaStream_t s) {
+    const LevelH& L0 = P->lev[0];
+    const size_t plane = L0.npix() * sizeof(T);
+    char* hout = reinterpret_cast<char*>(P->out_host) + (size_t)g * L0.nd * plane;
+    const char* dsrc = reinterpret_cast<const char*>(j.psi_out);
+    bool split = false;
+    if constexpr (std::is_same<T, float>::value && std::is_same<C, float>::value)
+      split = P->d.pg != 0 && P->nchunk % kOutParts == 0 && pg2_applies(j);
+    cudaError_t e;
+    if (!split) {
+      if ((e = launch_pg<T, C>(j, PG_JACOBI, P->d.pg != 0, P->nchunk, s)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(P->out_ev[0], s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(P->out_s[0], P->out_ev[0], 0)) != cudaSuccess) return e;
+      if ((e = cudaMemcpyAsync(hout, dsrc, L0.nd * plane, cudaMemcpyDeviceToHost, P->out_s[0])) != cudaSuccess)
+        return e;
+      if ((e = cudaEventRecord(P->out_ev[1], P->out_s[0])) != cudaSuccess) return e;
+      return cudaStreamWaitEvent(s, P->out_ev[1], 0);
+    }
+    if ((e = cudaEventRecord(P->out_ev[0], s)) != cudaSuccess) return e;
+    const int per = P->nchunk / kOutParts;
+    const size_t bytes = (size_t)per * P->dpc * plane;
+    for (int i = 0; i < kOutParts; ++i) {
+      cudaStream_t si = P->out_s[i];
+      if ((e = cudaStreamWaitEvent(si, P->out_ev[0], 0)) != cudaSuccess) return e;
+      PgArgs<T, C> ji = j;
+      ji.chunk0 = i * per;
+      if ((e = launch_pg<T, C>(ji, PG_JACOBI, true, per, si)) != cudaSuccess) return e;
+      if ((e = cudaMemcpyAsync(hout + i * bytes, dsrc + i * bytes, bytes, cudaMemcpyDeviceToHost, si)) != cudaSuccess)
+        return e;
+      if ((e = cudaEventRecord(P->out_ev[i + 1], si)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(s, P->out_ev[i + 1], 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  // One cycle on host buffers: psi_in to the device copy, the cycle, every
+  // group's result streamed to psi_out as its final launch completes (a
+  // cycle with the learned step changes psi after that launch: its copy
+  // follows the whole cycle instead).
+  static int mg_cycle_host(btmg_problem* P, const void* h_in, void* h_out, double* rel, cudaStream_t s) {
+    const size_t bytes = (size_t)P->G * P->lev[0].n() * sizeof(T);
+    if (!P->d_hpsi) CK(cudaMalloc(&P->d_hpsi, bytes));
+    for (int i = 0; i < kOutParts; ++i)
+      if (!P->out_s[i]) CK(cudaStreamCreateWithFlags(&P->out_s[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= kOutParts; ++i)
+      if (!P->out_ev[i]) CK(cudaEventCreateWithFlags(&P->out_ev[i], cudaEventDisableTiming));
+    CK(cudaMemcpyAsync(P->d_hpsi, h_in, bytes, cudaMemcpyHostToDevice, s));
+    if (P->learned) {
+      if (int rc = mg_cycle(P, P->d_hpsi, nullptr, s)) return rc;
+      CK(cudaMemcpyAsync(h_out, P->d_hpsi, bytes, cudaMemcpyDeviceToHost, s));
+      return rel ? read_rel(P, s, 0, nullptr, rel) : BTMG_OK;
+    }
+    P->out_host = h_out;
+    const int rc = mg_cycle(P, P->d_hpsi, rel, s);
+    P->out_host = nullptr;
+    return rc;
   }
 
   static int cycle_group(btmg_problem* P, T* psi_g, int g, cudaStream_t s, bool learn = false) {
@@ -1039,6 +1115,11 @@ int dispatch(int dtype, Args&&... args) {
 template <typename T, typename C> struct RunCycle {
   static int run(btmg_problem* P, void* psi, double* rel, cudaStream_t s) { return Impl<T, C>::mg_cycle(P, psi, rel, s); }
 };
+template <typename T, typename C> struct RunCycleHost {
+  static int run(btmg_problem* P, const void* in, void* out, double* rel, cudaStream_t s) {
+    return Impl<T, C>::mg_cycle_host(P, in, out, rel, s);
+  }
+};
 template <typename T, typename C> struct RunSolve {
   static int run(btmg_problem* P, void* psi, double rtol, int mc, btmg_solve_info* info, cudaStream_t s) {
     return Impl<T, C>::solve(P, psi, rtol, mc, info, s);
@@ -1124,6 +1205,11 @@ void destroy(btmg_problem* P) {
     if (p) cudaFree(p);
   if (P->h_pinned) cudaFreeHost(P->h_pinned);
   if (P->own_stream) cudaStreamDestroy(P->own_stream);
+  for (auto& st : P->out_s)
+    if (st) cudaStreamDestroy(st);
+  for (auto& ev : P->out_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (P->d_hpsi) cudaFree(P->d_hpsi);
   if (P->order_event) cudaEventDestroy(P->order_event);
   delete P;
 }
@@ -2233,6 +2319,11 @@ int btmg_prolong(btmg_problem* p, int32_t level, const void* coarse, void* fine,
 int btmg_mg_cycle(btmg_problem* p, void* psi, double* rel_resid, void* stream) {
   if (!p || !psi) return fail(BTMG_ERR_INVALID_ARG, "null argument");
   return dispatch<RunCycle>(p->dtype, p, psi, rel_resid, (cudaStream_t)stream);
+}
+
+int btmg_mg_cycle_host(btmg_problem* p, const void* psi_in, void* psi_out, double* rel_resid, void* stream) {
+  if (!p || !psi_in || !psi_out) return fail(BTMG_ERR_INVALID_ARG, "null argument");
+  return dispatch<RunCycleHost>(p->dtype, p, psi_in, psi_out, rel_resid, (cudaStream_t)stream);
 }
 
 int btmg_solve(btmg_problem* p, void* psi, double rtol, int32_t max_cycles, btmg_solve_info* info, void* stream) {

@@ -118,6 +118,7 @@ template <typename T, typename C> struct PgArgs {
   // [nd][ny][nx] scratch of Psi_x, Psi_y, k_x, k_y
   C cm1[7], cd1[7], cs1[7];
   C *gpx, *gpy, *gkx, *gky;
+  int chunk0;  // k_pg2: direction chunk of blockIdx.y = 0 (a launch over chunks chunk0 ..)
 };
 
 // ------------------------------------------------------- upwind Jacobi ----

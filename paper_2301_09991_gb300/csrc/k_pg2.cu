@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
   __shared__ __align__(8) uint64_t bar;
 
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x, chunk_id = blockIdx.y;
+  const int tile = blockIdx.x, chunk_id = a.chunk0 + blockIdx.y;
   const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
   const int nx = a.nx, ny = a.ny;
   const size_t npix = (size_t)nx * ny;
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(NT, 2) k_pg2(const PgArgs<float, float> a, con
     if (tid == 0) {
       double s = 0.0;
       for (int w = 0; w < NT / 32; ++w) s += red[w];
-      a.norm_part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s * (double)a.dxdy;
+      a.norm_part[(size_t)chunk_id * gridDim.x + blockIdx.x] = s * (double)a.dxdy;
     }
   }
 }
