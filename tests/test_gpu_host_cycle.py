@@ -5,7 +5,7 @@ direction chunks (the paired kernel's final launch split into four
 direction ranges, each copied back as it completes), one group and three
 groups; FP64 with PG and FP32 with the upwind fine scheme (one final launch,
 the copy after it); page-locked and pageable host memory; in place and into
-a second buffer.
+a second buffer; a cycle with the learned correction.
 """
 import pytest
 import torch
@@ -62,3 +62,25 @@ def test_host_cycle_rejects_device_tensors():
     gp = btmg.Problem(prob, dtype=btmg.F32, pg=1)
     with pytest.raises(ValueError):
         gp.mg_cycle_host(gp.zeros())
+
+
+def test_host_cycle_with_the_learned_step():
+    """A cycle with the learned correction changes psi after its final PG
+    Jacobi launch, so its copy back follows the whole cycle: two problems
+    with the same network, one cycled on device buffers and one on host
+    buffers, agree bit for bit over three cycles (learned steps in the first
+    and third)."""
+    prob = I.checkerboard(n=48, ny=40, n_polar=8, n_azim=16, blocks=4, seed=69, c=0.95, length=5.0)
+    net = btmg.UNet(in_channels=btmg.LEARN_FEATURES, seed=3)
+    dev = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+    hst = btmg.Problem(prob, dtype=btmg.F32, pg=0)
+    dev.set_learned(net, every=2)
+    hst.set_learned(net, every=2)
+    psi0 = I.random_field(dev.shape, seed=70)
+    d = torch.tensor(psi0, dtype=torch.float32, device="cuda")
+    h = torch.tensor(psi0, dtype=torch.float32).pin_memory()
+    for call in range(3):
+        r_dev = dev.mg_cycle(d)
+        r_host = hst.mg_cycle_host(h)
+        assert r_host == r_dev, (call, r_host, r_dev)
+        assert torch.equal(h, d.cpu()), call
