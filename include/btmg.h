@@ -181,15 +181,18 @@ int btmg_mg_cycle(btmg_problem* p, void* psi, double* rel_resid, void* stream);
  * device buffer that the problem owns (allocated by the first call, freed
  * with the problem), the cycle runs, and the result is written to psi_out
  * (host, same layout; may be psi_in).  With page-locked host buffers the
- * copy back overlaps the cycle's last kernel: each group's final PG Jacobi
- * (FP32 paired kernel, direction chunks a multiple of 4) runs as four
- * launches over consecutive direction ranges on side streams, and every
- * range is copied as soon as its launch is done; other kernels copy a
- * group while the next group cycles.  rel_resid as in btmg_mg_cycle; with
- * it the call returns when psi_out is complete, without it psi_out is
- * complete once `stream` is.  The result equals btmg_mg_cycle's bit for
- * bit.  Errors as btmg_mg_cycle; BTMG_ERR_CUDA if the device buffer cannot
- * be allocated.                                                            */
+ * copies overlap kernels: each group's final PG Jacobi (FP32 paired kernel,
+ * direction chunks a multiple of 4) runs as four launches over consecutive
+ * direction ranges on side streams, every range copied back as soon as its
+ * launch is done (other kernels copy a group while the next group cycles);
+ * with one group on the paired kernel the copy in also arrives in four
+ * ranges, each followed at once by its scalar-flux partials and its
+ * residual with zero source, and the source is added in the restriction to
+ * level 1.  rel_resid as in btmg_mg_cycle (then summed in another order:
+ * equal to about 1e-8); with it the call returns when psi_out is complete,
+ * without it psi_out is complete once `stream` is.  psi_out equals
+ * btmg_mg_cycle's result bit for bit.  Errors as btmg_mg_cycle;
+ * BTMG_ERR_OOM if the device buffers cannot be allocated.                 */
 int btmg_mg_cycle_host(btmg_problem* p, const void* psi_in, void* psi_out, double* rel_resid, void* stream);
 
 /* Fixed-source solve from the caller's psi: groups in order, each cycled

@@ -264,6 +264,10 @@ struct btmg_problem {
   // call runs the host destination of every group's final PG Jacobi, which
   // is streamed out in direction ranges on the side streams
   void* d_hpsi = nullptr;  // [G][nd][ny][nx] storage type
+  void* d_hzero = nullptr; // [ny][nx] zeros (compute type): the source of the range residuals
+  double* d_hparts = nullptr;  // residual-norm partials of the level-1 restriction that forms r
+  int n_hparts = 0;
+  bool first_restricted = false;  // level 1's source is already formed (skip the first restriction)
   void* out_host = nullptr;
   cudaStream_t out_s[kOutParts] = {};
   cudaEvent_t out_ev[kOutParts + 1] = {};
@@ -552,7 +556,7 @@ template <typename T, typename C> struct Impl {
       tail = P->plain_tail;
     }
     // 2. restriction to every coarser level (those of the tail inside it)
-    for (int l = 0; l + 1 < L && l < tail; ++l) {
+    for (int l = P->first_restricted ? 1 : 0; l + 1 < L && l < tail; ++l) {
       const LevelH &A = P->lev[l], &B = P->lev[l + 1];
       if ((e = timed(P, PC_RESTRICT, s, [&] {
              return launch_restrict<C>(dptr<C>(P->d_s[l]), dptr<C>(P->d_s[l + 1]), dptr<C>(P->d_rcoef[l]), A.nx,
@@ -693,6 +697,72 @@ template <typename T, typename C> struct Impl {
     return cudaSuccess;
   }
 
+  // The host-buffer cycle with the copy in overlapped too (one group, FP32
+  // paired kernel, no learned step, refinement source or smoother): psi
+  // arrives in kOutParts direction ranges on the side streams, and each
+  // range's scalar-flux partials and its residual with zero source (-A psi)
+  // run as soon as it is in; then the source b, the restriction to level 1
+  // that forms r = b - A psi on the way (bit for bit the residual kernel's
+  // r, written back for the finest sweeps) with the residual norm, and the
+  // rest of the cycle with the copy back of mg_cycle_host.  Returns
+  // kNotPipelined, having queued nothing, when the problem does not qualify.
+  static constexpr int kNotPipelined = 1;  // not a status (statuses are 0 or negative)
+  static int mg_cycle_host_pipelined(btmg_problem* P, const void* h_in, void* h_out, double* rel, cudaStream_t s) {
+    if constexpr (!(std::is_same<T, float>::value && std::is_same<C, float>::value)) {
+      return kNotPipelined;
+    } else {
+      const LevelH &L0 = P->lev[0], &L1 = P->lev[P->L > 1 ? 1 : 0];
+      if (P->G != 1 || P->d.pg == 0 || P->learned || P->inner_extra || P->zero_src || P->d.scat_levels != 0 ||
+          P->L < 2 || P->plain_tail < 1 || P->nchunk % kOutParts != 0)
+        return kNotPipelined;
+      PgArgs<T, C> a = pg_args(P, 0, dptr<T>(P->d_hpsi));
+      a.b = dptr<C>(P->d_hzero);
+      a.extra = nullptr;
+      a.r_out = dptr<C>(P->d_s[0]);
+      a.norm_part = P->d_norm_part;  // the range launches' partials are not used
+      int nparts = 0;
+      if (!pg2_applies(a) || !restrict_rb_applies(L0.nx, L0.ny, L0.nr, L0.nc, L1.nx, L1.ny, L1.nr, L1.nc, L0.fx,
+                                                  L0.fy, L0.fr, L0.fc, 1 << 24, &nparts))
+        return kNotPipelined;
+      if (!P->d_hparts) {
+        CK(cudaMalloc(&P->d_hparts, (size_t)nparts * sizeof(double)));
+        P->n_hparts = nparts;
+      }
+      const size_t plane = L0.npix() * sizeof(T);
+      const int per = P->nchunk / kOutParts;
+      const size_t rbytes = (size_t)per * P->dpc * plane;
+      CK(cudaEventRecord(P->out_ev[0], s));
+      for (int i = 0; i < kOutParts; ++i) {
+        cudaStream_t si = P->out_s[i];
+        const size_t n0 = (size_t)i * per * P->dpc;  // first direction of the range
+        CK(cudaStreamWaitEvent(si, P->out_ev[0], 0));
+        CK(cudaMemcpyAsync(reinterpret_cast<char*>(P->d_hpsi) + i * rbytes,
+                           reinterpret_cast<const char*>(h_in) + i * rbytes, rbytes, cudaMemcpyHostToDevice, si));
+        CK(launch_phi_partial<T, C>(dptr<T>(P->d_hpsi) + n0 * L0.npix(),
+                                    dptr<C>(P->d_phi_part) + (size_t)i * per * L0.npix(),
+                                    reinterpret_cast<const Dir<C>*>(P->d_dir[0]) + n0, L0.nx, L0.ny,
+                                    per * P->dpc, P->dpc, per, si));
+        PgArgs<T, C> ai = a;
+        ai.chunk0 = i * per;
+        CK(launch_pg<T, C>(ai, PG_RESID, true, per, si));
+        CK(cudaEventRecord(P->out_ev[i + 1], si));
+        CK(cudaStreamWaitEvent(s, P->out_ev[i + 1], 0));
+      }
+      CK(source(P, 0, s, true, false));
+      CK(launch_restrict_rb(dptr<C>(P->d_s[0]), dptr<C>(P->d_b), dptr<C>(P->d_s[1]), dptr<C>(P->d_rcoef[0]),
+                            reinterpret_cast<const Dir<C>*>(P->d_dir[0]), L0.dx * L0.dy, P->d_hparts, L0.nx,
+                            L0.ny, L0.nr, L0.nc, L1.nx, L1.ny, L1.nr, L1.nc, s));
+      CK(launch_sum2(P->d_hparts, P->n_hparts, P->d_rn2, P->d_qn2_part, P->n_q_blocks, P->d_qn2, s));
+      P->out_host = h_out;
+      P->first_restricted = true;
+      const cudaError_t e = cycle_part_b(P, dptr<T>(P->d_hpsi), 0, s);
+      P->first_restricted = false;
+      P->out_host = nullptr;
+      CK(e);
+      return rel ? read_rel(P, s, 0, nullptr, rel) : BTMG_OK;
+    }
+  }
+
   // One cycle on host buffers: psi_in to the device copy, the cycle, every
   // group's result streamed to psi_out as its final launch completes (a
   // cycle with the learned step changes psi after that launch: its copy
@@ -704,6 +774,12 @@ template <typename T, typename C> struct Impl {
       if (!P->out_s[i]) CK(cudaStreamCreateWithFlags(&P->out_s[i], cudaStreamNonBlocking));
     for (int i = 0; i <= kOutParts; ++i)
       if (!P->out_ev[i]) CK(cudaEventCreateWithFlags(&P->out_ev[i], cudaEventDisableTiming));
+    if (!P->d_hzero) {
+      CK(cudaMalloc(&P->d_hzero, P->lev[0].npix() * sizeof(C)));
+      CK(cudaMemsetAsync(P->d_hzero, 0, P->lev[0].npix() * sizeof(C), s));
+    }
+    const int prc = mg_cycle_host_pipelined(P, h_in, h_out, rel, s);
+    if (prc != kNotPipelined) return prc;
     CK(cudaMemcpyAsync(P->d_hpsi, h_in, bytes, cudaMemcpyHostToDevice, s));
     if (P->learned) {
       if (int rc = mg_cycle(P, P->d_hpsi, nullptr, s)) return rc;
@@ -1210,6 +1286,8 @@ void destroy(btmg_problem* P) {
   for (auto& ev : P->out_ev)
     if (ev) cudaEventDestroy(ev);
   if (P->d_hpsi) cudaFree(P->d_hpsi);
+  if (P->d_hzero) cudaFree(P->d_hzero);
+  if (P->d_hparts) cudaFree(P->d_hparts);
   if (P->order_event) cudaEventDestroy(P->order_event);
   delete P;
 }

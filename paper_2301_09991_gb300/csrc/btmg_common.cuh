@@ -292,6 +292,14 @@ template <typename C>
 cudaError_t launch_phi_sum(const C* phi_part, int nchunk, int npix, C* phi, cudaStream_t s);
 // out[0] = sum(part[0..n)) (deterministic, one block)
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s);
+// FP32 restriction level 0 -> 1 of the fine residual r = r' + b assembled
+// on the fly (r' = -A psi from a residual launch with zero source), r written
+// back, with one norm partial p_n dx dy r^2 per CTA (k_mg_impl.cuh)
+bool restrict_rb_applies(int nx, int ny, int nr, int nc, int nxc, int nyc, int nrc, int ncc, int fx, int fy,
+                         int fr, int fc, int max_parts, int* nparts);
+cudaError_t launch_restrict_rb(float* r, const float* b, float* coarse, const float* rcoef, const Dir<float>* dir,
+                               double dxdy, double* part, int nx, int ny, int nr, int nc, int nxc, int nyc, int nrc,
+                               int ncc, cudaStream_t s);
 // two such sums in one launch (each in launch_sum's order, so the same bits)
 cudaError_t launch_sum2(const double* part_a, int na, double* out_a, const double* part_b, int nb, double* out_b,
                         cudaStream_t s);

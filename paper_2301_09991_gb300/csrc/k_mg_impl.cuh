@@ -627,6 +627,66 @@ __global__ void k_restrict4(const float* __restrict__ fine, float* __restrict__ 
   *reinterpret_cast<float4*>(coarse + ((size_t)N * nyc + Y) * nxc + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
+// k_restrict4 for a fine residual assembled here: r = r' + b, with r' the
+// residual of a launch with zero source (-A psi) and b isotropic; r is
+// written back in place (b - A psi with one rounding, as the residual kernel
+// forms it), restricted exactly as k_restrict4 restricts r, and the CTA's
+// share of the weighted squared norm sum p_n dx dy r^2 written to
+// part[block] (the fine nodes of the CTA's coarse cells).
+__global__ void __launch_bounds__(256) k_restrict4_rb(float* __restrict__ r, const float* __restrict__ b,
+                                                      float* __restrict__ coarse, const float* __restrict__ rcoef,
+                                                      const Dir<float>* __restrict__ dir, double dxdy,
+                                                      double* __restrict__ part, int nx, int ny, int nr, int nc,
+                                                      int nxc, int nyc, int nrc, int ncc) {
+  pdl_wait();
+  pdl_launch();
+  __shared__ double red[8];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y * blockDim.y + threadIdx.y, N = blockIdx.z;
+  double nrm = 0.0;
+  if (4 * q < nxc && Y < nyc) {
+    const int f = N / (nrc * ncc), J = (N % (nrc * ncc)) / ncc, I = N % ncc;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int aa = 0; aa < 2; ++aa)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb) {
+        const int n = f * nr * nc + (2 * J + aa) * nc + 2 * I + bb;
+        const float w = rcoef[n];
+        double ns = 0.0;
+#pragma unroll
+        for (int yy = 0; yy < 2; ++yy) {
+          float* row = r + ((size_t)n * ny + 2 * Y + yy) * nx + 8 * q;
+          const float* brow = b + (size_t)(2 * Y + yy) * nx + 8 * q;
+          const float4 u = *reinterpret_cast<const float4*>(row), v = *reinterpret_cast<const float4*>(row + 4);
+          const float4 bu = *reinterpret_cast<const float4*>(brow), bv = *reinterpret_cast<const float4*>(brow + 4);
+          const float x[8] = {bu.x + u.x, bu.y + u.y, bu.z + u.z, bu.w + u.w,
+                              bv.x + v.x, bv.y + v.y, bv.z + v.z, bv.w + v.w};
+          *reinterpret_cast<float4*>(row) = make_float4(x[0], x[1], x[2], x[3]);
+          *reinterpret_cast<float4*>(row + 4) = make_float4(x[4], x[5], x[6], x[7]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            acc[k] += w * x[2 * k];
+            acc[k] += w * x[2 * k + 1];
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) ns += (double)x[k] * (double)x[k];
+        }
+        nrm += (double)dir[n].w * ns;
+      }
+    *reinterpret_cast<float4*>(coarse + ((size_t)N * nyc + Y) * nxc + 4 * q) =
+        make_float4(acc[0], acc[1], acc[2], acc[3]);
+  }
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((t & 31) == 0) red[t >> 5] = nrm;
+  __syncthreads();
+  if (t == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < 8; ++w) sum += red[w];
+    part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum * dxdy;
+  }
+}
+
 template <typename C>
 __global__ void k_prolong(const C* __restrict__ coarse, C* __restrict__ fine, int nx, int ny, int nr, int nc,
                           int nxc, int nyc, int nrc, int ncc, int fx, int fy, int fr, int fc) {
@@ -1208,6 +1268,26 @@ cudaError_t launch_coarse_batch(const CoarseBatch& cb, int nu, int tu, int ctas,
 
 cudaError_t launch_sum(const double* part, int n, double* out, cudaStream_t s) {
   return launch_pdl(k_sum, dim3(1), dim3(1024), 0, s, part, n, out);
+}
+// restriction level 0 -> 1 of r = r' + b with the norm partials
+// (k_restrict4_rb); false when the level is not of k_restrict4's form or
+// the partials do not fit max_parts; *nparts receives their number
+bool restrict_rb_applies(int nx, int ny, int nr, int nc, int nxc, int nyc, int nrc, int ncc, int fx, int fy,
+                         int fr, int fc, int max_parts, int* nparts) {
+  if (!(fx == 2 && fy == 2 && fr == 2 && fc == 2 && nx == 2 * nxc && ny == 2 * nyc && nr == 2 * nrc &&
+        nc == 2 * ncc && nxc % 4 == 0 && 8 * nrc * ncc <= 65535))
+    return false;
+  const long parts = (long)((nxc / 4 + 31) / 32) * ((nyc + 7) / 8) * (8 * nrc * ncc);
+  if (parts > max_parts) return false;
+  *nparts = (int)parts;
+  return true;
+}
+cudaError_t launch_restrict_rb(float* r, const float* b, float* coarse, const float* rcoef, const Dir<float>* dir,
+                               double dxdy, double* part, int nx, int ny, int nr, int nc, int nxc, int nyc, int nrc,
+                               int ncc, cudaStream_t s) {
+  const dim3 block(32, 8), grid((nxc / 4 + 31) / 32, (nyc + 7) / 8, 8 * nrc * ncc);
+  return launch_pdl(k_restrict4_rb, grid, block, 0, s, r, b, coarse, rcoef, dir, dxdy, part, nx, ny, nr, nc, nxc,
+                    nyc, nrc, ncc);
 }
 cudaError_t launch_sum2(const double* part_a, int na, double* out_a, const double* part_b, int nb, double* out_b,
                         cudaStream_t s) {
