@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(256) k_restrict4_rb(float* __restrict__ r, con
       for (int bb = 0; bb < 2; ++bb) {
         const int n = f * nr * nc + (2 * J + aa) * nc + 2 * I + bb;
         const float w = rcoef[n];
-        double ns = 0.0;
+        float ns = 0.f;  // squares in FP32 (FP64 arithmetic is slow on this GPU), summed in FP64 below
 #pragma unroll
         for (int yy = 0; yy < 2; ++yy) {
           float* row = r + ((size_t)n * ny + 2 * Y + yy) * nx + 8 * q;
@@ -669,9 +669,9 @@ __global__ void __launch_bounds__(256) k_restrict4_rb(float* __restrict__ r, con
             acc[k] += w * x[2 * k + 1];
           }
 #pragma unroll
-          for (int k = 0; k < 8; ++k) ns += (double)x[k] * (double)x[k];
+          for (int k = 0; k < 8; ++k) ns += x[k] * x[k];
         }
-        nrm += (double)dir[n].w * ns;
+        nrm += (double)dir[n].w * (double)ns;
       }
     *reinterpret_cast<float4*>(coarse + ((size_t)N * nyc + Y) * nxc + 4 * q) =
         make_float4(acc[0], acc[1], acc[2], acc[3]);

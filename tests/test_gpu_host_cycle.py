@@ -2,7 +2,7 @@
 buffers (btmg_mg_cycle): from the same input the same psi bit for bit and
 the same residual norm (to 1e-6: with one group on the paired kernel the
 copy in overlaps the residual, whose norm is then summed from the FP32
-residual in another order, the squares in FP64 rather than in FP32 groups),
+residual in another order),
 on two calls in a row.  Cases: FP32 with PG and 8 direction chunks (the
 paired kernel's final launch split into four direction ranges, each copied
 back as it completes; with one group also the copy in split, each range's
